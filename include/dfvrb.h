@@ -1,0 +1,163 @@
+/*
+ * dfvrb.h -- C ABI of the GB300 (sm_103a) diffuse rigid-body finite-volume
+ * library: the explicit Eulerian cell update of Wallis, Barton & Nikiforakis,
+ * "A unified diffuse interface method for the interaction of rigid bodies with
+ * elastoplastic solids and multi-phase mixtures" (arXiv:2111.11806).
+ *
+ * The calls follow the paper's statement of the problem (Sec. 3, eq:sys_vec_form):
+ * a uniform Cartesian grid, materials, initial primitive fields including the
+ * rigid field r, a time step from the CFL condition, then steps of seeding
+ * (Sec. 3.2) and SSP-RK3 (Sec. 3.1).
+ *
+ * Conventions used by every call
+ *  - Status: every call returns dfv_status, 0 on success, < 0 on error.  No
+ *    C++ exception crosses the ABI.  dfv_last_error(grid) gives a message for
+ *    the last error on that grid (a static or grid-owned string).
+ *  - Memory: the library allocates NO device memory.  The caller provides one
+ *    device workspace of at least dfv_workspace_bytes() bytes (256-byte
+ *    aligned) and keeps it alive until dfv_destroy(); the library places all
+ *    state planes, temporaries and reduction scratch in it.  Host buffers are
+ *    owned by the caller and are only read or written during the call.
+ *  - Streams: all device work of a grid is issued on the cudaStream_t passed
+ *    at creation (NULL = legacy default stream).  Calls that return host data
+ *    (dfv_compute_dt, dfv_get_fields to host, dfv_get_body, dfv_check)
+ *    synchronise that stream.
+ *  - Field layout: structure of arrays, one plane per variable, planes stored
+ *    one after another, each plane ncell = n0*n1*n2 doubles with x fastest
+ *    (cell (i,j,k) at i + n0*(j + n1*k)).
+ *    Primitive planes (N materials, d dimensions, nv stretch components):
+ *        phi_1..phi_{N-1}, rho_1..rho_N, u_1..u_d, p, V_1..V_nv, r
+ *    Conserved planes, same count and order of groups:
+ *        phi_1..phi_{N-1}, (phi rho)_1..(phi rho)_N, (rho u)_1..(rho u)_d, rho E, V_1..V_nv, r
+ *    nv = 0 for fluids; for solids nv = 3 (1-D: xx,yy,zz) or 5 (2-D:
+ *    xx,xy,yx,yy,zz).  With N = 1 there is no phi plane and the single
+ *    density plane is rho.
+ *  - Boundaries: bc[2*d] / bc[2*d+1] for the low / high side of direction d:
+ *    DFV_BC_TRANSMISSIVE (zero-gradient halo) or DFV_BC_PERIODIC (both sides
+ *    of a direction must then be periodic).
+ */
+#ifndef DFVRB_H
+#define DFVRB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int dfv_status;
+
+#define DFV_OK 0
+#define DFV_ERR_ARG (-1)          /* invalid argument or call order */
+#define DFV_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define DFV_ERR_NONPHYSICAL (-3)  /* a kernel saw rho <= 0, c^2 <= 0 or NaN */
+#define DFV_ERR_TIMEOUT (-4)      /* a host wait exceeded its time limit */
+#define DFV_ERR_WORKSPACE (-5)    /* workspace too small or misaligned */
+#define DFV_ERR_UNSUPPORTED (-6)  /* combination not built (e.g. 3-D solid) */
+
+#define DFV_FP64 0       /* plain FP64 everywhere */
+#define DFV_FP32 1       /* FP32 storage, reconstruction and fluxes; FP64 in
+                            closures of cells with a volume fraction < 1e-6
+                            and in the polar decomposition */
+
+#define DFV_BC_TRANSMISSIVE 0
+#define DFV_BC_PERIODIC 1
+
+#define DFV_MAT_IDEAL 0       /* p = (gamma-1) rho e                  (Sec. 2.1.3) */
+#define DFV_MAT_STIFFENED 1   /* p = (gamma-1) rho e - gamma p_inf (Mie-Grueneisen form) */
+#define DFV_MAT_ROMENSKII 2   /* eq:Romenskii with shear energy G J^2/rho (Sec. 2.1.3) */
+
+#define DFV_FIELDS_CONSERVED 0
+#define DFV_FIELDS_PRIMITIVE 1
+
+typedef struct {
+    double gamma;    /* ideal / stiffened: adiabatic index */
+    double pinf;     /* stiffened: p_inf (Pa) */
+    double rho0;     /* Romenskii: reference density */
+    double K0;       /* Romenskii: bulk-like modulus */
+    double G0;       /* Romenskii: shear modulus at rho0 */
+    double alpha;    /* Romenskii: cold-curve exponent */
+    double beta;     /* Romenskii: shear-modulus exponent */
+    double Gamma0;   /* Romenskii: Grueneisen coefficient */
+    double sigma_y;  /* yield stress for perfect plasticity (0: fluid) */
+} dfv_material_params;
+
+typedef struct {
+    int nmat;            /* number of materials, 1 or 2 */
+    int solid;           /* 1: carry the stretch tensor V (elastoplastic) */
+    int use_thinc;       /* 1: MUSCL-BVD-THINC on phi and r (Sec. 3.1); 0: MUSCL only */
+    double thinc_beta;   /* THINC steepness (1.6) */
+} dfv_options;
+
+typedef struct dfv_grid dfv_grid;
+
+/* Bytes of device workspace a grid needs (all precisions and options given
+ * here).  dim in 1..3; n[d] >= 1 for d < dim. */
+dfv_status dfv_workspace_bytes(int dim, const int n[3], int nmat, int solid, int precision, size_t *bytes);
+
+/* Create a grid on [lo, hi] with n cells per direction (Sec. 3: uniform
+ * Cartesian mesh; the paper's AMR hierarchy is not built).  workspace: device
+ * pointer, 256-byte aligned, >= dfv_workspace_bytes() bytes, owned by the
+ * caller.  stream: a cudaStream_t or NULL.  On success *out owns host memory
+ * only, released by dfv_destroy. */
+dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const double hi[3], const int bc[6],
+                           int precision, const dfv_options *opt, void *workspace, size_t workspace_bytes,
+                           void *stream, dfv_grid **out);
+
+/* Add material number *id_out (0, 1, ... in call order; exactly opt->nmat
+ * materials before dfv_set_fields).  Closures: Sec. 2.1.2-2.1.3. */
+dfv_status dfv_add_material(dfv_grid *g, int kind, const dfv_material_params *p, int *id_out);
+
+/* Initial fields from FP64 primitive planes (layout above).  on_device = 1:
+ * `prim` is a device pointer; 0: host pointer.  Conversion to conserved
+ * variables uses the mixture rules of Sec. 2.2. */
+dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device);
+
+/* Copy the current fields out as FP64 planes: which = DFV_FIELDS_CONSERVED
+ * or DFV_FIELDS_PRIMITIVE.  on_device selects a device or host destination. */
+dfv_status dfv_get_fields(dfv_grid *g, double *out, int which, int on_device);
+
+/* Rigid-body velocity v_r (Sec. 2.3, eq:revo), position and mass.  dynamic =
+ * 1: after every step v += dt F/m, x += dt v with F the pressure force sum
+ * over grad r (not in the paper, which imposes v_r).  Only dim components of
+ * v are used. */
+dfv_status dfv_set_body(dfv_grid *g, const double v[3], const double x[3], double mass, int dynamic);
+
+/* Force of the last step (evaluated after seeding), velocity and position. */
+dfv_status dfv_get_body(dfv_grid *g, double force[3], double v[3], double x[3]);
+
+/* dt = cfl / max_cells sum_d (|u_d| + c)/dx_d (also covering the body speed)
+ * on the current fields (Sec. 3: a fraction of the largest stable step).
+ * Synchronises the stream; returns DFV_ERR_NONPHYSICAL if a kernel flagged
+ * a non-physical state. */
+dfv_status dfv_compute_dt(dfv_grid *g, double cfl, double *dt_out);
+
+/* One time step of size dt: rigid seeding (Sec. 3.2), three SSP-RK3 stages of
+ * the spatial operator of eq:spat_op (Sec. 3.1) with the thermodynamic
+ * variables of rigid cells (r > 0.5) carried unchanged, plastic relaxation
+ * (solids), body update (dynamic body).  Asynchronous on the stream. */
+dfv_status dfv_step(dfv_grid *g, double dt);
+
+/* `steps` steps with dt computed on the device each step from `cfl`
+ * (clipped to land on t_end when t_end > 0), all launches on the stream with
+ * no host synchronisation; the sequence of one step is captured once into a
+ * CUDA graph and replayed.  *t_out (optional) receives the simulated time
+ * (synchronises). */
+dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_out);
+
+/* Synchronise the stream (waiting at most timeout_ms, <= 0: no limit) and
+ * report DFV_ERR_NONPHYSICAL / DFV_ERR_TIMEOUT. */
+dfv_status dfv_check(dfv_grid *g, int timeout_ms);
+
+/* Number of kernel launches issued by the library on this grid so far. */
+dfv_status dfv_launch_count(const dfv_grid *g, long long *count);
+
+dfv_status dfv_destroy(dfv_grid *g);
+
+const char *dfv_last_error(const dfv_grid *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFVRB_H */

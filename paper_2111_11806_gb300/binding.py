@@ -1,0 +1,253 @@
+"""ctypes binding of libdfvrb.so (include/dfvrb.h): the same entry points,
+argument marshalling only.  PyTorch supplies the device workspace and the
+CUDA stream; every step of the solver runs in the library's kernels.  There is
+no CPU fallback: without the built library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdfvrb.so")
+
+DFV_OK = 0
+DFV_ERR = {-1: "DFV_ERR_ARG", -2: "DFV_ERR_CUDA", -3: "DFV_ERR_NONPHYSICAL", -4: "DFV_ERR_TIMEOUT",
+           -5: "DFV_ERR_WORKSPACE", -6: "DFV_ERR_UNSUPPORTED"}
+DFV_FP64, DFV_FP32 = 0, 1
+DFV_BC_TRANSMISSIVE, DFV_BC_PERIODIC = 0, 1
+DFV_FIELDS_CONSERVED, DFV_FIELDS_PRIMITIVE = 0, 1
+MAT_KIND = {"ideal": 0, "stiffened": 1, "romenskii": 2}
+
+EXPORTS = ("dfv_workspace_bytes", "dfv_create_grid", "dfv_add_material", "dfv_set_fields", "dfv_get_fields",
+           "dfv_set_body", "dfv_get_body", "dfv_compute_dt", "dfv_step", "dfv_run", "dfv_check",
+           "dfv_launch_count", "dfv_destroy", "dfv_last_error")
+
+
+class dfv_material_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("gamma", "pinf", "rho0", "K0", "G0", "alpha", "beta", "Gamma0", "sigma_y")]
+
+
+class dfv_options(ctypes.Structure):
+    _fields_ = [("nmat", ctypes.c_int), ("solid", ctypes.c_int), ("use_thinc", ctypes.c_int),
+                ("thinc_beta", ctypes.c_double)]
+
+
+class DfvError(RuntimeError):
+    pass
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+def load(path: str = LIB_PATH):
+    """Load libdfvrb.so and declare the prototypes of include/dfvrb.h."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise DfvError("libdfvrb.so is not built (%s); run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    L.dfv_workspace_bytes.argtypes = [ctypes.c_int, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    L.dfv_create_grid.argtypes = [ctypes.c_int, _ip, _dp, _dp, _ip, ctypes.c_int, ctypes.POINTER(dfv_options),
+                                  _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]
+    L.dfv_add_material.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(dfv_material_params), _ip]
+    L.dfv_set_fields.argtypes = [_vp, _vp, ctypes.c_int]
+    L.dfv_get_fields.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int]
+    L.dfv_set_body.argtypes = [_vp, _dp, _dp, ctypes.c_double, ctypes.c_int]
+    L.dfv_get_body.argtypes = [_vp, _dp, _dp, _dp]
+    L.dfv_compute_dt.argtypes = [_vp, ctypes.c_double, _dp]
+    L.dfv_step.argtypes = [_vp, ctypes.c_double]
+    L.dfv_run.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+    L.dfv_check.argtypes = [_vp, ctypes.c_int]
+    L.dfv_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.dfv_destroy.argtypes = [_vp]
+    L.dfv_last_error.argtypes = [_vp]
+    L.dfv_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "dfv_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status, handle=None, what=""):
+    if status != DFV_OK:
+        msg = ""
+        if handle:
+            m = load().dfv_last_error(handle)
+            msg = m.decode() if m else ""
+        raise DfvError("%s: %s %s" % (what, DFV_ERR.get(status, status), msg))
+
+
+def _d3(x):
+    a = np.zeros(3)
+    a[: len(x)] = x
+    return a
+
+
+def material_struct(m: dict) -> dfv_material_params:
+    p = dfv_material_params()
+    p.gamma = m.get("gamma", 0.0)
+    p.pinf = m.get("pinf", 0.0)
+    p.rho0 = m.get("rho0", 0.0)
+    p.K0 = m.get("K0", 0.0)
+    p.G0 = m.get("G0", 0.0)
+    p.alpha = m.get("alpha", 0.0)
+    p.beta = m.get("beta", 0.0)
+    p.Gamma0 = m.get("Gamma0", 0.0)
+    p.sigma_y = m.get("sigY", 0.0)
+    return p
+
+
+def workspace_bytes(dim, n, nmat, solid, precision) -> int:
+    n3 = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    out = ctypes.c_size_t()
+    _check(load().dfv_workspace_bytes(dim, n3, nmat, int(bool(solid)), precision, ctypes.byref(out)),
+           what="dfv_workspace_bytes")
+    return out.value
+
+
+class Grid:
+    """One grid of the CUDA library.  Device memory: one torch uint8 tensor
+    (the workspace), owned by this object.  Stream: torch's current stream on
+    `device` unless one is given."""
+
+    def __init__(self, dim, n, lo, hi, materials, solid=False, precision=DFV_FP64, periodic=None,
+                 use_thinc=True, thinc_beta=1.6, device="cuda:0", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise DfvError("a CUDA device is required (no CPU fallback)")
+        L = load()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.dim = dim
+        self.n = tuple(int(x) for x in n)
+        self.nmat = len(materials)
+        self.solid = bool(solid)
+        self.precision = precision
+        self.ncell = int(np.prod(self.n))
+        nbytes = workspace_bytes(dim, self.n, self.nmat, solid, precision)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        per = list(periodic or [0] * dim)
+        bc = (ctypes.c_int * 6)(*sum(([DFV_BC_PERIODIC] * 2 if p else [DFV_BC_TRANSMISSIVE] * 2 for p in per), []),
+                                *([0] * (6 - 2 * dim)))
+        n3 = (ctypes.c_int * 3)(*(list(self.n) + [1] * (3 - dim)))
+        lo3 = _d3(lo)
+        hi3 = _d3(hi)
+        opt = dfv_options(self.nmat, int(self.solid), int(bool(use_thinc)), float(thinc_beta))
+        h = _vp()
+        with torch.cuda.device(self.device):
+            st = L.dfv_create_grid(dim, n3, lo3.ctypes.data_as(_dp), hi3.ctypes.data_as(_dp), bc, precision,
+                                   ctypes.byref(opt), _vp(aligned), nbytes, _vp(self.stream.cuda_stream),
+                                   ctypes.byref(h))
+        _check(st, None, "dfv_create_grid")
+        self._h = h
+        for m in materials:
+            p = material_struct(m)
+            _check(L.dfv_add_material(self._h, MAT_KIND[m["kind"]], ctypes.byref(p), None), self._h,
+                   "dfv_add_material")
+        self.nvar = (self.nmat - 1) + self.nmat + dim + 1 + ((3 if dim == 1 else 5 if dim == 2 else 9)
+                                                            if solid else 0) + 1
+
+    @classmethod
+    def from_workload(cls, wl, precision=DFV_FP64, **kw):
+        g = cls(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, solid=wl.solid, precision=precision,
+                periodic=wl.periodic, **kw)
+        g.set_fields(wl.prim)
+        g.set_body(wl.body_v, wl.body_x, wl.body_mass, wl.body_dynamic)
+        return g
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                self.stream.synchronize()
+            except Exception:
+                pass
+            load().dfv_destroy(h)
+            self._h = None
+
+    def _ctx(self):
+        return self.torch.cuda.device(self.device)
+
+    # ---- fields
+    def set_fields(self, prim):
+        """prim: numpy (host) or torch cuda float64 array of shape (nvar, ncell)."""
+        if hasattr(prim, "is_cuda") and prim.is_cuda:
+            t = prim.contiguous()
+            assert t.dtype == self.torch.float64 and t.numel() == self.nvar * self.ncell
+            with self._ctx():
+                _check(load().dfv_set_fields(self._h, _vp(t.data_ptr()), 1), self._h, "dfv_set_fields")
+            self._keep = t
+            return
+        a = np.ascontiguousarray(np.asarray(prim, dtype=np.float64)).reshape(self.nvar, self.ncell)
+        with self._ctx():
+            _check(load().dfv_set_fields(self._h, _vp(a.ctypes.data), 0), self._h, "dfv_set_fields")
+
+    def get_fields(self, which=DFV_FIELDS_CONSERVED, out=None):
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            with self._ctx():
+                _check(load().dfv_get_fields(self._h, _vp(out.data_ptr()), which, 1), self._h, "dfv_get_fields")
+            return out
+        a = np.zeros((self.nvar, self.ncell)) if out is None else out
+        with self._ctx():
+            _check(load().dfv_get_fields(self._h, _vp(a.ctypes.data), which, 0), self._h, "dfv_get_fields")
+        return a
+
+    def cons(self):
+        return self.get_fields(DFV_FIELDS_CONSERVED)
+
+    def prim(self):
+        return self.get_fields(DFV_FIELDS_PRIMITIVE)
+
+    # ---- body
+    def set_body(self, v=(0, 0, 0), x=(0, 0, 0), mass=0.0, dynamic=False):
+        with self._ctx():
+            _check(load().dfv_set_body(self._h, _d3(v).ctypes.data_as(_dp), _d3(x).ctypes.data_as(_dp),
+                                       float(mass), int(bool(dynamic))), self._h, "dfv_set_body")
+
+    def body(self):
+        f, v, x = np.zeros(3), np.zeros(3), np.zeros(3)
+        with self._ctx():
+            _check(load().dfv_get_body(self._h, f.ctypes.data_as(_dp), v.ctypes.data_as(_dp),
+                                       x.ctypes.data_as(_dp)), self._h, "dfv_get_body")
+        return f, v, x
+
+    # ---- time stepping
+    def compute_dt(self, cfl):
+        dt = ctypes.c_double()
+        with self._ctx():
+            _check(load().dfv_compute_dt(self._h, float(cfl), ctypes.byref(dt)), self._h, "dfv_compute_dt")
+        return dt.value
+
+    def step(self, dt):
+        with self._ctx():
+            _check(load().dfv_step(self._h, float(dt)), self._h, "dfv_step")
+
+    def run(self, steps, cfl, t_end=0.0, sync=True):
+        t = ctypes.c_double()
+        with self._ctx():
+            _check(load().dfv_run(self._h, int(steps), float(cfl), float(t_end or 0.0),
+                                  ctypes.byref(t) if sync else None), self._h, "dfv_run")
+        return t.value if sync else None
+
+    def check(self, timeout_ms=0):
+        with self._ctx():
+            _check(load().dfv_check(self._h, int(timeout_ms)), self._h, "dfv_check")
+
+    def launch_count(self):
+        c = ctypes.c_longlong()
+        _check(load().dfv_launch_count(self._h, ctypes.byref(c)), self._h, "dfv_launch_count")
+        return c.value

@@ -1,0 +1,516 @@
+// dfv_api.cu -- the C ABI declared in include/dfvrb.h.
+//
+// Host-side orchestration only: argument checks, placement of all device
+// buffers inside the caller's workspace, and the launch sequence of a step
+// (seed, three RK stages, finalize), optionally captured once into a CUDA
+// graph and replayed.  No device memory is allocated here.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+
+#include "../../include/dfvrb.h"
+#include "dfv_kernels.cuh"
+#include "dfv_ops.h"
+
+using dfv::Ctl;
+using dfv::GridP;
+using dfv::Ops;
+
+struct dfv_grid {
+    int dim = 0, precision = 0, nmat_opt = 1, nmat = 0, solid = 0;
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    GridP g;
+    const Ops *ops = nullptr;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    Ctl *ctl = nullptr;
+    double *partials = nullptr;
+    void *U = nullptr, *U1 = nullptr, *U3 = nullptr;
+    double *staging = nullptr;
+    long long nb_stage = 0, nb_cfl = 0;
+    bool fields_set = false, smax_valid = false;
+    bool dynamic = false;
+    std::string err;
+    long long launches = 0;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_ready = false;
+};
+
+namespace {
+
+const char *k_no_grid = "dfv: null grid";
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+long long cells_of(int dim, const int n[3])
+{
+    long long c = 1;
+    for (int d = 0; d < dim; d++) c *= n[d];
+    return c;
+}
+
+int nvar_of(int dim, int nmat, int solid)
+{
+    const int nv = solid ? (dim == 1 ? 3 : (dim == 2 ? 5 : 9)) : 0;
+    return (nmat - 1) + nmat + dim + 1 + nv + 1;
+}
+
+struct Layout {
+    size_t off_ctl, off_part, off_U, off_U1, off_U3, off_stage, total;
+    long long pitch, nb_stage, nb_cfl;
+};
+
+long long stage_blocks(int dim, const int n[3])
+{
+    // tile shapes of dfv_kernels.cuh
+    const int tx = dim == 1 ? 256 : 32, ty = dim == 1 ? 1 : (dim == 2 ? 8 : 4), tz = dim == 3 ? 2 : 1;
+    const long long bx = (n[0] + tx - 1) / tx;
+    const long long by = dim >= 2 ? (n[1] + ty - 1) / ty : 1;
+    const long long bz = dim >= 3 ? (n[2] + tz - 1) / tz : 1;
+    return bx * by * bz;
+}
+
+Layout plan(int dim, const int n[3], int nmat, int solid, int precision)
+{
+    Layout L;
+    const long long nc = cells_of(dim, n);
+    const int nvar = nvar_of(dim, nmat, solid);
+    const int w = precision == DFV_FP32 ? 4 : 8;
+    L.pitch = (nc + 63) / 64 * 64;
+    L.nb_stage = stage_blocks(dim, n);
+    L.nb_cfl = dfv::gs_blocks(nc);
+    const long long nparts = L.nb_stage > L.nb_cfl ? L.nb_stage : L.nb_cfl;
+    size_t off = 0;
+    L.off_ctl = off;
+    off += align256(sizeof(Ctl));
+    L.off_part = off;
+    off += align256(sizeof(double) * 4 * (size_t)nparts);
+    const size_t state = align256((size_t)w * nvar * (size_t)L.pitch);
+    L.off_U = off;
+    off += state;
+    L.off_U1 = off;
+    off += state;
+    L.off_U3 = off;
+    off += state;
+    L.off_stage = off;
+    off += align256(sizeof(double) * nvar * (size_t)nc);
+    L.total = off;
+    return L;
+}
+
+dfv_status fail(dfv_grid *g, dfv_status s, const std::string &msg)
+{
+    if (g) g->err = msg;
+    return s;
+}
+
+dfv_status cuda_fail(dfv_grid *g, cudaError_t e, const char *where)
+{
+    return fail(g, DFV_ERR_CUDA, std::string("dfv: ") + where + ": " + cudaGetErrorString(e));
+}
+
+#define DFV_CU(g, call, where)                              \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(g, e_, where); \
+    } while (0)
+
+__global__ void k_init_ctl(Ctl *c)
+{
+    memset(c, 0, sizeof(Ctl));
+}
+
+__global__ void k_set_body(Ctl *c, double v0, double v1, double v2, double x0, double x1, double x2, double mass,
+                           int dynamic)
+{
+    c->v[0] = v0;
+    c->v[1] = v1;
+    c->v[2] = v2;
+    c->x[0] = x0;
+    c->x[1] = x1;
+    c->x[2] = x2;
+    c->mass = mass;
+    c->dynamic = dynamic;
+}
+
+__global__ void k_set_run(Ctl *c, double cfl, double t_end)
+{
+    c->cfl = cfl;
+    c->t_end = t_end;
+}
+
+dfv_status sync_stream(dfv_grid *g, int timeout_ms)
+{
+    if (timeout_ms <= 0) {
+        DFV_CU(g, cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
+        return DFV_OK;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(g->stream);
+        if (e == cudaSuccess) return DFV_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(g, e, "cudaStreamQuery");
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+        if (ms.count() > timeout_ms) return fail(g, DFV_ERR_TIMEOUT, "dfv: wait for the stream timed out");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+dfv_status read_ctl(dfv_grid *g, Ctl *h)
+{
+    DFV_CU(g, cudaMemcpyAsync(h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->stream), "read ctl");
+    DFV_CU(g, cudaStreamSynchronize(g->stream), "read ctl sync");
+    if (h->err) return fail(g, DFV_ERR_NONPHYSICAL, "dfv: non-physical state (rho <= 0, c^2 <= 0 or NaN)");
+    return DFV_OK;
+}
+
+// One-block finalize: nb_max partial blocks hold the CFL maxima.
+dfv_status finalize(dfv_grid *g, int mode, long long nb_max)
+{
+    dfv::k_finalize<<<1, 1024, 0, g->stream>>>(g->ctl, g->partials, nb_max, g->nb_stage, mode, g->dim, g->g.dx[0],
+                                                g->g.dx[1], g->g.dx[2]);
+    g->launches++;
+    DFV_CU(g, cudaGetLastError(), "k_finalize");
+    return DFV_OK;
+}
+
+// CFL reduction over the stored state into ctl->smax.
+dfv_status reduce_cfl(dfv_grid *g)
+{
+    DFV_CU(g, g->ops->cfl(g->g, g->U, g->partials, (int)g->nb_cfl, g->stream), "k_cfl");
+    g->launches++;
+    dfv_status s = finalize(g, 1, g->nb_cfl);
+    if (s == DFV_OK) g->smax_valid = true;
+    return s;
+}
+
+// The launches of one step: seeding (Sec. 3.2), SSP-RK3 (Sec. 3.1), finalize.
+// mode_extra = 8 asks the finalize kernel for the next dt (device-driven runs).
+dfv_status launch_step(dfv_grid *g, int mode_extra)
+{
+    const int want_force = g->dynamic ? 1 : 0;
+    DFV_CU(g, g->ops->seed(g->g, g->U, g->ctl, g->stream), "k_seed");
+    DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, g->stream), "k_stage<1>");
+    DFV_CU(g, g->ops->stage(2, g->g, g->U1, g->U, g->U3, g->ctl, g->partials, 0, g->stream), "k_stage<2>");
+    DFV_CU(g, g->ops->stage(3, g->g, g->U3, g->U, g->U, g->ctl, g->partials, 0, g->stream), "k_stage<3>");
+    g->launches += 4;
+    return finalize(g, 1 | (want_force ? 2 : 0) | 4 | mode_extra, g->nb_stage);
+}
+
+const Ops *pick_ops(int precision, int dim, int nmat, int solid)
+{
+    return dfv::ops_for(precision == DFV_FP32 ? 1 : 0, dim, nmat, solid);
+}
+
+}  // namespace
+
+extern "C" {
+
+dfv_status dfv_workspace_bytes(int dim, const int n[3], int nmat, int solid, int precision, size_t *bytes)
+{
+    if (!n || !bytes || dim < 1 || dim > 3 || nmat < 1 || nmat > 2) return DFV_ERR_ARG;
+    if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
+    for (int d = 0; d < dim; d++)
+        if (n[d] < 1) return DFV_ERR_ARG;
+    int n3[3] = {n[0], dim >= 2 ? n[1] : 1, dim >= 3 ? n[2] : 1};
+    *bytes = plan(dim, n3, nmat, solid ? 1 : 0, precision).total;
+    return DFV_OK;
+}
+
+dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const double hi[3], const int bc[6],
+                           int precision, const dfv_options *opt, void *workspace, size_t workspace_bytes,
+                           void *stream, dfv_grid **out)
+{
+    if (!out || !n || !lo || !hi || !opt) return DFV_ERR_ARG;
+    *out = nullptr;
+    if (dim < 1 || dim > 3 || opt->nmat < 1 || opt->nmat > 2) return DFV_ERR_ARG;
+    if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
+    int n3[3] = {1, 1, 1};
+    for (int d = 0; d < dim; d++) {
+        if (n[d] < 1 || !(hi[d] > lo[d])) return DFV_ERR_ARG;
+        n3[d] = n[d];
+    }
+    int bcs[6] = {0, 0, 0, 0, 0, 0};
+    if (bc)
+        for (int k = 0; k < 2 * dim; k++) bcs[k] = bc[k];
+    for (int d = 0; d < dim; d++) {
+        if ((bcs[2 * d] == DFV_BC_PERIODIC) != (bcs[2 * d + 1] == DFV_BC_PERIODIC)) return DFV_ERR_ARG;
+        for (int s = 0; s < 2; s++)
+            if (bcs[2 * d + s] != DFV_BC_PERIODIC && bcs[2 * d + s] != DFV_BC_TRANSMISSIVE) return DFV_ERR_ARG;
+    }
+    const Ops *ops = pick_ops(precision, dim, opt->nmat, opt->solid ? 1 : 0);
+    if (!ops) return DFV_ERR_UNSUPPORTED;
+    const Layout L = plan(dim, n3, opt->nmat, opt->solid ? 1 : 0, precision);
+    if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) return DFV_ERR_WORKSPACE;
+
+    dfv_grid *g = new dfv_grid();
+    g->dim = dim;
+    g->precision = precision;
+    g->nmat_opt = opt->nmat;
+    g->solid = opt->solid ? 1 : 0;
+    for (int k = 0; k < 6; k++) g->bc[k] = bcs[k];
+    g->ops = ops;
+    g->stream = (cudaStream_t)stream;
+    g->ws = (char *)workspace;
+    g->ws_bytes = workspace_bytes;
+    g->ctl = (Ctl *)(g->ws + L.off_ctl);
+    g->partials = (double *)(g->ws + L.off_part);
+    g->U = g->ws + L.off_U;
+    g->U1 = g->ws + L.off_U1;
+    g->U3 = g->ws + L.off_U3;
+    g->staging = (double *)(g->ws + L.off_stage);
+    g->nb_stage = L.nb_stage;
+    g->nb_cfl = L.nb_cfl;
+
+    GridP &p = g->g;
+    memset(&p, 0, sizeof(p));
+    p.dim = dim;
+    p.ncell = 1;
+    p.dxmin = 1e300;
+    p.dV = 1.0;
+    for (int d = 0; d < 3; d++) {
+        p.n[d] = n3[d];
+        p.periodic[d] = (d < dim) ? (bcs[2 * d] == DFV_BC_PERIODIC) : 0;
+        p.lo[d] = d < dim ? lo[d] : 0.0;
+        p.dx[d] = d < dim ? (hi[d] - lo[d]) / n3[d] : 1.0;
+        p.inv_dx[d] = 1.0 / p.dx[d];
+        p.ncell *= n3[d];
+        if (d < dim) {
+            p.dxmin = std::fmin(p.dxmin, p.dx[d]);
+            p.dV *= p.dx[d];
+        }
+    }
+    p.pitch = L.pitch;
+    p.use_thinc = opt->use_thinc ? 1 : 0;
+    p.beta = opt->thinc_beta > 0.0 ? opt->thinc_beta : 1.6;
+    p.cosh_b = std::cosh(p.beta);
+    p.sinh_b = std::sinh(p.beta);
+    p.tanh_b = std::tanh(p.beta);
+    p.phi_guard = 1e-14;
+
+    cudaError_t e = ops->prepare();
+    if (e != cudaSuccess) {
+        delete g;
+        return DFV_ERR_CUDA;
+    }
+    k_init_ctl<<<1, 1, 0, g->stream>>>(g->ctl);
+    g->launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        delete g;
+        return DFV_ERR_CUDA;
+    }
+    *out = g;
+    return DFV_OK;
+}
+
+dfv_status dfv_add_material(dfv_grid *g, int kind, const dfv_material_params *m, int *id_out)
+{
+    if (!g) return DFV_ERR_ARG;
+    if (!m) return fail(g, DFV_ERR_ARG, "dfv_add_material: null parameters");
+    if (g->nmat >= g->nmat_opt) return fail(g, DFV_ERR_ARG, "dfv_add_material: all materials already added");
+    if (kind < DFV_MAT_IDEAL || kind > DFV_MAT_ROMENSKII) return fail(g, DFV_ERR_ARG, "dfv_add_material: bad kind");
+    if (kind != DFV_MAT_ROMENSKII && !(m->gamma > 1.0)) return fail(g, DFV_ERR_ARG, "dfv_add_material: gamma <= 1");
+    if (kind == DFV_MAT_ROMENSKII && !(m->rho0 > 0.0 && m->Gamma0 > 0.0 && m->alpha != 0.0))
+        return fail(g, DFV_ERR_ARG, "dfv_add_material: bad Romenskii parameters");
+    dfv::MatP &p = g->g.mat[g->nmat];
+    p.kind = kind;
+    p.gamma = m->gamma;
+    p.pinf = m->pinf;
+    p.rho0 = m->rho0;
+    p.K0 = m->K0;
+    p.G0 = m->G0;
+    p.alpha = m->alpha;
+    p.beta = m->beta;
+    p.Gamma0 = m->Gamma0;
+    p.sigY = m->sigma_y;
+    if (id_out) *id_out = g->nmat;
+    g->nmat++;
+    g->graph_ready = false;
+    return DFV_OK;
+}
+
+dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device)
+{
+    if (!g) return DFV_ERR_ARG;
+    if (!prim) return fail(g, DFV_ERR_ARG, "dfv_set_fields: null field pointer");
+    if (g->nmat != g->nmat_opt) return fail(g, DFV_ERR_ARG, "dfv_set_fields: materials missing");
+    const size_t bytes = sizeof(double) * g->ops->nvar * (size_t)g->g.ncell;
+    DFV_CU(g, cudaMemcpyAsync(g->staging, prim, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              g->stream),
+           "dfv_set_fields copy");
+    DFV_CU(g, g->ops->prim_to_cons(g->g, g->staging, g->g.ncell, g->U, g->stream), "k_prim_to_cons");
+    g->launches++;
+    if (!on_device) DFV_CU(g, cudaStreamSynchronize(g->stream), "dfv_set_fields sync");
+    g->fields_set = true;
+    g->smax_valid = false;
+    return DFV_OK;
+}
+
+dfv_status dfv_get_fields(dfv_grid *g, double *outp, int which, int on_device)
+{
+    if (!g) return DFV_ERR_ARG;
+    if (!outp) return fail(g, DFV_ERR_ARG, "dfv_get_fields: null output");
+    if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_get_fields: fields not set");
+    if (which == DFV_FIELDS_PRIMITIVE) {
+        DFV_CU(g, g->ops->cons_to_prim(g->g, g->U, g->staging, g->g.ncell, g->stream), "k_cons_to_prim");
+    } else if (which == DFV_FIELDS_CONSERVED) {
+        DFV_CU(g, g->ops->cons_to_f64(g->g, g->U, g->staging, g->g.ncell, g->ops->nvar, g->stream), "k_cons_to_f64");
+    } else {
+        return fail(g, DFV_ERR_ARG, "dfv_get_fields: bad `which`");
+    }
+    g->launches++;
+    const size_t bytes = sizeof(double) * g->ops->nvar * (size_t)g->g.ncell;
+    DFV_CU(g, cudaMemcpyAsync(outp, g->staging, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              g->stream),
+           "dfv_get_fields copy");
+    if (!on_device) DFV_CU(g, cudaStreamSynchronize(g->stream), "dfv_get_fields sync");
+    return DFV_OK;
+}
+
+dfv_status dfv_set_body(dfv_grid *g, const double v[3], const double x[3], double mass, int dynamic)
+{
+    if (!g) return DFV_ERR_ARG;
+    double vv[3] = {0, 0, 0}, xx[3] = {0, 0, 0};
+    for (int d = 0; d < 3; d++) {
+        vv[d] = (v && d < g->dim) ? v[d] : 0.0;
+        xx[d] = x ? x[d] : 0.0;
+    }
+    if (dynamic && !(mass > 0.0)) return fail(g, DFV_ERR_ARG, "dfv_set_body: a dynamic body needs mass > 0");
+    k_set_body<<<1, 1, 0, g->stream>>>(g->ctl, vv[0], vv[1], vv[2], xx[0], xx[1], xx[2], mass, dynamic ? 1 : 0);
+    g->launches++;
+    DFV_CU(g, cudaGetLastError(), "k_set_body");
+    g->dynamic = dynamic != 0;
+    g->smax_valid = false;   // the body speed enters the CFL bound
+    g->graph_ready = false;
+    return DFV_OK;
+}
+
+dfv_status dfv_get_body(dfv_grid *g, double force[3], double v[3], double x[3])
+{
+    if (!g) return DFV_ERR_ARG;
+    Ctl h;
+    dfv_status s = read_ctl(g, &h);
+    for (int d = 0; d < 3; d++) {
+        if (force) force[d] = h.force[d];
+        if (v) v[d] = h.v[d];
+        if (x) x[d] = h.x[d];
+    }
+    return s;
+}
+
+dfv_status dfv_compute_dt(dfv_grid *g, double cfl, double *dt_out)
+{
+    if (!g) return DFV_ERR_ARG;
+    if (!dt_out || !(cfl > 0.0)) return fail(g, DFV_ERR_ARG, "dfv_compute_dt: bad arguments");
+    if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_compute_dt: fields not set");
+    if (!g->smax_valid) {
+        dfv_status s = reduce_cfl(g);
+        if (s != DFV_OK) return s;
+    }
+    Ctl h;
+    dfv_status s = read_ctl(g, &h);
+    *dt_out = cfl / h.smax;
+    return s;
+}
+
+dfv_status dfv_step(dfv_grid *g, double dt)
+{
+    if (!g) return DFV_ERR_ARG;
+    if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_step: fields not set");
+    if (!(dt >= 0.0)) return fail(g, DFV_ERR_ARG, "dfv_step: dt must be >= 0");
+    dfv::k_set_dt<<<1, 1, 0, g->stream>>>(g->ctl, dt);
+    g->launches++;
+    DFV_CU(g, cudaGetLastError(), "k_set_dt");
+    dfv_status s = launch_step(g, 0);
+    if (s == DFV_OK) g->smax_valid = true;
+    return s;
+}
+
+dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_out)
+{
+    if (!g) return DFV_ERR_ARG;
+    if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_run: fields not set");
+    if (steps < 0 || !(cfl > 0.0)) return fail(g, DFV_ERR_ARG, "dfv_run: bad arguments");
+    k_set_run<<<1, 1, 0, g->stream>>>(g->ctl, cfl, t_end > 0.0 ? t_end : 0.0);
+    g->launches++;
+    DFV_CU(g, cudaGetLastError(), "k_set_run");
+    if (!g->smax_valid) {
+        dfv_status s = reduce_cfl(g);
+        if (s != DFV_OK) return s;
+    }
+    dfv_status s = finalize(g, 8, 0);   // dt from the current smax
+    if (s != DFV_OK) return s;
+    const bool use_graph = g->stream != nullptr && steps > 1;
+    if (use_graph && !g->graph_ready) {
+        if (g->graph) {
+            cudaGraphExecDestroy(g->graph);
+            g->graph = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        DFV_CU(g, cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const long long before = g->launches;
+        dfv_status cs = launch_step(g, 8);
+        cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+        g->launches = before;   // capture launches nothing
+        if (cs != DFV_OK) return cs;
+        if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
+        e = cudaGraphInstantiate(&g->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
+        g->graph_ready = true;
+    }
+    for (int k = 0; k < steps; k++) {
+        if (use_graph) {
+            DFV_CU(g, cudaGraphLaunch(g->graph, g->stream), "graph launch");
+            g->launches += 5;
+        } else {
+            s = launch_step(g, 8);
+            if (s != DFV_OK) return s;
+        }
+    }
+    g->smax_valid = true;
+    if (t_out) {
+        Ctl h;
+        s = read_ctl(g, &h);
+        *t_out = h.t;
+        return s;
+    }
+    return DFV_OK;
+}
+
+dfv_status dfv_check(dfv_grid *g, int timeout_ms)
+{
+    if (!g) return DFV_ERR_ARG;
+    dfv_status s = sync_stream(g, timeout_ms);
+    if (s != DFV_OK) return s;
+    Ctl h;
+    return read_ctl(g, &h);
+}
+
+dfv_status dfv_launch_count(const dfv_grid *g, long long *count)
+{
+    if (!g || !count) return DFV_ERR_ARG;
+    *count = g->launches;
+    return DFV_OK;
+}
+
+dfv_status dfv_destroy(dfv_grid *g)
+{
+    if (!g) return DFV_ERR_ARG;
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    delete g;
+    return DFV_OK;
+}
+
+const char *dfv_last_error(const dfv_grid *g)
+{
+    if (!g) return k_no_grid;
+    return g->err.c_str();
+}
+
+}  // extern "C"

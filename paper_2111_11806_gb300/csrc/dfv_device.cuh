@@ -1,0 +1,602 @@
+// dfv_device.cuh -- device-side physics of the diffuse rigid-body
+// finite-volume update (arXiv:2111.11806), written for sm_103a.
+//
+// Everything here is a __device__ function templated on the compute type T
+// (double for the plain FP64 form, float for the FP32 bulk form) and on the
+// system shape (dimension, number of materials, solid or fluid), so that every
+// index into the per-cell state is a compile-time constant and lives in
+// registers.  The stretch-tensor logarithm and the plastic return are always
+// evaluated in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dfv {
+
+// ------------------------------------------------------------------ params
+
+struct MatP {
+    int kind;                 // 0 ideal, 1 stiffened, 2 Romenskii
+    double gamma, pinf;
+    double rho0, K0, G0, alpha, beta, Gamma0;
+    double sigY;
+};
+
+struct GridP {
+    int dim;
+    int n[3];
+    int periodic[3];
+    double lo[3], dx[3], inv_dx[3];
+    long long ncell, pitch;   // cells, elements between planes
+    double dV, dxmin;
+    MatP mat[2];
+    int use_thinc;
+    double beta, cosh_b, sinh_b, tanh_b;   // THINC constants
+    double phi_guard;
+};
+
+// Device-resident control block: time step, time, body state and the error
+// word.  Kernels read dt and the body velocity from here so that a whole step
+// can be replayed from a CUDA graph without host involvement.
+struct Ctl {
+    double dt, t, t_end, cfl;
+    double smax;              // max_cells sum_d (|u_d|+c)/dx_d of the last reduction
+    double force[3];
+    double v[3];
+    double x[3];
+    double mass;
+    int dynamic;
+    int auto_dt;              // 1: the finalize kernel sets the next dt from cfl
+    unsigned int err;         // bit 0: rho<=0/NaN in an update, bit 1: c^2<=0/NaN
+    int steps;
+};
+
+enum { ERR_STATE = 1u, ERR_SOUND = 2u };
+
+// ------------------------------------------------------------------ layout
+
+template <int DIM, int NMAT, bool SOLID>
+struct Lay {
+    static constexpr int NV = SOLID ? (DIM == 1 ? 3 : (DIM == 2 ? 5 : 9)) : 0;
+    static constexpr int IPHI = 0;
+    static constexpr int IAR = NMAT - 1;
+    static constexpr int IMOM = 2 * NMAT - 1;
+    static constexpr int IE = IMOM + DIM;
+    static constexpr int IV = IE + 1;
+    static constexpr int IR = IV + NV;
+    static constexpr int NVAR = IR + 1;
+    static constexpr int NB = SOLID ? DIM : 0;   // V*_{d b} entries kept per face
+    static constexpr int NF = NVAR + 1 + NB;     // per-face record: fluxes, u*_d, V*_{d.}
+};
+
+// stored stretch component c -> tensor indices (a, b)
+__host__ __device__ constexpr int v_row(int dim, int c)
+{
+    return dim == 1 ? c : (dim == 2 ? (c < 2 ? 0 : (c < 4 ? 1 : 2)) : c / 3);
+}
+__host__ __device__ constexpr int v_col(int dim, int c)
+{
+    return dim == 1 ? c : (dim == 2 ? (c == 0 ? 0 : (c == 1 ? 1 : (c == 2 ? 0 : (c == 3 ? 1 : 2)))) : c % 3);
+}
+
+// ------------------------------------------------------------------ math
+
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double m_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double m_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float m_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double m_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float m_max(float a, float b) { return fmaxf(a, b); }
+
+__device__ __forceinline__ int map_idx(int i, int n, int periodic)
+{
+    if (periodic) {
+        int m = i % n;
+        return m < 0 ? m + n : m;
+    }
+    return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
+}
+
+// ------------------------------------------------------ material closure
+
+template <class T>
+struct Ref {
+    T Gam, eref, pref, deref, dpref, G;
+};
+
+// Mie-Grueneisen reference curves p = p_ref + rho Gamma (e - e_ref) of one
+// material (Sec. 2.1.2-2.1.3): ideal gas (p_ref = e_ref = 0), stiffened gas
+// (e_ref = 0, p_ref = -gamma p_inf), Romenskii solid (eq:Romenskii, cold term
+// K0/(2 rho alpha^2)(x^alpha - 1)^2 as printed, shear energy G J^2/rho with
+// G = G0 x^(beta+1), x = rho/rho0, and p_ref = rho^2 de_ref/drho).
+template <class T>
+__device__ __forceinline__ Ref<T> mat_ref(const MatP &m, T rho, T J2)
+{
+    Ref<T> r;
+    if (m.kind == 2) {
+        const T al = (T)m.alpha, be = (T)m.beta, K0 = (T)m.K0, rho0 = (T)m.rho0;
+        const T x = rho / rho0;
+        const T xa = m_pow(x, al);
+        const T xm1 = xa - T(1);
+        const T ec = K0 / (T(2) * rho * al * al) * xm1 * xm1;
+        const T pc = -K0 / (T(2) * al * al) * xm1 * xm1 + (K0 / al) * xm1 * xa;
+        const T dpc = (K0 / rho0) * (xa / x) * (T(2) * xa - T(1) - xm1 / al);
+        const T G = (T)m.G0 * m_pow(x, be + T(1));
+        const T ps = be * G * J2;
+        r.Gam = (T)m.Gamma0;
+        r.eref = ec + G * J2 / rho;
+        r.pref = pc + ps;
+        r.deref = (pc + ps) / (rho * rho);
+        r.dpref = dpc + be * (be + T(1)) * G * J2 / rho;
+        r.G = G;
+    } else {
+        r.Gam = (T)(m.gamma - 1.0);
+        r.eref = T(0);
+        r.pref = (m.kind == 1) ? (T)(-m.gamma * m.pinf) : T(0);
+        r.deref = T(0);
+        r.dpref = T(0);
+        r.G = T(0);
+    }
+    return r;
+}
+
+// ------------------------------------------------- stretch tensor (FP64)
+
+// dev(H) = ln V with V^2 = A A^T (Sec. 2.1.2), traceless part, and
+// J^2 = |dev H|^2.  2-D: A A^T is block diagonal, so the in-plane 2x2 block is
+// diagonalised in closed form through the double angle 2 theta of its
+// eigenvectors; 1-D: diagonal.  Also returns the data needed to rebuild a
+// tensor with the same eigenvectors (plastic return).
+struct Eig2 {
+    double d[3];       // deviatoric log-stretches (in-plane 1, 2; out-of-plane)
+    double c2, s2;     // cos 2 theta, sin 2 theta of the in-plane eigenvectors
+};
+
+template <int DIM>
+__device__ __forceinline__ void stretch_log(const double A[3][3], double H[3][3], double &J2, Eig2 &e)
+{
+    double h0, h1, h2;
+    if (DIM == 1) {
+        h0 = 0.5 * log(A[0][0] * A[0][0]);
+        h1 = 0.5 * log(A[1][1] * A[1][1]);
+        h2 = 0.5 * log(A[2][2] * A[2][2]);
+        e.c2 = 1.0;
+        e.s2 = 0.0;
+    } else {
+        const double b00 = A[0][0] * A[0][0] + A[0][1] * A[0][1];
+        const double b01 = A[0][0] * A[1][0] + A[0][1] * A[1][1];
+        const double b11 = A[1][0] * A[1][0] + A[1][1] * A[1][1];
+        const double b22 = A[2][2] * A[2][2];
+        const double mid = 0.5 * (b00 + b11), half = 0.5 * (b00 - b11);
+        const double rad = sqrt(half * half + b01 * b01);
+        h0 = 0.5 * log(mid + rad);
+        h1 = 0.5 * log(mid - rad);
+        h2 = 0.5 * log(b22);
+        e.c2 = rad > 0.0 ? half / rad : 1.0;
+        e.s2 = rad > 0.0 ? b01 / rad : 0.0;
+    }
+    const double hm = (h0 + h1 + h2) * (1.0 / 3.0);
+    e.d[0] = h0 - hm;
+    e.d[1] = h1 - hm;
+    e.d[2] = h2 - hm;
+    J2 = e.d[0] * e.d[0] + e.d[1] * e.d[1] + e.d[2] * e.d[2];
+    const double av = 0.5 * (e.d[0] + e.d[1]), df = 0.5 * (e.d[0] - e.d[1]);
+    H[0][0] = av + df * e.c2;
+    H[1][1] = av - df * e.c2;
+    H[0][1] = H[1][0] = df * e.s2;
+    H[2][2] = e.d[2];
+    H[0][2] = H[2][0] = H[1][2] = H[2][1] = 0.0;
+}
+
+// ------------------------------------------------------------- thermo
+
+template <class T, int DIM, int NMAT, bool SOLID>
+struct State {
+    T phi[NMAT], ar[NMAT];
+    T rho, u[DIM], p, rhoE, c2, G, sigY;
+    T H[DIM][DIM];     // dev(H), in-plane block
+};
+
+template <class T, int DIM, int NMAT, bool SOLID>
+__device__ __forceinline__ void unpack_A(const T *w, double A[3][3])
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) A[a][b] = 0.0;
+#pragma unroll
+    for (int c = 0; c < L::NV; c++) A[v_row(DIM, c)][v_col(DIM, c)] = (double)w[L::IV + c];
+}
+
+// Full state from primitives w (mixture rules of Sec. 2.2): rho = sum phi_l rho_l,
+// rho e = sum [ (phi rho)_l e_ref,l + phi_l (p - p_ref,l)/Gamma_l ],
+// G = sum(phi_l G_l/Gamma_l)/sum(phi_l/Gamma_l) (sigma_Y with the same weights),
+// c^2 = sum(Y_l c_l^2/Gamma_l)/sum(phi_l/Gamma_l) with c_l^2 = a_l^2 + 4/3 G_l/rho_l.
+template <class T, int DIM, int NMAT, bool SOLID>
+__device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, State<T, DIM, NMAT, SOLID> &s)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    T fsum = T(0);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; l++) {
+        s.phi[l] = w[L::IPHI + l];
+        fsum += s.phi[l];
+    }
+    s.phi[NMAT - 1] = T(1) - fsum;
+    T rhol[NMAT];
+    s.rho = T(0);
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) {
+        rhol[l] = w[L::IAR + l];
+        s.ar[l] = s.phi[l] * rhol[l];
+        s.rho += s.ar[l];
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; a++) s.u[a] = w[L::IMOM + a];
+    s.p = w[L::IE];
+    T J2 = T(0);
+    if (SOLID) {
+        double A[3][3], H[3][3], j2;
+        Eig2 e;
+        unpack_A<T, DIM, NMAT, SOLID>(w, A);
+        stretch_log<DIM>(A, H, j2, e);
+        J2 = (T)j2;
+#pragma unroll
+        for (int a = 0; a < DIM; a++)
+#pragma unroll
+            for (int b = 0; b < DIM; b++) s.H[a][b] = (T)H[a][b];
+    }
+    T rhoe = T(0), den = T(0), Gn = T(0), Sn = T(0), Yn = T(0);
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) {
+        const Ref<T> r = mat_ref<T>(g.mat[l], rhol[l], J2);
+        if (s.ar[l] != T(0)) rhoe += s.ar[l] * r.eref;
+        rhoe += s.phi[l] * (s.p - r.pref) / r.Gam;
+        den += s.phi[l] / r.Gam;
+        Gn += s.phi[l] * r.G / r.Gam;
+        Sn += s.phi[l] * (T)g.mat[l].sigY / r.Gam;
+        const T rl = rhol[l];
+        const T a2 = r.Gam * s.p / rl + (s.p - r.pref) / rl + r.dpref - r.Gam * rl * r.deref;
+        const T c2l = a2 + T(4) / T(3) * r.G / rl;
+        if (s.ar[l] != T(0)) Yn += (s.ar[l] / s.rho) * c2l / r.Gam;
+    }
+    T ke = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; a++) ke += T(0.5) * s.rho * s.u[a] * s.u[a];
+    s.rhoE = rhoe + ke;
+    s.G = Gn / den;
+    s.sigY = Sn / den;
+    s.c2 = Yn / den;
+}
+
+template <class T, int NMAT>
+__device__ __forceinline__ bool needs_fp64(const T *phi_first)
+{
+    if (NMAT < 2) return false;
+    T fsum = T(0), mn = T(1);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; l++) {
+        mn = m_min(mn, phi_first[l]);
+        fsum += phi_first[l];
+    }
+    mn = m_min(mn, T(1) - fsum);
+    return mn < T(1e-6);
+}
+
+// State from primitives in the compute type T; the FP32 form switches to FP64
+// for cells whose smallest volume fraction is below 1e-6.
+template <class T, int DIM, int NMAT, bool SOLID>
+__device__ __forceinline__ void state_from_prim(const GridP &g, const T *w, State<T, DIM, NMAT, SOLID> &s)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    if (sizeof(T) == 4 && needs_fp64<T, NMAT>(w + L::IPHI)) {
+        double wd[L::NVAR];
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) wd[v] = (double)w[v];
+        State<double, DIM, NMAT, SOLID> sd;
+        state_from_prim_ct<double, DIM, NMAT, SOLID>(g, wd, sd);
+#pragma unroll
+        for (int l = 0; l < NMAT; l++) {
+            s.phi[l] = (T)sd.phi[l];
+            s.ar[l] = (T)sd.ar[l];
+        }
+        s.rho = (T)sd.rho;
+#pragma unroll
+        for (int a = 0; a < DIM; a++) s.u[a] = (T)sd.u[a];
+        s.p = (T)sd.p;
+        s.rhoE = (T)sd.rhoE;
+        s.c2 = (T)sd.c2;
+        s.G = (T)sd.G;
+        s.sigY = (T)sd.sigY;
+        if (SOLID) {
+#pragma unroll
+            for (int a = 0; a < DIM; a++)
+#pragma unroll
+                for (int b = 0; b < DIM; b++) s.H[a][b] = (T)sd.H[a][b];
+        }
+        return;
+    }
+    state_from_prim_ct<T, DIM, NMAT, SOLID>(g, w, s);
+}
+
+// Conserved -> primitive (Sec. 2.2): rho_l = (phi rho)_l / max(phi_l, guard),
+// u = (rho u)/rho and the mixture pressure
+// p = (rho E - rho|u|^2/2 - sum[(phi rho)_l e_ref,l - phi_l p_ref,l/Gamma_l]) / sum phi_l/Gamma_l.
+template <class T, int DIM, int NMAT, bool SOLID>
+__device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    T phi[NMAT], ar[NMAT], rho = T(0), fsum = T(0);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; l++) {
+        phi[l] = q[L::IPHI + l];
+        fsum += phi[l];
+    }
+    phi[NMAT - 1] = T(1) - fsum;
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) {
+        ar[l] = q[L::IAR + l];
+        rho += ar[l];
+    }
+    T u[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) u[a] = q[L::IMOM + a] / rho;
+    T J2 = T(0);
+    if (SOLID) {
+        double A[3][3], H[3][3], j2;
+        Eig2 e;
+        unpack_A<T, DIM, NMAT, SOLID>(q, A);
+        stretch_log<DIM>(A, H, j2, e);
+        J2 = (T)j2;
+    }
+    T ke = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; a++) ke += T(0.5) * rho * u[a] * u[a];
+    T num = q[L::IE] - ke, den = T(0);
+    T rhol[NMAT];
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) {
+        const T ph = phi[l] > (T)g.phi_guard ? phi[l] : (T)g.phi_guard;
+        rhol[l] = (NMAT == 1) ? rho : ar[l] / ph;
+        const Ref<T> r = mat_ref<T>(g.mat[l], rhol[l], J2);
+        if (ar[l] != T(0)) num -= ar[l] * r.eref;
+        num += phi[l] * r.pref / r.Gam;
+        den += phi[l] / r.Gam;
+    }
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; l++) w[L::IPHI + l] = phi[l];
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) w[L::IAR + l] = rhol[l];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) w[L::IMOM + a] = u[a];
+    w[L::IE] = num / den;
+#pragma unroll
+    for (int c = 0; c < L::NV; c++) w[L::IV + c] = q[L::IV + c];
+    w[L::IR] = q[L::IR];
+}
+
+template <class T, int DIM, int NMAT, bool SOLID>
+__device__ __forceinline__ void cons_to_prim(const GridP &g, const T *q, T *w)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    if (sizeof(T) == 4 && needs_fp64<T, NMAT>(q + L::IPHI)) {
+        double qd[L::NVAR], wd[L::NVAR];
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) qd[v] = (double)q[v];
+        cons_to_prim_ct<double, DIM, NMAT, SOLID>(g, qd, wd);
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) w[v] = (T)wd[v];
+        return;
+    }
+    cons_to_prim_ct<T, DIM, NMAT, SOLID>(g, q, w);
+}
+
+template <class T, int DIM, int NMAT, bool SOLID>
+__device__ __forceinline__ void prim_to_cons(const GridP &g, const T *w, T *q)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    State<T, DIM, NMAT, SOLID> s;
+    state_from_prim<T, DIM, NMAT, SOLID>(g, w, s);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; l++) q[L::IPHI + l] = s.phi[l];
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) q[L::IAR + l] = s.ar[l];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) q[L::IMOM + a] = s.rho * s.u[a];
+    q[L::IE] = s.rhoE;
+#pragma unroll
+    for (int c = 0; c < L::NV; c++) q[L::IV + c] = w[L::IV + c];
+    q[L::IR] = w[L::IR];
+}
+
+// ------------------------------------------------------- reconstruction
+
+template <class T>
+__device__ __forceinline__ T vanleer(T a, T b)
+{
+    return (a * b <= T(0)) ? T(0) : T(2) * a * b / (a + b);
+}
+
+// THINC face values of a cell (Sec. 3.1, MUSCL-BVD-THINC): the tanh profile
+// q_min + dq/2 (1 + theta tanh(beta (x - x_c))) on [0,1] whose cell average is
+// q0 has tanh(beta x_c) = (cosh beta - exp(theta beta (2C-1)))/sinh beta with
+// C = (q0 - q_min)/dq; its end values are returned.  Only monotone cells with
+// 1e-8 < C < 1 - 1e-8.
+template <class T>
+__device__ __forceinline__ bool thinc(const GridP &g, T qm, T q0, T qp, T &fm, T &fp)
+{
+    if ((qp - q0) * (q0 - qm) <= T(0)) return false;
+    const T qmin = m_min(qm, qp), qmax = m_max(qm, qp);
+    const T dq = qmax - qmin;
+    const T th = (qp - qm) >= T(0) ? T(1) : T(-1);
+    const T C = (q0 - qmin) / dq;
+    if (!(C > T(1e-8) && C < T(1) - T(1e-8))) return false;
+    const T B = m_exp(th * (T)g.beta * (T(2) * C - T(1)));
+    const T ty = ((T)g.cosh_b - B) / (T)g.sinh_b;
+    const T tb = (T)g.tanh_b;
+    const T t1 = (tb - ty) / (T(1) - tb * ty);
+    fm = qmin + T(0.5) * dq * (T(1) - th * ty);
+    fp = qmin + T(0.5) * dq * (T(1) + th * t1);
+    return true;
+}
+
+// Left and right states at the face between cells f-1 and f of a pencil,
+// s[0..5] = q_{f-3} .. q_{f+2}.  MUSCL (van Leer) for every primitive; for a
+// volume fraction (frac = true) the BVD rule keeps a cell's THINC face values
+// only where its total boundary variation is strictly below MUSCL's.
+template <class T>
+__device__ __forceinline__ void recon_face(const GridP &g, const T *s, bool frac, T &qL, T &qR)
+{
+    const T slB = vanleer(s[2] - s[1], s[3] - s[2]);
+    const T slC = vanleer(s[3] - s[2], s[4] - s[3]);
+    const T Bp = s[2] + T(0.5) * slB, Cm = s[3] - T(0.5) * slC;
+    qL = Bp;
+    qR = Cm;
+    if (!frac || !g.use_thinc) return;
+    const T slA = vanleer(s[1] - s[0], s[2] - s[1]);
+    const T slE = vanleer(s[4] - s[3], s[5] - s[4]);
+    const T Ap = s[1] + T(0.5) * slA, Bm = s[2] - T(0.5) * slB;
+    const T Cp = s[3] + T(0.5) * slC, Em = s[4] - T(0.5) * slE;
+    T tAm = s[1] - T(0.5) * slA, tAp = Ap, tBm = Bm, tBp = Bp, tCm = Cm, tCp = Cp, tEm = Em, tEp = s[4] + T(0.5) * slE;
+    thinc<T>(g, s[0], s[1], s[2], tAm, tAp);
+    thinc<T>(g, s[1], s[2], s[3], tBm, tBp);
+    thinc<T>(g, s[2], s[3], s[4], tCm, tCp);
+    thinc<T>(g, s[3], s[4], s[5], tEm, tEp);
+    const T tbvBM = m_abs(Ap - Bm) + m_abs(Bp - Cm);
+    const T tbvBT = m_abs(tAp - tBm) + m_abs(tBp - tCm);
+    const T tbvCM = m_abs(Bp - Cm) + m_abs(Cp - Em);
+    const T tbvCT = m_abs(tBp - tCm) + m_abs(tCp - tEm);
+    if (tbvBT < tbvBM) qL = tBp;
+    if (tbvCT < tbvCM) qR = tCm;
+}
+
+// ------------------------------------------------------------- Riemann
+
+// HLLC flux across a face normal to direction D (Sec. 3.1: Toro's HLLC; the
+// fluid pressure replaced by the normal traction T = p - 2G devH_DD for solids;
+// Davis wave speeds; partial densities scaled like the mixture density).
+// out[0..NVAR-1]: flux of every plane (r: upwind with the body velocity vr),
+// out[NVAR]: face velocity u*_D, out[NVAR+1+b]: V*_{D b} (upwind by S*).
+template <class T, int DIM, int NMAT, bool SOLID, int D>
+__device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR, T vr, T *out)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    State<T, DIM, NMAT, SOLID> sl, sr;
+    state_from_prim<T, DIM, NMAT, SOLID>(g, wL, sl);
+    state_from_prim<T, DIM, NMAT, SOLID>(g, wR, sr);
+    const T cL = m_sqrt(sl.c2), cR = m_sqrt(sr.c2);
+    const T uL = sl.u[D], uR = sr.u[D];
+    const T TL = SOLID ? sl.p - T(2) * sl.G * sl.H[D][D] : sl.p;
+    const T TR = SOLID ? sr.p - T(2) * sr.G * sr.H[D][D] : sr.p;
+    const T SL = m_min(uL - cL, uR - cR);
+    const T SR = m_max(uL + cL, uR + cR);
+    const T Ss = (TR - TL + sl.rho * uL * (SL - uL) - sr.rho * uR * (SR - uR)) /
+                 (sl.rho * (SL - uL) - sr.rho * (SR - uR));
+    int region;
+    if (SL >= T(0)) region = 0;
+    else if (Ss >= T(0)) region = 1;
+    else if (SR > T(0)) region = 2;
+    else region = 3;
+    const State<T, DIM, NMAT, SOLID> &K = (region <= 1) ? sl : sr;
+    const T SK = (region <= 1) ? SL : SR;
+    const T TK = (region <= 1) ? TL : TR;
+    const T uK = K.u[D];
+    // physical flux of the selected side
+    T sig[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) sig[a] = (a == D ? -K.p : T(0)) + (SOLID ? T(2) * K.G * K.H[a][D] : T(0));
+    T work = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; a++) work += K.u[a] * sig[a];
+    const bool star = (region == 1 || region == 2);
+    const T chi = star ? (SK - uK) / (SK - Ss) : T(0);
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) {
+        const T F = K.ar[l] * uK;
+        out[L::IAR + l] = star ? F + SK * (K.ar[l] * chi - K.ar[l]) : F;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const T m = K.rho * K.u[a];
+        const T F = m * uK - sig[a];
+        const T Us = K.rho * chi * (a == D ? Ss : K.u[a]);
+        out[L::IMOM + a] = star ? F + SK * (Us - m) : F;
+    }
+    {
+        const T F = K.rhoE * uK - work;
+        const T EK = K.rhoE / K.rho;
+        const T Us = K.rho * chi * (EK + (Ss - uK) * (Ss + TK / (K.rho * (SK - uK))));
+        out[L::IE] = star ? F + SK * (Us - K.rhoE) : F;
+    }
+    // interface state at x/t = 0
+    const bool left = Ss >= T(0);
+    const T *wu = left ? wL : wR;
+    T us[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) us[a] = left ? sl.u[a] : sr.u[a];
+    us[D] = (region == 0) ? uL : ((region == 3) ? uR : Ss);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; l++) out[L::IPHI + l] = wu[L::IPHI + l] * us[D];
+#pragma unroll
+    for (int c = 0; c < L::NV; c++) {
+        const int a = v_row(DIM, c), b = v_col(DIM, c);
+        // F(V_ab) = V*_ab u*_D - V*_Db u*_a ; V*_Db is stored whenever b < DIM or (D,b) = (2,2)
+        T vdb = T(0);
+#pragma unroll
+        for (int cc = 0; cc < L::NV; cc++)
+            if (v_row(DIM, cc) == D && v_col(DIM, cc) == b) vdb = wu[L::IV + cc];
+        const T ua = (a < DIM) ? us[a] : T(0);
+        out[L::IV + c] = wu[L::IV + c] * us[D] - vdb * ua;
+    }
+    out[L::IR] = (vr > T(0)) ? wL[L::IR] * vr : ((vr < T(0)) ? wR[L::IR] * vr : T(0));
+    out[L::NVAR] = us[D];
+#pragma unroll
+    for (int b = 0; b < L::NB; b++) {
+        T vdb = T(0);
+#pragma unroll
+        for (int cc = 0; cc < L::NV; cc++)
+            if (v_row(DIM, cc) == D && v_col(DIM, cc) == b) vdb = wu[L::IV + cc];
+        out[L::NVAR + 1 + b] = vdb;
+    }
+}
+
+// -------------------------------------------------------- plastic return
+
+// Perfect plasticity by instantaneous radial return, in FP64: the stored A is
+// replaced by its symmetric unimodular stretch Q diag(exp(s d_k)) Q^T with d_k
+// the deviatoric log-stretches and s = min(1, sigma_Y/sigma_vm),
+// sigma_vm = sqrt(3/2) 2 G |d| (mixture G and sigma_Y).  Energy, masses and
+// momenta are untouched.
+template <int DIM>
+__device__ __forceinline__ void plastic_return(double A[3][3], double G, double sigY)
+{
+    double H[3][3], J2;
+    Eig2 e;
+    stretch_log<DIM>(A, H, J2, e);
+    const double svm = sqrt(1.5) * 2.0 * G * sqrt(J2);
+    const double sc = (svm > sigY) ? sigY / svm : 1.0;
+    const double e0 = exp(sc * e.d[0]), e1 = exp(sc * e.d[1]), e2 = exp(sc * e.d[2]);
+    const double av = 0.5 * (e0 + e1), df = 0.5 * (e0 - e1);
+    A[0][0] = av + df * e.c2;
+    A[1][1] = av - df * e.c2;
+    A[0][1] = A[1][0] = df * e.s2;
+    A[2][2] = e2;
+    A[0][2] = A[2][0] = A[1][2] = A[2][1] = 0.0;
+    if (DIM == 1) {
+        A[0][0] = e0;
+        A[1][1] = e1;
+        A[0][1] = A[1][0] = 0.0;
+    }
+}
+
+}  // namespace dfv

@@ -1,0 +1,110 @@
+// dfv_inst.cuh -- builds the launcher table of one precision; included by
+// dfv_inst_f64.cu and dfv_inst_f32.cu with R set to the storage type.
+#pragma once
+
+#include "dfv_kernels.cuh"
+#include "dfv_ops.h"
+
+namespace dfv {
+
+template <class R, int DIM, int NMAT, bool SOLID>
+struct Impl {
+    using L = Lay<DIM, NMAT, SOLID>;
+    using TL = Tile<DIM>;
+
+    static dim3 stage_grid(const GridP &g)
+    {
+        return dim3((g.n[0] + TL::TX - 1) / TL::TX, (g.n[1] + TL::TY - 1) / TL::TY, (g.n[2] + TL::TZ - 1) / TL::TZ);
+    }
+
+    static constexpr size_t smem = StageSmem<R, DIM, NMAT, SOLID>::bytes;
+
+    // Opt the stage kernels in to their dynamic shared memory on the current
+    // device (called at grid creation, outside any stream capture).
+    static cudaError_t prepare()
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_stage<R, DIM, NMAT, SOLID, 1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_stage<R, DIM, NMAT, SOLID, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_stage<R, DIM, NMAT, SOLID, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        return e;
+    }
+
+    template <int S>
+    static cudaError_t stage_s(const GridP &g, const StageArgs &a, cudaStream_t st)
+    {
+        k_stage<R, DIM, NMAT, SOLID, S><<<stage_grid(g), TL::THREADS, smem, st>>>(a, g);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t stage(int s, const GridP &g, const void *in, const void *un, void *out, Ctl *ctl,
+                             double *partials, int want_force, cudaStream_t st)
+    {
+        StageArgs a;
+        a.in = in;
+        a.un = un;
+        a.out = out;
+        a.ctl = ctl;
+        a.partials = partials;
+        a.want_force = want_force;
+        if (s == 1) return stage_s<1>(g, a, st);
+        if (s == 2) return stage_s<2>(g, a, st);
+        return stage_s<3>(g, a, st);
+    }
+
+    static cudaError_t seed(const GridP &g, void *U, const Ctl *ctl, cudaStream_t st)
+    {
+        k_seed<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(U, ctl, g);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t cfl(const GridP &g, const void *U, double *partials, int nblocks, cudaStream_t st)
+    {
+        k_cfl<R, DIM, NMAT, SOLID><<<nblocks, 256, 0, st>>>(U, partials, g);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t p2c(const GridP &g, const double *prim, long long pp, void *U, cudaStream_t st)
+    {
+        k_prim_to_cons<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(prim, pp, U, g);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t c2p(const GridP &g, const void *U, double *prim, long long pp, cudaStream_t st)
+    {
+        k_cons_to_prim<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(U, prim, pp, g);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t c2f(const GridP &g, const void *U, double *o, long long pp, int nvar, cudaStream_t st)
+    {
+        k_cons_to_f64<R><<<gs_blocks(g.ncell), 256, 0, st>>>(U, o, pp, nvar, g);
+        return cudaGetLastError();
+    }
+
+    static const Ops *ops()
+    {
+        static const Ops o = {L::NVAR, TL::THREADS, (int)sizeof(R), &prepare, &stage_grid, &seed, &stage, &cfl,
+                              &p2c, &c2p, &c2f};
+        return &o;
+    }
+};
+
+// Tables of one dimension (3-D solids are not built).
+template <class R, int DIM>
+const Ops *select_ops_dim(int nmat, int solid)
+{
+    if (nmat == 1 && !solid) return Impl<R, DIM, 1, false>::ops();
+    if (nmat == 2 && !solid) return Impl<R, DIM, 2, false>::ops();
+    if constexpr (DIM <= 2) {
+        if (nmat == 1 && solid) return Impl<R, DIM, 1, true>::ops();
+        if (nmat == 2 && solid) return Impl<R, DIM, 2, true>::ops();
+    }
+    return nullptr;
+}
+
+}  // namespace dfv

@@ -1,0 +1,583 @@
+// dfv_kernels.cuh -- the kernels of one time step (arXiv:2111.11806, Sec. 3):
+//   k_seed      rigid interface seeding (Sec. 3.2), in place, band cells only
+//   k_stage<S>  one SSP-RK3 stage (Sec. 3.1): halo-3 tile of primitives in
+//               shared memory, per-face MUSCL-BVD-THINC + HLLC, divergence,
+//               non-conservative terms, rigid mask, RK combination; stage 1
+//               also sums the pressure force, stage 3 applies the plastic
+//               return and reduces the CFL wave speed of the new state
+//   k_cfl       CFL wave-speed reduction of a stored state
+//   k_finalize  one block: deterministic sums of the per-block partials,
+//               body update, next dt
+//   k_prim_to_cons / k_cons_to_prim / k_cons_to_f64   field conversion
+#pragma once
+
+#include "dfv_device.cuh"
+
+namespace dfv {
+
+// ------------------------------------------------------------ tiling
+
+template <int DIM>
+struct Tile;
+template <>
+struct Tile<1> {
+    static constexpr int TX = 256, TY = 1, TZ = 1, THREADS = 288;
+};
+template <>
+struct Tile<2> {
+    static constexpr int TX = 32, TY = 8, TZ = 1, THREADS = 288;
+};
+template <>
+struct Tile<3> {
+    static constexpr int TX = 32, TY = 4, TZ = 2, THREADS = 384;
+};
+
+template <int DIM>
+struct Box {
+    using TL = Tile<DIM>;
+    static constexpr int HX = 3, HY = DIM >= 2 ? 3 : 0, HZ = DIM >= 3 ? 3 : 0;
+    static constexpr int BX = TL::TX + 2 * HX, BY = TL::TY + 2 * HY, BZ = TL::TZ + 2 * HZ;
+    static constexpr int N = BX * BY * BZ;
+    static constexpr int CELLS = TL::TX * TL::TY * TL::TZ;
+    static constexpr int FX = (TL::TX + 1) * TL::TY * TL::TZ;
+    static constexpr int FY = TL::TX * (TL::TY + 1) * TL::TZ;
+    static constexpr int FZ = TL::TX * TL::TY * (TL::TZ + 1);
+    static constexpr int MAXF = FX > FY ? (FX > FZ ? FX : FZ) : (FY > FZ ? FY : FZ);
+    __host__ __device__ static constexpr int stride(int d) { return d == 0 ? 1 : (d == 1 ? BX : BX * BY); }
+};
+
+template <class R, int DIM, int NMAT, bool SOLID>
+struct StageSmem {
+    using L = Lay<DIM, NMAT, SOLID>;
+    using B = Box<DIM>;
+    static constexpr size_t bytes =
+        ((sizeof(R) * ((size_t)L::NVAR * B::N + (size_t)L::NF * B::MAXF) + 7) & ~(size_t)7) + 4 * 32 * sizeof(double);
+};
+
+// ---------------------------------------------------- compensated sums
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// Accumulator: plain in FP64, (hi, lo) pair with TwoSum in FP32.
+template <class R>
+struct Acc {
+    R hi, lo;
+    __device__ __forceinline__ void zero() { hi = R(0); lo = R(0); }
+    __device__ __forceinline__ void add(R x)
+    {
+        if (sizeof(R) == 8) {
+            hi += x;
+        } else {
+            float s, e;
+            two_sum((float)hi, (float)x, s, e);
+            hi = (R)s;
+            lo += (R)e;
+        }
+    }
+};
+
+// out = ca*un + cb*(in - dt*D) with one final rounding in FP32 (error-free
+// products and TwoSum on every partial sum, the Dot2 scheme of Ogita, Rump &
+// Oishi); plain evaluation in FP64.
+template <class R>
+__device__ __forceinline__ R rk_combine(int stage, R un, R in, const Acc<R> &D, double dt, R ca, R cb)
+{
+    if (sizeof(R) == 8) {
+        const R y = in - (R)dt * D.hi;
+        return stage == 1 ? y : ca * un + cb * y;
+    } else {
+        const float fdt = (float)dt;
+        // y = in - dt*(hi+lo), kept as (y, ey)
+        const float p = fdt * (float)D.hi;
+        const float pe = fmaf(fdt, (float)D.hi, -p);
+        float y, ey;
+        two_sum((float)in, -p, y, ey);
+        ey += -pe - fdt * (float)D.lo;
+        if (stage == 1) return (R)(y + ey);
+        const float a = (float)ca * (float)un;
+        const float ae = fmaf((float)ca, (float)un, -a);
+        const float b = (float)cb * y;
+        const float be = fmaf((float)cb, y, -b);
+        float s, se;
+        two_sum(a, b, s, se);
+        return (R)(s + (se + ae + be + (float)cb * ey));
+    }
+}
+
+// --------------------------------------------------- block reductions
+
+// Fixed-order block reduction of up to 4 doubles (max for k = 0, sum for the
+// rest): warp shuffles, then warp leaders in index order.
+template <int THREADS>
+__device__ __forceinline__ void block_reduce4(double v[4], double *scratch /* 4*32 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double m = __shfl_down_sync(0xffffffffu, v[0], o);
+        v[0] = fmax(v[0], m);
+#pragma unroll
+        for (int k = 1; k < 4; k++) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0)
+        for (int k = 0; k < 4; k++) scratch[k * 32 + warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        constexpr int NW = (THREADS + 31) / 32;
+        double r[4] = {scratch[0], scratch[32], scratch[64], scratch[96]};
+        for (int w = 1; w < NW; w++) {
+            r[0] = fmax(r[0], scratch[w]);
+            for (int k = 1; k < 4; k++) r[k] += scratch[k * 32 + w];
+        }
+        for (int k = 0; k < 4; k++) v[k] = r[k];
+    }
+}
+
+// --------------------------------------------------------------- stage
+
+struct StageArgs {
+    const void *in;     // U^(s-1) (stage input, read with halo)
+    const void *un;     // U^n (read at the cell only)
+    void *out;          // U^(s)
+    Ctl *ctl;
+    double *partials;   // 4 doubles per block
+    int want_force;
+};
+
+template <class R, int DIM, int NMAT, bool SOLID, int D>
+__device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, bool own, int lx, int ly, int lz,
+                                      Acc<R> *Dacc)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    using B = Box<DIM>;
+    using TL = Tile<DIM>;
+    constexpr int EX = TL::TX + (D == 0), EY = TL::TY + (D == 1), EZ = TL::TZ + (D == 2);
+    constexpr int NFACE = EX * EY * EZ;
+    constexpr int SD = B::stride(D);
+    for (int item = threadIdx.x; item < NFACE; item += TL::THREADS) {
+        const int fx = item % EX, fy = (item / EX) % EY, fz = item / (EX * EY);
+        // box index of the cell on the right of the face
+        const int bc = ((fz + B::HZ) * B::BY + (fy + B::HY)) * B::BX + (fx + B::HX);
+        R wL[L::NVAR], wR[L::NVAR];
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) {
+            R s[6];
+#pragma unroll
+            for (int k = 0; k < 6; k++) s[k] = sW[v * B::N + bc + (k - 3) * SD];
+            const bool frac = (v >= L::IPHI && v < L::IPHI + NMAT - 1) || v == L::IR;
+            recon_face<R>(g, s, frac, wL[v], wR[v]);
+        }
+        R F[L::NF];
+        riemann<R, DIM, NMAT, SOLID, D>(g, wL, wR, vr, F);
+#pragma unroll
+        for (int k = 0; k < L::NF; k++) sF[k * B::MAXF + item] = F[k];
+    }
+    __syncthreads();
+    if (own) {
+        const int fl = (lz * EY + ly) * EX + lx;
+        const int fr = fl + (D == 0 ? 1 : (D == 1 ? EX : EX * EY));
+        const int bcell = ((lz + B::HZ) * B::BY + (ly + B::HY)) * B::BX + (lx + B::HX);
+        const R inv = (R)g.inv_dx[D];
+        const R dus = sF[L::NVAR * B::MAXF + fr] - sF[L::NVAR * B::MAXF + fl];
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) {
+            const R div = (sF[v * B::MAXF + fr] - sF[v * B::MAXF + fl]) * inv;
+            R snc = R(0);
+            if (v >= L::IPHI && v < L::IPHI + NMAT - 1) snc = sW[v * B::N + bcell] * dus * inv;
+            if (SOLID && v >= L::IV && v < L::IV + L::NV) {
+                const int c = v - L::IV;
+                const int a = v_row(DIM, c), b = v_col(DIM, c);
+                const R ua = (a < DIM) ? sW[(L::IMOM + a) * B::N + bcell] : R(0);
+                const R dv = (b < L::NB) ? sF[(L::NVAR + 1 + b) * B::MAXF + fr] - sF[(L::NVAR + 1 + b) * B::MAXF + fl]
+                                         : R(0);
+                snc = (R(2) / R(3) * sW[v * B::N + bcell] * dus - ua * dv) * inv;
+            }
+            Dacc[v].add(div - snc);
+        }
+    }
+    __syncthreads();
+}
+
+template <class R, int DIM, int NMAT, bool SOLID, int STAGE>
+__global__ void __launch_bounds__(Tile<DIM>::THREADS) k_stage(StageArgs a, GridP g)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    using B = Box<DIM>;
+    using TL = Tile<DIM>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sW = reinterpret_cast<R *>(smem_raw);
+    R *sF = sW + (size_t)L::NVAR * B::N;
+    double *sred = reinterpret_cast<double *>(
+        smem_raw + ((sizeof(R) * ((size_t)L::NVAR * B::N + (size_t)L::NF * B::MAXF) + 7) & ~(size_t)7));
+
+    const R *in = reinterpret_cast<const R *>(a.in);
+    const R *un = reinterpret_cast<const R *>(a.un);
+    R *out = reinterpret_cast<R *>(a.out);
+    const long long P = g.pitch;
+    const int ox = blockIdx.x * TL::TX, oy = blockIdx.y * TL::TY, oz = blockIdx.z * TL::TZ;
+
+    // 1. primitives of the tile and its halo (the corner regions are unused)
+    for (int i = threadIdx.x; i < B::N; i += TL::THREADS) {
+        const int bx = i % B::BX, by = (i / B::BX) % B::BY, bz = i / (B::BX * B::BY);
+        const int lx = bx - B::HX, ly = by - B::HY, lz = bz - B::HZ;
+        const int outside = (lx < 0 || lx >= TL::TX) + (ly < 0 || ly >= TL::TY) + (lz < 0 || lz >= TL::TZ);
+        if (outside > 1) continue;
+        const int gx = map_idx(ox + lx, g.n[0], g.periodic[0]);
+        const int gy = DIM >= 2 ? map_idx(oy + ly, g.n[1], g.periodic[1]) : 0;
+        const int gz = DIM >= 3 ? map_idx(oz + lz, g.n[2], g.periodic[2]) : 0;
+        const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
+        R q[L::NVAR], w[L::NVAR];
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) q[v] = in[v * P + c];
+        cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) sW[v * B::N + i] = w[v];
+    }
+    __syncthreads();
+
+    const bool own = threadIdx.x < B::CELLS;
+    const int lx = threadIdx.x % TL::TX, ly = (threadIdx.x / TL::TX) % TL::TY, lz = threadIdx.x / (TL::TX * TL::TY);
+    const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+    const bool inside = own && gx < g.n[0] && gy < g.n[1] && gz < g.n[2];
+    const double dt = a.ctl->dt;
+    R vr[3] = {(R)a.ctl->v[0], (R)a.ctl->v[1], (R)a.ctl->v[2]};
+
+    Acc<R> Dacc[L::NVAR];
+#pragma unroll
+    for (int v = 0; v < L::NVAR; v++) Dacc[v].zero();
+
+    sweep<R, DIM, NMAT, SOLID, 0>(g, sW, sF, vr[0], own, lx, ly, lz, Dacc);
+    if constexpr (DIM >= 2) sweep<R, DIM, NMAT, SOLID, 1>(g, sW, sF, vr[1], own, lx, ly, lz, Dacc);
+    if constexpr (DIM >= 3) sweep<R, DIM, NMAT, SOLID, 2>(g, sW, sF, vr[2], own, lx, ly, lz, Dacc);
+
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    if (inside) {
+        const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
+        const int bcell = ((lz + B::HZ) * B::BY + (ly + B::HY)) * B::BX + (lx + B::HX);
+        const bool masked = un[L::IR * P + c] > R(0.5);
+        const R ca = STAGE == 2 ? R(0.75) : (STAGE == 3 ? R(1.0 / 3.0) : R(0));
+        const R cb = STAGE == 2 ? R(0.25) : (STAGE == 3 ? R(2.0 / 3.0) : R(1));
+        R o[L::NVAR];
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) {
+            const R unv = un[v * P + c];
+            if (masked && v != L::IR) {
+                o[v] = unv;
+            } else {
+                o[v] = rk_combine<R>(STAGE, unv, in[v * P + c], Dacc[v], dt, ca, cb);
+            }
+        }
+        if (SOLID && STAGE == 3 && !masked) {
+            // plastic relaxation on the new state (mixture G, sigma_Y from its primitives)
+            R w[L::NVAR];
+            cons_to_prim<R, DIM, NMAT, SOLID>(g, o, w);
+            State<R, DIM, NMAT, SOLID> s;
+            state_from_prim<R, DIM, NMAT, SOLID>(g, w, s);
+            double A[3][3];
+            unpack_A<R, DIM, NMAT, SOLID>(o, A);
+            plastic_return<DIM>(A, (double)s.G, (double)s.sigY);
+#pragma unroll
+            for (int cc = 0; cc < L::NV; cc++) o[L::IV + cc] = (R)A[v_row(DIM, cc)][v_col(DIM, cc)];
+        }
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) out[v * P + c] = o[v];
+        if (!(o[L::IAR] + (NMAT > 1 ? o[L::IAR + NMAT - 1] : R(0)) > R(0)) || !(o[L::IE] == o[L::IE]))
+            atomicOr(&a.ctl->err, (unsigned)ERR_STATE);
+        if (STAGE == 1 && a.want_force) {
+            // pressure force: p (grad r) dV with central differences (Youngs)
+            const R p = sW[L::IE * B::N + bcell];
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+                const int sd = B::stride(d);
+                const R gr = (sW[L::IR * B::N + bcell + sd] - sW[L::IR * B::N + bcell - sd]) / (R(2) * (R)g.dx[d]);
+                red[1 + d] = (double)p * (double)gr * g.dV;
+            }
+        }
+        if (STAGE == 3) {
+            R w[L::NVAR];
+            cons_to_prim<R, DIM, NMAT, SOLID>(g, o, w);
+            State<R, DIM, NMAT, SOLID> s;
+            state_from_prim<R, DIM, NMAT, SOLID>(g, w, s);
+            if (!(s.c2 > R(0))) atomicOr(&a.ctl->err, (unsigned)ERR_SOUND);
+            const double cs = sqrt((double)s.c2);
+            double sum = 0.0;
+#pragma unroll
+            for (int d = 0; d < DIM; d++) sum += (fabs((double)s.u[d]) + cs) / g.dx[d];
+            red[0] = sum;
+        }
+    }
+    if (STAGE == 3 || (STAGE == 1 && a.want_force)) {
+        block_reduce4<TL::THREADS>(red, sred);
+        if (threadIdx.x == 0) {
+            const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+            double *pp = a.partials + 4 * b;
+            if (STAGE == 3) pp[0] = red[0];
+            else {
+                pp[1] = red[1];
+                pp[2] = red[2];
+                pp[3] = red[3];
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------- seeding
+
+// Rigid seeding (Sec. 3.2, original variant), one thread per cell, in place:
+// cells with r > 0.5 and |grad r| dx_min > 1e-10 get the outward normal
+// n = -grad r/|grad r| (Youngs, Sec. 3.3), probe points at 1.0, 1.5, ..., 4.0
+// dx_min along n, the first point whose 2^dim enclosing cell centres are in the
+// domain (wrapped if periodic) with r < 0.5 is interpolated multilinearly in
+// the primitives, and u <- (I - 2nn^T) u + 2 (v_r.n) n, V <- (I - 2nn^T) V (I - 2nn^T).
+// Only r < 0.5 cells are read and only r > 0.5 cells written, so the update is
+// independent of thread order.  Evaluated in FP64.
+template <class R, int DIM, int NMAT, bool SOLID>
+__global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    R *U = reinterpret_cast<R *>(Uv);
+    const long long P = g.pitch;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const double rc = (double)U[L::IR * P + c];
+        if (!(rc > 0.5)) continue;
+        int ijk[3];
+        ijk[0] = (int)(c % g.n[0]);
+        ijk[1] = (int)((c / g.n[0]) % g.n[1]);
+        ijk[2] = (int)(c / ((long long)g.n[0] * g.n[1]));
+        double gr[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            int lo[3] = {ijk[0], ijk[1], ijk[2]}, hi[3] = {ijk[0], ijk[1], ijk[2]};
+            lo[d] = map_idx(ijk[d] - 1, g.n[d], g.periodic[d]);
+            hi[d] = map_idx(ijk[d] + 1, g.n[d], g.periodic[d]);
+            const long long cl = lo[0] + (long long)g.n[0] * (lo[1] + (long long)g.n[1] * lo[2]);
+            const long long ch = hi[0] + (long long)g.n[0] * (hi[1] + (long long)g.n[1] * hi[2]);
+            gr[d] = ((double)U[L::IR * P + ch] - (double)U[L::IR * P + cl]) / (2.0 * g.dx[d]);
+        }
+        const double gn = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+        if (!(gn * g.dxmin > 1e-10)) continue;
+        const double nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
+        double wi[L::NVAR];
+        bool found = false;
+        for (int step = 0; step < 7 && !found; step++) {
+            const double sd = (1.0 + 0.5 * step) * g.dxmin;
+            int base[3] = {0, 0, 0};
+            double fr[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+                const double xp = g.lo[d] + (ijk[d] + 0.5) * g.dx[d] + sd * nv[d];
+                const double fi = (xp - g.lo[d]) / g.dx[d] - 0.5;
+                const double fl = floor(fi);
+                base[d] = (int)fl;
+                fr[d] = fi - fl;
+            }
+            long long cidx[1 << DIM];
+            double wts[1 << DIM];
+            bool ok = true;
+#pragma unroll
+            for (int m = 0; m < (1 << DIM); m++) {
+                int ci[3] = {0, 0, 0};
+                double wt = 1.0;
+#pragma unroll
+                for (int d = 0; d < DIM; d++) {
+                    const int bit = (m >> d) & 1;
+                    int ii = base[d] + bit;
+                    if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
+                    else if (ii < 0 || ii > g.n[d] - 1) ok = false;
+                    ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
+                    wt *= bit ? fr[d] : (1.0 - fr[d]);
+                }
+                cidx[m] = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
+                wts[m] = wt;
+                if (ok && !((double)U[L::IR * P + cidx[m]] < 0.5)) ok = false;
+            }
+            if (!ok) continue;
+#pragma unroll
+            for (int v = 0; v < L::NVAR; v++) wi[v] = 0.0;
+#pragma unroll
+            for (int m = 0; m < (1 << DIM); m++) {
+                double q[L::NVAR], w[L::NVAR];
+#pragma unroll
+                for (int v = 0; v < L::NVAR; v++) q[v] = (double)U[v * P + cidx[m]];
+                cons_to_prim_ct<double, DIM, NMAT, SOLID>(g, q, w);
+#pragma unroll
+                for (int v = 0; v < L::NVAR; v++) wi[v] += wts[m] * w[v];
+            }
+            found = true;
+        }
+        if (!found) continue;
+        double Pm[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) Pm[i][j] = (i == j ? 1.0 : 0.0) - 2.0 * nv[i] * nv[j];
+        const double vn = ctl->v[0] * nv[0] + ctl->v[1] * nv[1] + ctl->v[2] * nv[2];
+        double u[3] = {0.0, 0.0, 0.0}, unew[3];
+#pragma unroll
+        for (int a = 0; a < DIM; a++) u[a] = wi[L::IMOM + a];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            unew[i] = 2.0 * vn * nv[i];
+#pragma unroll
+            for (int j = 0; j < 3; j++) unew[i] += Pm[i][j] * u[j];
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; a++) wi[L::IMOM + a] = unew[a];
+        if (SOLID) {
+            double A[3][3], PA[3][3];
+            unpack_A<double, DIM, NMAT, SOLID>(wi, A);
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = 0; k < 3; k++) s += Pm[i][k] * A[k][j];
+                    PA[i][j] = s;
+                }
+#pragma unroll
+            for (int cc = 0; cc < L::NV; cc++) {
+                const int i = v_row(DIM, cc), j = v_col(DIM, cc);
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; k++) s += PA[i][k] * Pm[k][j];
+                wi[L::IV + cc] = s;
+            }
+        }
+        wi[L::IR] = rc;
+        double q[L::NVAR];
+        prim_to_cons<double, DIM, NMAT, SOLID>(g, wi, q);
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++)
+            if (v != L::IR) U[v * P + c] = (R)q[v];
+    }
+}
+
+// ------------------------------------------------------------------ CFL
+
+template <class R, int DIM, int NMAT, bool SOLID>
+__global__ void __launch_bounds__(256) k_cfl(const void *Uv, double *partials, GridP g)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    __shared__ double sred[4 * 32];
+    const R *U = reinterpret_cast<const R *>(Uv);
+    const long long P = g.pitch;
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        R q[L::NVAR], w[L::NVAR];
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) q[v] = U[v * P + c];
+        cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
+        State<R, DIM, NMAT, SOLID> s;
+        state_from_prim<R, DIM, NMAT, SOLID>(g, w, s);
+        const double cs = sqrt((double)s.c2);
+        double sum = 0.0;
+#pragma unroll
+        for (int d = 0; d < DIM; d++) sum += (fabs((double)s.u[d]) + cs) / g.dx[d];
+        if (!(sum == sum)) sum = __longlong_as_double(0x7ff0000000000000LL);   // NaN -> +inf: dt = 0
+        red[0] = fmax(red[0], sum);
+    }
+    block_reduce4<256>(red, sred);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x] = red[0];
+}
+
+// ------------------------------------------------------------ finalize
+
+// mode bit 0: reduce the CFL partials (nb_cfl blocks) into ctl->smax
+// mode bit 1: reduce the force partials (nb_force blocks) into ctl->force
+// mode bit 2: end of a step: body update with ctl->dt, t += dt
+// mode bit 3: set the next dt from ctl->cfl (and t_end when > 0)
+static __global__ void __launch_bounds__(1024) k_finalize(Ctl *ctl, const double *partials, long long nb_cfl,
+                                                   long long nb_force, int mode, int dim, double dx0, double dx1,
+                                                   double dx2)
+{
+    __shared__ double sred[4 * 32];
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    if (mode & 1)
+        for (long long b = threadIdx.x; b < nb_cfl; b += blockDim.x) red[0] = fmax(red[0], partials[4 * b]);
+    if (mode & 2)
+        for (long long b = threadIdx.x; b < nb_force; b += blockDim.x) {
+            red[1] += partials[4 * b + 1];
+            red[2] += partials[4 * b + 2];
+            red[3] += partials[4 * b + 3];
+        }
+    block_reduce4<1024>(red, sred);
+    if (threadIdx.x != 0) return;
+    const double dxs[3] = {dx0, dx1, dx2};
+    if (mode & 2)
+        for (int d = 0; d < 3; d++) ctl->force[d] = red[1 + d];
+    if (mode & 4) {
+        if (ctl->dynamic && ctl->mass > 0.0)
+            for (int d = 0; d < 3; d++) {
+                ctl->v[d] += ctl->dt * ctl->force[d] / ctl->mass;
+                ctl->x[d] += ctl->dt * ctl->v[d];
+            }
+        ctl->t += ctl->dt;
+        ctl->steps += 1;
+    }
+    if (mode & 1) {
+        double sb = 0.0;
+        for (int d = 0; d < dim; d++) sb += fabs(ctl->v[d]) / dxs[d];
+        ctl->smax = fmax(red[0], sb);
+    }
+    if (mode & 8) {
+        double dt = ctl->cfl / ctl->smax;
+        if (ctl->t_end > 0.0) dt = fmin(dt, fmax(ctl->t_end - ctl->t, 0.0));
+        if (!(dt == dt)) dt = 0.0;
+        ctl->dt = dt;
+    }
+}
+
+static __global__ void k_set_dt(Ctl *ctl, double dt) { ctl->dt = dt; }
+
+// ------------------------------------------------------------ conversions
+
+template <class R, int DIM, int NMAT, bool SOLID>
+__global__ void __launch_bounds__(256) k_prim_to_cons(const double *prim, long long ppitch, void *Uv, GridP g)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    R *U = reinterpret_cast<R *>(Uv);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        double w[L::NVAR], q[L::NVAR];
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) w[v] = prim[v * ppitch + c];
+        prim_to_cons<double, DIM, NMAT, SOLID>(g, w, q);
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) U[v * g.pitch + c] = (R)q[v];
+    }
+}
+
+template <class R, int DIM, int NMAT, bool SOLID>
+__global__ void __launch_bounds__(256) k_cons_to_prim(const void *Uv, double *prim, long long ppitch, GridP g)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    const R *U = reinterpret_cast<const R *>(Uv);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        double q[L::NVAR], w[L::NVAR];
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) q[v] = (double)U[v * g.pitch + c];
+        cons_to_prim_ct<double, DIM, NMAT, SOLID>(g, q, w);
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++) prim[v * ppitch + c] = w[v];
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_cons_to_f64(const void *Uv, double *outp, long long ppitch, int nvar, GridP g)
+{
+    const R *U = reinterpret_cast<const R *>(Uv);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x)
+        for (int v = 0; v < nvar; v++) outp[v * ppitch + c] = (double)U[v * g.pitch + c];
+}
+
+}  // namespace dfv

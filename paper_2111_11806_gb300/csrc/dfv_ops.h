@@ -1,0 +1,60 @@
+// dfv_ops.h -- host-side table of launchers for one (precision, dimension,
+// materials, solid) combination.  The C ABI in dfv_api.cu picks a table at
+// grid creation and issues every launch of a step through it.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dfv_device.cuh"
+
+namespace dfv {
+
+struct StageArgs;
+
+struct Ops {
+    int nvar;
+    int threads_stage;
+    int elem_bytes;
+    cudaError_t (*prepare)();
+    dim3 (*stage_grid)(const GridP &);
+    cudaError_t (*seed)(const GridP &, void *U, const Ctl *ctl, cudaStream_t);
+    cudaError_t (*stage)(int stage, const GridP &, const void *in, const void *un, void *out, Ctl *ctl,
+                         double *partials, int want_force, cudaStream_t);
+    cudaError_t (*cfl)(const GridP &, const void *U, double *partials, int nblocks, cudaStream_t);
+    cudaError_t (*prim_to_cons)(const GridP &, const double *prim, long long ppitch, void *U, cudaStream_t);
+    cudaError_t (*cons_to_prim)(const GridP &, const void *U, double *prim, long long ppitch, cudaStream_t);
+    cudaError_t (*cons_to_f64)(const GridP &, const void *U, double *out, long long ppitch, int nvar, cudaStream_t);
+};
+
+// nullptr when the combination is not built.  One translation unit per
+// (precision, dimension) so that the build compiles them in parallel.
+const Ops *ops_f64_d1(int nmat, int solid);
+const Ops *ops_f64_d2(int nmat, int solid);
+const Ops *ops_f64_d3(int nmat, int solid);
+const Ops *ops_f32_d1(int nmat, int solid);
+const Ops *ops_f32_d2(int nmat, int solid);
+const Ops *ops_f32_d3(int nmat, int solid);
+
+inline const Ops *ops_for(int precision_fp32, int dim, int nmat, int solid)
+{
+    if (precision_fp32) {
+        if (dim == 1) return ops_f32_d1(nmat, solid);
+        if (dim == 2) return ops_f32_d2(nmat, solid);
+        if (dim == 3) return ops_f32_d3(nmat, solid);
+    } else {
+        if (dim == 1) return ops_f64_d1(nmat, solid);
+        if (dim == 2) return ops_f64_d2(nmat, solid);
+        if (dim == 3) return ops_f64_d3(nmat, solid);
+    }
+    return nullptr;
+}
+
+// Grid-stride launches use at most this many blocks of 256 threads.
+inline int gs_blocks(long long n)
+{
+    long long b = (n + 255) / 256;
+    const long long cap = 152LL * 16;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace dfv

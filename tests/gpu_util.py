@@ -1,0 +1,44 @@
+"""Helpers of the GPU parity tests: running the oracle and the CUDA library on
+the same seeded workload and measuring per-plane relative L1 differences."""
+import numpy as np
+
+import workloads as W
+
+
+def plane_scales(ref, wl):
+    """Denominator of the relative L1 per conserved plane: sum |ref|, with
+    momentum planes floored at sum(rho) * 10 m/s so that near-zero momenta
+    are measured against a physical scale rather than round-off."""
+    L = W.layout(wl.dim, wl.nmat, wl.solid)
+    rho = ref[L["irho"]: L["irho"] + wl.nmat].sum(axis=0)
+    s = np.abs(ref).sum(axis=1)
+    for a in range(wl.dim):
+        s[L["iu"] + a] = max(s[L["iu"] + a], 10.0 * np.abs(rho).sum())
+    s[L["ir"]] = max(s[L["ir"]], 1e-3 * ref.shape[1])
+    for l in range(wl.nmat - 1):
+        s[L["iphi"] + l] = max(s[L["iphi"] + l], 1e-3 * ref.shape[1])
+    return np.where(s > 0, s, 1.0)
+
+
+def rel_l1(got, ref, wl):
+    return np.abs(got - ref).sum(axis=1) / plane_scales(ref, wl)
+
+
+def run_both(wl, steps, precision, cfl=None, use_run=False):
+    """Advance the oracle and the GPU grid `steps` steps with the oracle's dt
+    (dfv_step) or the device-computed dt (dfv_run); returns (oracle, grid)."""
+    from oracle import Oracle
+    from paper_2111_11806_gb300 import binding as B
+    cfl = wl.cfl if cfl is None else cfl
+    o = Oracle.from_workload(wl)
+    g = B.Grid.from_workload(wl, precision=precision)
+    if use_run:
+        g.run(steps, cfl)
+        for _ in range(steps):
+            o.step(o.compute_dt(cfl))
+    else:
+        for _ in range(steps):
+            dt = o.compute_dt(cfl)
+            o.step(dt)
+            g.step(dt)
+    return o, g
