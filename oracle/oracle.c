@@ -85,6 +85,8 @@ static int map_index(const ostate *s, int d, int i)
     return i;
 }
 
+static double phi_clip(double f);
+
 static void mat_zero(double M[3][3])
 {
     for (int a = 0; a < 3; a++)
@@ -298,6 +300,7 @@ static void thermo_from_prim(const ostate *s, const double *w, othermo *t)
     t->phi[N - 1] = 1.0 - fsum;
     t->rho = 0.0;
     for (int l = 0; l < N; l++) {
+        t->phi[l] = phi_clip(t->phi[l]);
         t->rhol[l] = w[s->iar + l];
         t->ar[l] = t->phi[l] * t->rhol[l];
         t->rho += t->ar[l];
@@ -341,8 +344,25 @@ static void thermo_from_prim(const ostate *s, const double *w, othermo *t)
     t->c2 = Ynum / den;
 }
 
+/* Volume fraction used as a closure weight: clipped to [0, 1] [reading; the
+ * transported phi may leave the interval by round-off-sized amounts at
+ * interfaces]. */
+static double phi_clip(double f) { return f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f); }
+
+/* Phasic density rho_l = (phi rho)_l / phi_l [Sec. 2.2].  Reading for a
+ * material that is absent from the cell (clipped phi_l < 1e-6): its phasic
+ * density is its reference density rho0 (when given), because the ratio of two
+ * round-off-sized numbers carries no information and, through a stiff cold
+ * curve, would set an arbitrary pressure. */
+#define PHI_ABSENT 1e-6
+static double phasic_density(const ostate *s, int l, double ar, double phc)
+{
+    if (phc < PHI_ABSENT && s->mat[l].rho0 > 0.0) return s->mat[l].rho0;
+    return ar / (phc > s->phi_guard ? phc : s->phi_guard);
+}
+
 /* Conserved -> primitive (Sec. 2.2): phasic densities rho_l = (phi rho)_l /
- * phi_l (phi_l guarded from below by phi_guard), velocity u = (rho u)/rho and
+ * phi_l (see phasic_density), velocity u = (rho u)/rho and
  * the mixture pressure
  * p = (rho e - sum_l [ (phi rho)_l e_ref,l - phi_l p_ref,l / Gamma_l ]) / sum_l phi_l/Gamma_l
  * with rho e = rho E - rho |u|^2 / 2. */
@@ -375,13 +395,13 @@ static void cons_to_prim(const ostate *s, const double *q, double *w)
     double num = rhoe, den = 0.0;
     double rhol[2];
     for (int l = 0; l < N; l++) {
-        double ph = phi[l] > s->phi_guard ? phi[l] : s->phi_guard;
-        rhol[l] = (N == 1) ? rho : ar[l] / ph;
+        double phc = phi_clip(phi[l]);
+        rhol[l] = (N == 1) ? rho : phasic_density(s, l, ar[l], phc);
         double ref[6];
         o_mat_ref(&s->mat[l], rhol[l], J2, ref);
         if (ar[l] != 0.0) num -= ar[l] * ref[1];
-        num += phi[l] * ref[2] / ref[0];
-        den += phi[l] / ref[0];
+        num += phc * ref[2] / ref[0];
+        den += phc / ref[0];
     }
     for (int l = 0; l < N - 1; l++) w[s->iphi + l] = phi[l];
     for (int l = 0; l < N; l++) w[s->iar + l] = rhol[l];
@@ -516,21 +536,55 @@ void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *
     K = (region <= 1) ? &L : &R;
     SK = (region <= 1) ? SL : SR;
     int nthermo_lo = s->iar, nthermo_hi = s->iE; /* ar .. rhoE inclusive */
+    oface *up = (Ss >= 0.0) ? &L : &R;
+    /* tangential traction and velocity at the face: the linear shear-wave
+     * Riemann problem, sigma -/+ Z u constant along the right/left shear
+     * characteristics, Z = sqrt(rho G) [reading: the paper's HLLD resolves
+     * shear waves; this keeps the traction continuous so that a gas (Z = 0)
+     * transmits no shear].  Without shear stiffness on either side the
+     * tangential velocity is taken upwind by S*. */
+    double sig_t[3] = {0.0, 0.0, 0.0}, ut_star[3] = {0.0, 0.0, 0.0};
+    double ZL = sqrt(L.t.rho * L.t.G), ZR = sqrt(R.t.rho * R.t.G);
+    for (int a = 0; a < 3; a++) {
+        if (a == d) continue;
+        double sL = 2.0 * L.t.G * L.t.devH[a][d], sR = 2.0 * R.t.G * R.t.devH[a][d];
+        if (ZL + ZR > 0.0) {
+            sig_t[a] = (ZR * sL + ZL * sR + ZL * ZR * (R.t.u[a] - L.t.u[a])) / (ZL + ZR);
+            ut_star[a] = (ZL * L.t.u[a] + ZR * R.t.u[a] + sR - sL) / (ZL + ZR);
+        } else {
+            sig_t[a] = 0.0;
+            ut_star[a] = up->t.u[a];
+        }
+    }
     if (region == 0 || region == 3) {
         for (int v = nthermo_lo; v <= nthermo_hi; v++) F[v] = K->F[v];
     } else {
+        /* HLLC on the advective part with the normal traction; the
+         * tangential traction enters through its star value */
         double uK = K->t.u[d];
         double chi = (SK - uK) / (SK - Ss);
-        double Us[OMAXV];
+        double Us[OMAXV], Fa[OMAXV];
+        for (int v = nthermo_lo; v <= nthermo_hi; v++) Fa[v] = K->F[v];
+        double work_t = 0.0, work_ts = 0.0;
+        for (int a = 0; a < 3; a++) {
+            if (a == d) continue;
+            double sK = 2.0 * K->t.G * K->t.devH[a][d];
+            if (a < s->dim) Fa[s->imom + a] += sK;        /* remove -sigma_ad */
+            work_t += K->t.u[a] * sK;
+            work_ts += ut_star[a] * sig_t[a];
+        }
+        Fa[s->iE] += work_t;                              /* remove -u_t sigma_td */
         for (int l = 0; l < N; l++) Us[s->iar + l] = K->t.ar[l] * chi;
         for (int a = 0; a < s->dim; a++) Us[s->imom + a] = K->t.rho * chi * (a == d ? Ss : K->t.u[a]);
         double EK = K->t.rhoE / K->t.rho;
         Us[s->iE] = K->t.rho * chi * (EK + (Ss - uK) * (Ss + K->T / (K->t.rho * (SK - uK))));
-        for (int v = nthermo_lo; v <= nthermo_hi; v++) F[v] = K->F[v] + SK * (Us[v] - K->U[v]);
+        for (int v = nthermo_lo; v <= nthermo_hi; v++) F[v] = Fa[v] + SK * (Us[v] - K->U[v]);
+        for (int a = 0; a < s->dim; a++)
+            if (a != d) F[s->imom + a] -= sig_t[a];
+        F[s->iE] -= work_ts;
     }
     /* interface state at x/t = 0 */
-    oface *up = (Ss >= 0.0) ? &L : &R;
-    for (int a = 0; a < 3; a++) us[a] = up->t.u[a];
+    for (int a = 0; a < 3; a++) us[a] = (region == 0 || region == 3) ? K->t.u[a] : ut_star[a];
     if (region == 0) us[d] = uL;
     else if (region == 3) us[d] = uR;
     else us[d] = Ss;

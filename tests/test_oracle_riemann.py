@@ -176,3 +176,30 @@ def test_hllc_mirror_symmetry():
     np.testing.assert_allclose(F2[[0, 1, 2, 4]], -F1[[0, 1, 2, 4]], rtol=1e-12)
     assert F2[3] == pytest.approx(F1[3], rel=1e-12)
     assert us2[0] == pytest.approx(-us1[0], rel=1e-12)
+
+
+def test_gas_solid_face_transmits_no_shear():
+    """A sheared, sliding solid against gas at rest: the tangential traction at
+    the face is the gas's, zero, so the tangential momentum flux is only the
+    momentum carried by the mass flux, however large the solid's shear stress,
+    and the face tangential velocity is the solid's (free slip)."""
+    o = Oracle(2, (4, 4), (0.0, 0.0), (1.0, 1.0), [W.ALUMINIUM, W.AIR], solid=True)
+    air = np.array([0.0, 2700.0, 1.225, 0.0, 0.0, 1e5, 1.0, 0.0, 0.0, 1.0, 1.0, 0.0])
+    s = 0.01
+    al = np.array([1.0, 2700.0, 1.225, 400.0, 0.0, 1e5, 1.0, s, 0.0, 1.0, 1.0, 0.0])
+    F, us, _ = o.riemann(1, air, al)          # face normal to y, gas below, solid above
+    mass = F[1] + F[2]
+    ux_up = 0.0 if us[1] >= 0.0 else 400.0     # tangential velocity carried across
+    sig_xy = 2 * o.closure(o.prim_to_cons(al))["G"] * oracle_devH_xy(s)
+    assert abs(F[3] - mass * ux_up) <= 1e-9 * abs(sig_xy)
+    # the solid's shear stress is released by a shear wave: u* = u + sigma_xy / Z
+    Z = math.sqrt(2700.0 * o.closure(o.prim_to_cons(al))["G"])
+    assert us[0] == pytest.approx(400.0 + sig_xy / Z, rel=1e-12)
+    F2, _, _ = o.riemann(1, al, al)
+    assert F2[3] == pytest.approx(-sig_xy, rel=1e-9)  # the solid alone does carry shear
+
+
+def oracle_devH_xy(s):
+    import oracle as ORC
+    dH, _ = ORC.vbar_log(np.array([[1.0, s, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]))
+    return dH[0, 1]

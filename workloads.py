@@ -27,9 +27,10 @@ import numpy as np
 
 SEED_BASE = 1111806
 
-# Material records: the parameters each closure needs.
-AIR = dict(kind="ideal", gamma=1.4)
-WATER = dict(kind="stiffened", gamma=4.4, pinf=6.0e8)
+# Material records: the parameters each closure needs.  rho0 of a gas is the
+# reference density its phasic density takes where it is absent from a cell.
+AIR = dict(kind="ideal", gamma=1.4, rho0=1.225)
+WATER = dict(kind="stiffened", gamma=4.4, pinf=6.0e8, rho0=1000.0)
 # Aluminium-like Romenskii solid: rho0, K0, G0 and the yield stress are the
 # impact workload's; alpha, beta, Gamma0 are the paper's Table 1 aluminium row.
 ALUMINIUM = dict(kind="romenskii", rho0=2700.0, K0=76.0e9, G0=26.0e9, alpha=0.627,
