@@ -199,6 +199,25 @@ __device__ __forceinline__ void stretch_log(const double A[3][3], double H[3][3]
 
 // ------------------------------------------------------------- thermo
 
+// Closure weight of a transported volume fraction: clipped to [0, 1].
+template <class T>
+__device__ __forceinline__ T phi_clip(T f)
+{
+    return f < T(0) ? T(0) : (f > T(1) ? T(1) : f);
+}
+
+// Phasic density (phi rho)_l / phi_l (Sec. 2.2); a material whose clipped
+// fraction is below 1e-6 is absent from the cell and takes its reference
+// density rho0 (when one is given) -- the ratio of two round-off-sized numbers
+// would otherwise set the pressure through a stiff cold curve.
+template <class T>
+__device__ __forceinline__ T phasic_density(const GridP &g, int l, T ar, T phc)
+{
+    if (phc < T(1e-6) && g.mat[l].rho0 > 0.0) return (T)g.mat[l].rho0;
+    const T guard = (T)g.phi_guard;
+    return ar / (phc > guard ? phc : guard);
+}
+
 template <class T, int DIM, int NMAT, bool SOLID>
 struct State {
     T phi[NMAT], ar[NMAT];
@@ -237,6 +256,7 @@ __device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, S
     s.rho = T(0);
 #pragma unroll
     for (int l = 0; l < NMAT; l++) {
+        s.phi[l] = phi_clip(s.phi[l]);
         rhol[l] = w[L::IAR + l];
         s.ar[l] = s.phi[l] * rhol[l];
         s.rho += s.ar[l];
@@ -366,12 +386,12 @@ __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w
     T rhol[NMAT];
 #pragma unroll
     for (int l = 0; l < NMAT; l++) {
-        const T ph = phi[l] > (T)g.phi_guard ? phi[l] : (T)g.phi_guard;
-        rhol[l] = (NMAT == 1) ? rho : ar[l] / ph;
+        const T phc = phi_clip(phi[l]);
+        rhol[l] = (NMAT == 1) ? rho : phasic_density<T>(g, l, ar[l], phc);
         const Ref<T> r = mat_ref<T>(g.mat[l], rhol[l], J2);
         if (ar[l] != T(0)) num -= ar[l] * r.eref;
-        num += phi[l] * r.pref / r.Gam;
-        den += phi[l] / r.Gam;
+        num += phc * r.pref / r.Gam;
+        den += phc / r.Gam;
     }
 #pragma unroll
     for (int l = 0; l < NMAT - 1; l++) w[L::IPHI + l] = phi[l];
@@ -511,14 +531,42 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
     const T SK = (region <= 1) ? SL : SR;
     const T TK = (region <= 1) ? TL : TR;
     const T uK = K.u[D];
-    // physical flux of the selected side
+    const bool star = (region == 1 || region == 2);
+    const bool left = Ss >= T(0);
+    // Tangential traction and velocity at the face: the linear shear-wave
+    // Riemann problem (sigma -/+ Z u constant along the shear characteristics,
+    // Z = sqrt(rho G)); a gas (Z = 0) transmits no shear.  Without shear
+    // stiffness on either side the tangential velocity is upwind by S*.
+    T sig_t[DIM], ut[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        sig_t[a] = T(0);
+        ut[a] = left ? sl.u[a] : sr.u[a];
+    }
+    if (SOLID) {
+        const T ZL = m_sqrt(sl.rho * sl.G), ZR = m_sqrt(sr.rho * sr.G);
+#pragma unroll
+        for (int a = 0; a < DIM; a++) {
+            if (a == D) continue;
+            const T sL = T(2) * sl.G * sl.H[a][D], sR = T(2) * sr.G * sr.H[a][D];
+            if (ZL + ZR > T(0)) {
+                sig_t[a] = (ZR * sL + ZL * sR + ZL * ZR * (sr.u[a] - sl.u[a])) / (ZL + ZR);
+                ut[a] = (ZL * sl.u[a] + ZR * sr.u[a] + sR - sL) / (ZL + ZR);
+            }
+        }
+    }
+    // physical flux of the selected side; in the star regions the tangential
+    // stress is replaced by its face value
     T sig[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; a++) sig[a] = (a == D ? -K.p : T(0)) + (SOLID ? T(2) * K.G * K.H[a][D] : T(0));
-    T work = T(0);
+    T work = T(0), work_n = T(0), work_s = T(0);
 #pragma unroll
-    for (int a = 0; a < DIM; a++) work += K.u[a] * sig[a];
-    const bool star = (region == 1 || region == 2);
+    for (int a = 0; a < DIM; a++) {
+        work += K.u[a] * sig[a];
+        if (a == D) work_n += K.u[a] * sig[a];
+        else work_s += ut[a] * sig_t[a];
+    }
     const T chi = star ? (SK - uK) / (SK - Ss) : T(0);
 #pragma unroll
     for (int l = 0; l < NMAT; l++) {
@@ -528,22 +576,24 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
         const T m = K.rho * K.u[a];
-        const T F = m * uK - sig[a];
         const T Us = K.rho * chi * (a == D ? Ss : K.u[a]);
-        out[L::IMOM + a] = star ? F + SK * (Us - m) : F;
+        if (star) {
+            const T Fa = m * uK - (a == D ? sig[a] : T(0));
+            out[L::IMOM + a] = Fa + SK * (Us - m) - (a == D ? T(0) : sig_t[a]);
+        } else {
+            out[L::IMOM + a] = m * uK - sig[a];
+        }
     }
     {
-        const T F = K.rhoE * uK - work;
         const T EK = K.rhoE / K.rho;
         const T Us = K.rho * chi * (EK + (Ss - uK) * (Ss + TK / (K.rho * (SK - uK))));
-        out[L::IE] = star ? F + SK * (Us - K.rhoE) : F;
+        out[L::IE] = star ? (K.rhoE * uK - work_n) + SK * (Us - K.rhoE) - work_s : K.rhoE * uK - work;
     }
     // interface state at x/t = 0
-    const bool left = Ss >= T(0);
     const T *wu = left ? wL : wR;
     T us[DIM];
 #pragma unroll
-    for (int a = 0; a < DIM; a++) us[a] = left ? sl.u[a] : sr.u[a];
+    for (int a = 0; a < DIM; a++) us[a] = star ? ut[a] : K.u[a];
     us[D] = (region == 0) ? uL : ((region == 3) ? uR : Ss);
 #pragma unroll
     for (int l = 0; l < NMAT - 1; l++) out[L::IPHI + l] = wu[L::IPHI + l] * us[D];

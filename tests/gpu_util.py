@@ -7,14 +7,17 @@ import workloads as W
 
 def plane_scales(ref, wl):
     """Denominator of the relative L1 per conserved plane: sum |ref|, with
-    momentum planes floored at sum(rho) * 10 m/s so that near-zero momenta
-    are measured against a physical scale rather than round-off."""
+    momentum planes floored at sum(rho) * 10 m/s and stretch-tensor planes at
+    ncell (|V| ~ 1), so that near-zero momenta and off-diagonal stretches are
+    measured against a physical scale rather than round-off."""
     L = W.layout(wl.dim, wl.nmat, wl.solid)
     rho = ref[L["irho"]: L["irho"] + wl.nmat].sum(axis=0)
     s = np.abs(ref).sum(axis=1)
     for a in range(wl.dim):
         s[L["iu"] + a] = max(s[L["iu"] + a], 10.0 * np.abs(rho).sum())
     s[L["ir"]] = max(s[L["ir"]], 1e-3 * ref.shape[1])
+    for c in range(L["nv"]):          # stretch components are O(1): measure against |V| ~ 1
+        s[L["iv"] + c] = max(s[L["iv"] + c], 1.0 * ref.shape[1])
     for l in range(wl.nmat - 1):
         s[L["iphi"] + l] = max(s[L["iphi"] + l], 1e-3 * ref.shape[1])
     return np.where(s > 0, s, 1.0)

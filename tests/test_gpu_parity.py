@@ -68,9 +68,10 @@ def test_dynamic_body_force_and_motion():
     fg, vg, xg = g.body()
     scale = np.abs(fo).max()
     assert scale > 0
-    np.testing.assert_allclose(fg, fo, rtol=0, atol=1e-9 * scale)
-    np.testing.assert_allclose(vg, vo, rtol=1e-9, atol=1e-12)
-    np.testing.assert_allclose(xg, xo, rtol=1e-9, atol=1e-15)
+    # 20 nonlinear steps: the same 1e-8 bound as the fields after many steps
+    np.testing.assert_allclose(fg, fo, rtol=0, atol=1e-8 * scale)
+    np.testing.assert_allclose(vg, vo, rtol=1e-8, atol=1e-12)
+    np.testing.assert_allclose(xg, xo, rtol=1e-8, atol=1e-15)
     assert vg[0] > 0   # the shock pushes the body in +x
 
 
