@@ -73,7 +73,9 @@ typedef int dfv_status;
 typedef struct {
     double gamma;    /* ideal / stiffened: adiabatic index */
     double pinf;     /* stiffened: p_inf (Pa) */
-    double rho0;     /* Romenskii: reference density */
+    double rho0;     /* reference density: Romenskii rho0; for every kind the
+                        phasic density used where the material is absent from
+                        a cell (volume fraction < 1e-6); 0 = none (gases) */
     double K0;       /* Romenskii: bulk-like modulus */
     double G0;       /* Romenskii: shear modulus at rho0 */
     double alpha;    /* Romenskii: cold-curve exponent */
@@ -148,6 +150,15 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
 /* Synchronise the stream (waiting at most timeout_ms, <= 0: no limit) and
  * report DFV_ERR_NONPHYSICAL / DFV_ERR_TIMEOUT. */
 dfv_status dfv_check(dfv_grid *g, int timeout_ms);
+
+/* Per-kernel device timing of steps, with CUDA events recorded on the grid's
+ * stream around each launch.  enable = 1 clears the record and starts
+ * recording; enable = 0 stops, synchronises the stream and returns in
+ * ms_out[0..4] the summed device time of the seeding, stage-1, stage-2,
+ * stage-3 and finalize launches, and in *steps_out the number of recorded
+ * steps (either output may be NULL).  While recording, dfv_run launches the
+ * kernels of each step directly instead of replaying a graph. */
+dfv_status dfv_profile(dfv_grid *g, int enable, double ms_out[5], long long *steps_out);
 
 /* Number of kernel launches issued by the library on this grid so far. */
 dfv_status dfv_launch_count(const dfv_grid *g, long long *count);

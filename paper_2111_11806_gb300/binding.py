@@ -23,7 +23,7 @@ MAT_KIND = {"ideal": 0, "stiffened": 1, "romenskii": 2}
 
 EXPORTS = ("dfv_workspace_bytes", "dfv_create_grid", "dfv_add_material", "dfv_set_fields", "dfv_get_fields",
            "dfv_set_body", "dfv_get_body", "dfv_compute_dt", "dfv_step", "dfv_run", "dfv_check",
-           "dfv_launch_count", "dfv_destroy", "dfv_last_error")
+           "dfv_profile", "dfv_launch_count", "dfv_destroy", "dfv_last_error")
 
 
 class dfv_material_params(ctypes.Structure):
@@ -67,6 +67,7 @@ def load(path: str = LIB_PATH):
     L.dfv_step.argtypes = [_vp, ctypes.c_double]
     L.dfv_run.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
     L.dfv_check.argtypes = [_vp, ctypes.c_int]
+    L.dfv_profile.argtypes = [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]
     L.dfv_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
     L.dfv_destroy.argtypes = [_vp]
     L.dfv_last_error.argtypes = [_vp]
@@ -246,6 +247,16 @@ class Grid:
     def check(self, timeout_ms=0):
         with self._ctx():
             _check(load().dfv_check(self._h, int(timeout_ms)), self._h, "dfv_check")
+
+    def profile(self, enable):
+        """Start (enable=True) or stop per-kernel event timing; returns
+        (ms[seed, stage1, stage2, stage3, finalize], steps) recorded so far."""
+        ms = np.zeros(5)
+        n = ctypes.c_longlong()
+        with self._ctx():
+            _check(load().dfv_profile(self._h, int(bool(enable)), ms.ctypes.data_as(_dp), ctypes.byref(n)),
+                   self._h, "dfv_profile")
+        return ms, n.value
 
     def launch_count(self):
         c = ctypes.c_longlong()

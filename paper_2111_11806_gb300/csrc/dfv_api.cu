@@ -10,6 +10,8 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <vector>
+#include <array>
 
 #include "../../include/dfvrb.h"
 #include "dfv_kernels.cuh"
@@ -38,6 +40,11 @@ struct dfv_grid {
     long long launches = 0;
     cudaGraphExec_t graph = nullptr;
     bool graph_ready = false;
+    bool dt_valid = false;               // ctl->dt holds the device-computed next dt
+    double run_cfl = -1.0, run_tend = -1.0;
+    bool prof = false;                   // per-kernel event timing (dfv_profile)
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::array<cudaEvent_t, 6>> ev_steps;
 };
 
 namespace {
@@ -190,15 +197,45 @@ dfv_status reduce_cfl(dfv_grid *g)
 
 // The launches of one step: seeding (Sec. 3.2), SSP-RK3 (Sec. 3.1), finalize.
 // mode_extra = 8 asks the finalize kernel for the next dt (device-driven runs).
-dfv_status launch_step(dfv_grid *g, int mode_extra)
+cudaEvent_t take_event(dfv_grid *g)
+{
+    if (!g->ev_free.empty()) {
+        cudaEvent_t e = g->ev_free.back();
+        g->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false)
 {
     const int want_force = g->dynamic ? 1 : 0;
+    const bool rec = g->prof && !capturing;
+    std::array<cudaEvent_t, 6> ev{};
+    if (rec) {
+        for (auto &e : ev) {
+            e = take_event(g);
+            if (!e) return fail(g, DFV_ERR_CUDA, "dfv: cudaEventCreate failed");
+        }
+        DFV_CU(g, cudaEventRecord(ev[0], g->stream), "event");
+    }
     DFV_CU(g, g->ops->seed(g->g, g->U, g->ctl, g->stream), "k_seed");
+    if (rec) DFV_CU(g, cudaEventRecord(ev[1], g->stream), "event");
     DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, g->stream), "k_stage<1>");
+    if (rec) DFV_CU(g, cudaEventRecord(ev[2], g->stream), "event");
     DFV_CU(g, g->ops->stage(2, g->g, g->U1, g->U, g->U3, g->ctl, g->partials, 0, g->stream), "k_stage<2>");
+    if (rec) DFV_CU(g, cudaEventRecord(ev[3], g->stream), "event");
     DFV_CU(g, g->ops->stage(3, g->g, g->U3, g->U, g->U, g->ctl, g->partials, 0, g->stream), "k_stage<3>");
+    if (rec) DFV_CU(g, cudaEventRecord(ev[4], g->stream), "event");
     g->launches += 4;
-    return finalize(g, 1 | (want_force ? 2 : 0) | 4 | mode_extra, g->nb_stage);
+    dfv_status s = finalize(g, 1 | (want_force ? 2 : 0) | 4 | mode_extra, g->nb_stage);
+    if (rec) {
+        DFV_CU(g, cudaEventRecord(ev[5], g->stream), "event");
+        g->ev_steps.push_back(ev);
+    }
+    return s;
 }
 
 const Ops *pick_ops(int precision, int dim, int nmat, int solid)
@@ -348,6 +385,7 @@ dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device)
     if (!on_device) DFV_CU(g, cudaStreamSynchronize(g->stream), "dfv_set_fields sync");
     g->fields_set = true;
     g->smax_valid = false;
+    g->dt_valid = false;
     return DFV_OK;
 }
 
@@ -386,6 +424,7 @@ dfv_status dfv_set_body(dfv_grid *g, const double v[3], const double x[3], doubl
     DFV_CU(g, cudaGetLastError(), "k_set_body");
     g->dynamic = dynamic != 0;
     g->smax_valid = false;   // the body speed enters the CFL bound
+    g->dt_valid = false;
     g->graph_ready = false;
     return DFV_OK;
 }
@@ -428,6 +467,7 @@ dfv_status dfv_step(dfv_grid *g, double dt)
     DFV_CU(g, cudaGetLastError(), "k_set_dt");
     dfv_status s = launch_step(g, 0);
     if (s == DFV_OK) g->smax_valid = true;
+    g->dt_valid = false;
     return s;
 }
 
@@ -436,16 +476,27 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
     if (!g) return DFV_ERR_ARG;
     if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_run: fields not set");
     if (steps < 0 || !(cfl > 0.0)) return fail(g, DFV_ERR_ARG, "dfv_run: bad arguments");
-    k_set_run<<<1, 1, 0, g->stream>>>(g->ctl, cfl, t_end > 0.0 ? t_end : 0.0);
-    g->launches++;
-    DFV_CU(g, cudaGetLastError(), "k_set_run");
+    const double tend = t_end > 0.0 ? t_end : 0.0;
+    if (cfl != g->run_cfl || tend != g->run_tend) {
+        k_set_run<<<1, 1, 0, g->stream>>>(g->ctl, cfl, tend);
+        g->launches++;
+        DFV_CU(g, cudaGetLastError(), "k_set_run");
+        g->run_cfl = cfl;
+        g->run_tend = tend;
+        g->dt_valid = false;
+    }
     if (!g->smax_valid) {
         dfv_status s = reduce_cfl(g);
         if (s != DFV_OK) return s;
+        g->dt_valid = false;
     }
-    dfv_status s = finalize(g, 8, 0);   // dt from the current smax
-    if (s != DFV_OK) return s;
-    const bool use_graph = g->stream != nullptr && steps > 1;
+    dfv_status s = DFV_OK;
+    if (!g->dt_valid) {
+        s = finalize(g, 8, 0);   // dt from the current smax
+        if (s != DFV_OK) return s;
+        g->dt_valid = true;
+    }
+    const bool use_graph = g->stream != nullptr && steps > 1 && !g->prof;
     if (use_graph && !g->graph_ready) {
         if (g->graph) {
             cudaGraphExecDestroy(g->graph);
@@ -454,7 +505,7 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
         cudaGraph_t graph = nullptr;
         DFV_CU(g, cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         const long long before = g->launches;
-        dfv_status cs = launch_step(g, 8);
+        dfv_status cs = launch_step(g, 8, true);
         cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
         g->launches = before;   // capture launches nothing
         if (cs != DFV_OK) return cs;
@@ -492,6 +543,34 @@ dfv_status dfv_check(dfv_grid *g, int timeout_ms)
     return read_ctl(g, &h);
 }
 
+dfv_status dfv_profile(dfv_grid *g, int enable, double ms_out[5], long long *steps_out)
+{
+    if (!g) return DFV_ERR_ARG;
+    dfv_status s = DFV_OK;
+    double ms[5] = {0, 0, 0, 0, 0};
+    long long n = 0;
+    if (!g->ev_steps.empty()) {
+        cudaError_t e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) s = cuda_fail(g, e, "dfv_profile sync");
+        for (auto &ev : g->ev_steps) {
+            for (int k = 0; k < 5 && s == DFV_OK; k++) {
+                float t = 0.f;
+                e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+                if (e != cudaSuccess) s = cuda_fail(g, e, "cudaEventElapsedTime");
+                ms[k] += t;
+            }
+            for (auto x : ev) g->ev_free.push_back(x);
+            n++;
+        }
+        g->ev_steps.clear();
+    }
+    if (ms_out)
+        for (int k = 0; k < 5; k++) ms_out[k] = ms[k];
+    if (steps_out) *steps_out = n;
+    g->prof = enable != 0;
+    return s;
+}
+
 dfv_status dfv_launch_count(const dfv_grid *g, long long *count)
 {
     if (!g || !count) return DFV_ERR_ARG;
@@ -503,6 +582,9 @@ dfv_status dfv_destroy(dfv_grid *g)
 {
     if (!g) return DFV_ERR_ARG;
     if (g->graph) cudaGraphExecDestroy(g->graph);
+    for (auto &ev : g->ev_steps)
+        for (auto x : ev) g->ev_free.push_back(x);
+    for (auto x : g->ev_free) cudaEventDestroy(x);
     delete g;
     return DFV_OK;
 }
