@@ -54,6 +54,7 @@ typedef int dfv_status;
 #define DFV_ERR_TIMEOUT (-4)      /* a host wait exceeded its time limit */
 #define DFV_ERR_WORKSPACE (-5)    /* workspace too small or misaligned */
 #define DFV_ERR_UNSUPPORTED (-6)  /* combination not built (e.g. 3-D solid) */
+#define DFV_ERR_TOO_LARGE (-7)    /* grid larger than a fixed-size scratch allows */
 
 #define DFV_FP64 0       /* plain FP64 everywhere */
 #define DFV_FP32 1       /* FP32 storage, reconstruction and fluxes; FP64 in
@@ -164,6 +165,35 @@ dfv_status dfv_profile(dfv_grid *g, int enable, double ms_out[5], long long *ste
 dfv_status dfv_launch_count(const dfv_grid *g, long long *count);
 
 dfv_status dfv_destroy(dfv_grid *g);
+
+/* Largest grid (cells) that dfv_compute_dt_noalloc accepts. */
+#define DFV_NOALLOC_MAX_CELLS (16LL * 1024 * 1024)
+
+/* The CFL time step of a conserved state that the caller already holds on the
+ * device, computed without allocating anything -- for callers that cannot
+ * call cudaMalloc (for example a solver embedded in a host code that owns and
+ * pools all device memory, or one that must not allocate while other work is
+ * running).  The paper has no counterpart: it is a packaging of the CFL
+ * reduction of dfv_compute_dt, returning the same dt for the same state.
+ *   dim, n, lo, hi, precision, opt: as for dfv_create_grid (bc not needed);
+ *   kinds[l], params[l]: the opt->nmat materials, as for dfv_add_material;
+ *   cons: device pointer to the conserved planes (layout above) stored as
+ *     doubles (DFV_FP64) or floats (DFV_FP32), plane_pitch elements apart
+ *     (plane_pitch >= ncell);
+ *   v_body: body velocity (the bound also covers it; NULL = at rest);
+ *   dt_out: host pointer, receives cfl / max_cells sum_d (|u_d| + c)/dx_d.
+ * Scratch: a fixed device array inside the library (DFV_NOALLOC_MAX_CELLS/256
+ * block partials and a small control block), held by every device that loads
+ * the library until the process exits; larger grids return
+ * DFV_ERR_TOO_LARGE.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls on a device share the array: calls whose work overlaps
+ * on the GPU (other threads, other streams) race and must be serialised by the
+ * caller.  The call synchronises `stream` (a cudaStream_t or NULL). */
+dfv_status dfv_compute_dt_noalloc(int dim, const int n[3], const double lo[3], const double hi[3], int precision,
+                                  const dfv_options *opt, const int kinds[], const dfv_material_params params[],
+                                  const void *cons, long long plane_pitch, const double v_body[3], double cfl,
+                                  void *stream, double *dt_out);
 
 const char *dfv_last_error(const dfv_grid *g);
 

@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(_HERE, "libdfvrb.so")
 
 DFV_OK = 0
 DFV_ERR = {-1: "DFV_ERR_ARG", -2: "DFV_ERR_CUDA", -3: "DFV_ERR_NONPHYSICAL", -4: "DFV_ERR_TIMEOUT",
-           -5: "DFV_ERR_WORKSPACE", -6: "DFV_ERR_UNSUPPORTED"}
+           -5: "DFV_ERR_WORKSPACE", -6: "DFV_ERR_UNSUPPORTED", -7: "DFV_ERR_TOO_LARGE"}
+DFV_NOALLOC_MAX_CELLS = 16 * 1024 * 1024
 DFV_FP64, DFV_FP32 = 0, 1
 DFV_BC_TRANSMISSIVE, DFV_BC_PERIODIC = 0, 1
 DFV_FIELDS_CONSERVED, DFV_FIELDS_PRIMITIVE = 0, 1
@@ -23,7 +24,7 @@ MAT_KIND = {"ideal": 0, "stiffened": 1, "romenskii": 2}
 
 EXPORTS = ("dfv_workspace_bytes", "dfv_create_grid", "dfv_add_material", "dfv_set_fields", "dfv_get_fields",
            "dfv_set_body", "dfv_get_body", "dfv_compute_dt", "dfv_step", "dfv_run", "dfv_check",
-           "dfv_profile", "dfv_launch_count", "dfv_destroy", "dfv_last_error")
+           "dfv_profile", "dfv_launch_count", "dfv_destroy", "dfv_last_error", "dfv_compute_dt_noalloc")
 
 
 class dfv_material_params(ctypes.Structure):
@@ -70,6 +71,9 @@ def load(path: str = LIB_PATH):
     L.dfv_profile.argtypes = [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]
     L.dfv_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
     L.dfv_destroy.argtypes = [_vp]
+    L.dfv_compute_dt_noalloc.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.c_int, ctypes.POINTER(dfv_options),
+                                         _ip, ctypes.POINTER(dfv_material_params), _vp, ctypes.c_longlong, _dp,
+                                         ctypes.c_double, _vp, _dp]
     L.dfv_last_error.argtypes = [_vp]
     L.dfv_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -114,6 +118,28 @@ def workspace_bytes(dim, n, nmat, solid, precision) -> int:
     _check(load().dfv_workspace_bytes(dim, n3, nmat, int(bool(solid)), precision, ctypes.byref(out)),
            what="dfv_workspace_bytes")
     return out.value
+
+
+def compute_dt_noalloc(dim, n, lo, hi, materials, cons_ptr, plane_pitch, cfl, precision=DFV_FP64, solid=False,
+                       v_body=(0.0, 0.0, 0.0), stream=0, use_thinc=True, thinc_beta=1.6):
+    """dfv_compute_dt_noalloc: the CFL dt of a conserved state the caller
+    holds on the device (cons_ptr: device address of the planes, plane_pitch
+    elements apart), computed with the library's fixed scratch array instead
+    of an allocated workspace -- for callers that cannot allocate device
+    memory.  Calls that overlap on the GPU share that scratch and race."""
+    L = load()
+    n3 = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - dim)))
+    lo3, hi3 = _d3(lo), _d3(hi)
+    opt = dfv_options(len(materials), int(bool(solid)), int(bool(use_thinc)), float(thinc_beta))
+    kinds = (ctypes.c_int * len(materials))(*[MAT_KIND[m["kind"]] for m in materials])
+    params = (dfv_material_params * len(materials))(*[material_struct(m) for m in materials])
+    vb = _d3(v_body)
+    dt = ctypes.c_double()
+    _check(L.dfv_compute_dt_noalloc(dim, n3, lo3.ctypes.data_as(_dp), hi3.ctypes.data_as(_dp), precision,
+                                    ctypes.byref(opt), kinds, params, _vp(cons_ptr), int(plane_pitch),
+                                    vb.ctypes.data_as(_dp), float(cfl), _vp(stream), ctypes.byref(dt)),
+           None, "dfv_compute_dt_noalloc")
+    return dt.value
 
 
 class Grid:
