@@ -328,6 +328,7 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
     p.sinh_b = std::sinh(p.beta);
     p.tanh_b = std::tanh(p.beta);
     p.phi_guard = 1e-14;
+    dfv::finish_params(p);
 
     cudaError_t e = ops->prepare();
     if (e != cudaSuccess) {
@@ -365,6 +366,7 @@ dfv_status dfv_add_material(dfv_grid *g, int kind, const dfv_material_params *m,
     p.beta = m->beta;
     p.Gamma0 = m->Gamma0;
     p.sigY = m->sigma_y;
+    dfv::finish_params(g->g);
     if (id_out) *id_out = g->nmat;
     g->nmat++;
     g->graph_ready = false;

@@ -23,6 +23,26 @@ struct MatP {
     double sigY;
 };
 
+// Material and grid constants in the compute precision, derived on the host
+// (finish_params) so that the FP32 form does no double-precision arithmetic
+// or conversion in its face and cell loops.
+template <class T>
+struct MatC {
+    int kind;
+    T Gam;          // Grueneisen coefficient (gamma - 1 for the gases)
+    T pref0;        // constant p_ref of the gases (-gamma p_inf, 0)
+    T rho0, K0, G0, alpha, beta, sigY;
+    int has_rho0;
+};
+
+template <class T>
+struct GridC {
+    T lo[3], dx[3], inv_dx[3];
+    T dxmin, dV;
+    T beta, cosh_b, sinh_b, tanh_b;   // THINC constants
+    T phi_guard;
+};
+
 struct GridP {
     int dim;
     int n[3];
@@ -34,7 +54,63 @@ struct GridP {
     int use_thinc;
     double beta, cosh_b, sinh_b, tanh_b;   // THINC constants
     double phi_guard;
+    MatC<double> mc_d[2];
+    MatC<float> mc_f[2];
+    GridC<double> gc_d;
+    GridC<float> gc_f;
 };
+
+template <class T>
+__host__ inline void fill_consts(const GridP &g, MatC<T> *mc, GridC<T> &gc)
+{
+    for (int l = 0; l < 2; l++) {
+        const MatP &m = g.mat[l];
+        mc[l].kind = m.kind;
+        mc[l].Gam = (T)(m.kind == 2 ? m.Gamma0 : m.gamma - 1.0);
+        mc[l].pref0 = (m.kind == 1) ? (T)(-m.gamma * m.pinf) : T(0);
+        mc[l].rho0 = (T)m.rho0;
+        mc[l].K0 = (T)m.K0;
+        mc[l].G0 = (T)m.G0;
+        mc[l].alpha = (T)m.alpha;
+        mc[l].beta = (T)m.beta;
+        mc[l].sigY = (T)m.sigY;
+        mc[l].has_rho0 = m.rho0 > 0.0;
+    }
+    for (int d = 0; d < 3; d++) {
+        gc.lo[d] = (T)g.lo[d];
+        gc.dx[d] = (T)g.dx[d];
+        gc.inv_dx[d] = (T)g.inv_dx[d];
+    }
+    gc.dxmin = (T)g.dxmin;
+    gc.dV = (T)g.dV;
+    gc.beta = (T)g.beta;
+    gc.cosh_b = (T)g.cosh_b;
+    gc.sinh_b = (T)g.sinh_b;
+    gc.tanh_b = (T)g.tanh_b;
+    gc.phi_guard = (T)g.phi_guard;
+}
+
+// Derive the per-precision constants from the double parameters; call after
+// every change of the grid or of a material.
+__host__ inline void finish_params(GridP &g)
+{
+    fill_consts<double>(g, g.mc_d, g.gc_d);
+    fill_consts<float>(g, g.mc_f, g.gc_f);
+}
+
+template <class T>
+__device__ __forceinline__ const MatC<T> &matc(const GridP &g, int l);
+template <>
+__device__ __forceinline__ const MatC<double> &matc<double>(const GridP &g, int l) { return g.mc_d[l]; }
+template <>
+__device__ __forceinline__ const MatC<float> &matc<float>(const GridP &g, int l) { return g.mc_f[l]; }
+
+template <class T>
+__device__ __forceinline__ const GridC<T> &gridc(const GridP &g);
+template <>
+__device__ __forceinline__ const GridC<double> &gridc<double>(const GridP &g) { return g.gc_d; }
+template <>
+__device__ __forceinline__ const GridC<float> &gridc<float>(const GridP &g) { return g.gc_f; }
 
 // Device-resident control block: time step, time, body state and the error
 // word.  Kernels read dt and the body velocity from here so that a whole step
@@ -119,29 +195,29 @@ struct Ref {
 // K0/(2 rho alpha^2)(x^alpha - 1)^2 as printed, shear energy G J^2/rho with
 // G = G0 x^(beta+1), x = rho/rho0, and p_ref = rho^2 de_ref/drho).
 template <class T>
-__device__ __forceinline__ Ref<T> mat_ref(const MatP &m, T rho, T J2)
+__device__ __forceinline__ Ref<T> mat_ref(const MatC<T> &m, T rho, T J2)
 {
     Ref<T> r;
     if (m.kind == 2) {
-        const T al = (T)m.alpha, be = (T)m.beta, K0 = (T)m.K0, rho0 = (T)m.rho0;
+        const T al = m.alpha, be = m.beta, K0 = m.K0, rho0 = m.rho0;
         const T x = rho / rho0;
         const T xa = m_pow(x, al);
         const T xm1 = xa - T(1);
         const T ec = K0 / (T(2) * rho * al * al) * xm1 * xm1;
         const T pc = -K0 / (T(2) * al * al) * xm1 * xm1 + (K0 / al) * xm1 * xa;
         const T dpc = (K0 / rho0) * (xa / x) * (T(2) * xa - T(1) - xm1 / al);
-        const T G = (T)m.G0 * m_pow(x, be + T(1));
+        const T G = m.G0 * m_pow(x, be + T(1));
         const T ps = be * G * J2;
-        r.Gam = (T)m.Gamma0;
+        r.Gam = m.Gam;
         r.eref = ec + G * J2 / rho;
         r.pref = pc + ps;
         r.deref = (pc + ps) / (rho * rho);
         r.dpref = dpc + be * (be + T(1)) * G * J2 / rho;
         r.G = G;
     } else {
-        r.Gam = (T)(m.gamma - 1.0);
+        r.Gam = m.Gam;
         r.eref = T(0);
-        r.pref = (m.kind == 1) ? (T)(-m.gamma * m.pinf) : T(0);
+        r.pref = m.pref0;
         r.deref = T(0);
         r.dpref = T(0);
         r.G = T(0);
@@ -213,8 +289,9 @@ __device__ __forceinline__ T phi_clip(T f)
 template <class T>
 __device__ __forceinline__ T phasic_density(const GridP &g, int l, T ar, T phc)
 {
-    if (phc < T(1e-6) && g.mat[l].rho0 > 0.0) return (T)g.mat[l].rho0;
-    const T guard = (T)g.phi_guard;
+    const MatC<T> &m = matc<T>(g, l);
+    if (phc < T(1e-6) && m.has_rho0) return m.rho0;
+    const T guard = gridc<T>(g).phi_guard;
     return ar / (phc > guard ? phc : guard);
 }
 
@@ -279,12 +356,12 @@ __device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, S
     T rhoe = T(0), den = T(0), Gn = T(0), Sn = T(0), Yn = T(0);
 #pragma unroll
     for (int l = 0; l < NMAT; l++) {
-        const Ref<T> r = mat_ref<T>(g.mat[l], rhol[l], J2);
+        const Ref<T> r = mat_ref<T>(matc<T>(g, l), rhol[l], J2);
         if (s.ar[l] != T(0)) rhoe += s.ar[l] * r.eref;
         rhoe += s.phi[l] * (s.p - r.pref) / r.Gam;
         den += s.phi[l] / r.Gam;
         Gn += s.phi[l] * r.G / r.Gam;
-        Sn += s.phi[l] * (T)g.mat[l].sigY / r.Gam;
+        Sn += s.phi[l] * matc<T>(g, l).sigY / r.Gam;
         const T rl = rhol[l];
         const T a2 = r.Gam * s.p / rl + (s.p - r.pref) / rl + r.dpref - r.Gam * rl * r.deref;
         const T c2l = a2 + T(4) / T(3) * r.G / rl;
@@ -388,7 +465,7 @@ __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w
     for (int l = 0; l < NMAT; l++) {
         const T phc = phi_clip(phi[l]);
         rhol[l] = (NMAT == 1) ? rho : phasic_density<T>(g, l, ar[l], phc);
-        const Ref<T> r = mat_ref<T>(g.mat[l], rhol[l], J2);
+        const Ref<T> r = mat_ref<T>(matc<T>(g, l), rhol[l], J2);
         if (ar[l] != T(0)) num -= ar[l] * r.eref;
         num += phc * r.pref / r.Gam;
         den += phc / r.Gam;
@@ -461,9 +538,10 @@ __device__ __forceinline__ bool thinc(const GridP &g, T qm, T q0, T qp, T &fm, T
     const T th = (qp - qm) >= T(0) ? T(1) : T(-1);
     const T C = (q0 - qmin) / dq;
     if (!(C > T(1e-8) && C < T(1) - T(1e-8))) return false;
-    const T B = m_exp(th * (T)g.beta * (T(2) * C - T(1)));
-    const T ty = ((T)g.cosh_b - B) / (T)g.sinh_b;
-    const T tb = (T)g.tanh_b;
+    const GridC<T> &gc = gridc<T>(g);
+    const T B = m_exp(th * gc.beta * (T(2) * C - T(1)));
+    const T ty = (gc.cosh_b - B) / gc.sinh_b;
+    const T tb = gc.tanh_b;
     const T t1 = (tb - ty) / (T(1) - tb * ty);
     fm = qmin + T(0.5) * dq * (T(1) - th * ty);
     fp = qmin + T(0.5) * dq * (T(1) + th * t1);

@@ -182,7 +182,7 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
         const int fl = (lz * EY + ly) * EX + lx;
         const int fr = fl + (D == 0 ? 1 : (D == 1 ? EX : EX * EY));
         const int bcell = ((lz + B::HZ) * B::BY + (ly + B::HY)) * B::BX + (lx + B::HX);
-        const R inv = (R)g.inv_dx[D];
+        const R inv = gridc<R>(g).inv_dx[D];
         const R dus = sF[L::NVAR * B::MAXF + fr] - sF[L::NVAR * B::MAXF + fl];
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) {
@@ -290,25 +290,27 @@ __global__ void __launch_bounds__(Tile<DIM>::THREADS) k_stage(StageArgs a, GridP
             atomicOr(&a.ctl->err, (unsigned)ERR_STATE);
         if (STAGE == 1 && a.want_force) {
             // pressure force: p (grad r) dV with central differences (Youngs)
+            const GridC<R> &gc = gridc<R>(g);
             const R p = sW[L::IE * B::N + bcell];
 #pragma unroll
             for (int d = 0; d < DIM; d++) {
                 const int sd = B::stride(d);
-                const R gr = (sW[L::IR * B::N + bcell + sd] - sW[L::IR * B::N + bcell - sd]) / (R(2) * (R)g.dx[d]);
-                red[1 + d] = (double)p * (double)gr * g.dV;
+                const R gr = (sW[L::IR * B::N + bcell + sd] - sW[L::IR * B::N + bcell - sd]) / (R(2) * gc.dx[d]);
+                red[1 + d] = (double)(p * gr * gc.dV);
             }
         }
         if (STAGE == 3) {
+            // CFL wave speed of the new state, in the compute precision
             R w[L::NVAR];
             cons_to_prim<R, DIM, NMAT, SOLID>(g, o, w);
             State<R, DIM, NMAT, SOLID> s;
             state_from_prim<R, DIM, NMAT, SOLID>(g, w, s);
             if (!(s.c2 > R(0))) atomicOr(&a.ctl->err, (unsigned)ERR_SOUND);
-            const double cs = sqrt((double)s.c2);
-            double sum = 0.0;
+            const R cs = m_sqrt(s.c2);
+            R sum = R(0);
 #pragma unroll
-            for (int d = 0; d < DIM; d++) sum += (fabs((double)s.u[d]) + cs) / g.dx[d];
-            red[0] = sum;
+            for (int d = 0; d < DIM; d++) sum += (m_abs(s.u[d]) + cs) / gridc<R>(g).dx[d];
+            red[0] = (double)sum;
         }
     }
     if (STAGE == 3 || (STAGE == 1 && a.want_force)) {
@@ -335,22 +337,24 @@ __global__ void __launch_bounds__(Tile<DIM>::THREADS) k_stage(StageArgs a, GridP
 // domain (wrapped if periodic) with r < 0.5 is interpolated multilinearly in
 // the primitives, and u <- (I - 2nn^T) u + 2 (v_r.n) n, V <- (I - 2nn^T) V (I - 2nn^T).
 // Only r < 0.5 cells are read and only r > 0.5 cells written, so the update is
-// independent of thread order.  Evaluated in FP64.
+// independent of thread order.  Evaluated in the storage precision (FP64
+// closures below phi = 1e-6 as everywhere in the FP32 form).
 template <class R, int DIM, int NMAT, bool SOLID>
 __global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     R *U = reinterpret_cast<R *>(Uv);
+    const GridC<R> &gc = gridc<R>(g);
     const long long P = g.pitch;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
-        const double rc = (double)U[L::IR * P + c];
-        if (!(rc > 0.5)) continue;
+        const R rc = U[L::IR * P + c];
+        if (!(rc > R(0.5))) continue;
         int ijk[3];
         ijk[0] = (int)(c % g.n[0]);
         ijk[1] = (int)((c / g.n[0]) % g.n[1]);
         ijk[2] = (int)(c / ((long long)g.n[0] * g.n[1]));
-        double gr[3] = {0.0, 0.0, 0.0};
+        R gr[3] = {R(0), R(0), R(0)};
 #pragma unroll
         for (int d = 0; d < DIM; d++) {
             int lo[3] = {ijk[0], ijk[1], ijk[2]}, hi[3] = {ijk[0], ijk[1], ijk[2]};
@@ -358,32 +362,32 @@ __global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
             hi[d] = map_idx(ijk[d] + 1, g.n[d], g.periodic[d]);
             const long long cl = lo[0] + (long long)g.n[0] * (lo[1] + (long long)g.n[1] * lo[2]);
             const long long ch = hi[0] + (long long)g.n[0] * (hi[1] + (long long)g.n[1] * hi[2]);
-            gr[d] = ((double)U[L::IR * P + ch] - (double)U[L::IR * P + cl]) / (2.0 * g.dx[d]);
+            gr[d] = (U[L::IR * P + ch] - U[L::IR * P + cl]) / (R(2) * gc.dx[d]);
         }
-        const double gn = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-        if (!(gn * g.dxmin > 1e-10)) continue;
-        const double nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
-        double wi[L::NVAR];
+        const R gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+        if (!(gn * gc.dxmin > R(1e-10))) continue;
+        const R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
+        R wi[L::NVAR];
         bool found = false;
         for (int step = 0; step < 7 && !found; step++) {
-            const double sd = (1.0 + 0.5 * step) * g.dxmin;
+            const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
             int base[3] = {0, 0, 0};
-            double fr[3] = {0.0, 0.0, 0.0};
+            R fr[3] = {R(0), R(0), R(0)};
 #pragma unroll
             for (int d = 0; d < DIM; d++) {
-                const double xp = g.lo[d] + (ijk[d] + 0.5) * g.dx[d] + sd * nv[d];
-                const double fi = (xp - g.lo[d]) / g.dx[d] - 0.5;
-                const double fl = floor(fi);
+                const R xp = gc.lo[d] + ((R)ijk[d] + R(0.5)) * gc.dx[d] + sd * nv[d];
+                const R fi = (xp - gc.lo[d]) / gc.dx[d] - R(0.5);
+                const R fl = floor(fi);
                 base[d] = (int)fl;
                 fr[d] = fi - fl;
             }
             long long cidx[1 << DIM];
-            double wts[1 << DIM];
+            R wts[1 << DIM];
             bool ok = true;
 #pragma unroll
             for (int m = 0; m < (1 << DIM); m++) {
                 int ci[3] = {0, 0, 0};
-                double wt = 1.0;
+                R wt = R(1);
 #pragma unroll
                 for (int d = 0; d < DIM; d++) {
                     const int bit = (m >> d) & 1;
@@ -391,39 +395,39 @@ __global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
                     if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
                     else if (ii < 0 || ii > g.n[d] - 1) ok = false;
                     ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
-                    wt *= bit ? fr[d] : (1.0 - fr[d]);
+                    wt *= bit ? fr[d] : (R(1) - fr[d]);
                 }
                 cidx[m] = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
                 wts[m] = wt;
-                if (ok && !((double)U[L::IR * P + cidx[m]] < 0.5)) ok = false;
+                if (ok && !(U[L::IR * P + cidx[m]] < R(0.5))) ok = false;
             }
             if (!ok) continue;
 #pragma unroll
-            for (int v = 0; v < L::NVAR; v++) wi[v] = 0.0;
+            for (int v = 0; v < L::NVAR; v++) wi[v] = R(0);
 #pragma unroll
             for (int m = 0; m < (1 << DIM); m++) {
-                double q[L::NVAR], w[L::NVAR];
+                R q[L::NVAR], w[L::NVAR];
 #pragma unroll
-                for (int v = 0; v < L::NVAR; v++) q[v] = (double)U[v * P + cidx[m]];
-                cons_to_prim_ct<double, DIM, NMAT, SOLID>(g, q, w);
+                for (int v = 0; v < L::NVAR; v++) q[v] = U[v * P + cidx[m]];
+                cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
 #pragma unroll
                 for (int v = 0; v < L::NVAR; v++) wi[v] += wts[m] * w[v];
             }
             found = true;
         }
         if (!found) continue;
-        double Pm[3][3];
+        R Pm[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int j = 0; j < 3; j++) Pm[i][j] = (i == j ? 1.0 : 0.0) - 2.0 * nv[i] * nv[j];
-        const double vn = ctl->v[0] * nv[0] + ctl->v[1] * nv[1] + ctl->v[2] * nv[2];
-        double u[3] = {0.0, 0.0, 0.0}, unew[3];
+            for (int j = 0; j < 3; j++) Pm[i][j] = (i == j ? R(1) : R(0)) - R(2) * nv[i] * nv[j];
+        const R vn = (R)ctl->v[0] * nv[0] + (R)ctl->v[1] * nv[1] + (R)ctl->v[2] * nv[2];
+        R u[3] = {R(0), R(0), R(0)}, unew[3];
 #pragma unroll
         for (int a = 0; a < DIM; a++) u[a] = wi[L::IMOM + a];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            unew[i] = 2.0 * vn * nv[i];
+            unew[i] = R(2) * vn * nv[i];
 #pragma unroll
             for (int j = 0; j < 3; j++) unew[i] += Pm[i][j] * u[j];
         }
@@ -431,31 +435,31 @@ __global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
         for (int a = 0; a < DIM; a++) wi[L::IMOM + a] = unew[a];
         if (SOLID) {
             double A[3][3], PA[3][3];
-            unpack_A<double, DIM, NMAT, SOLID>(wi, A);
+            unpack_A<R, DIM, NMAT, SOLID>(wi, A);
 #pragma unroll
             for (int i = 0; i < 3; i++)
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    double s = 0.0;
+                    double sm = 0.0;
 #pragma unroll
-                    for (int k = 0; k < 3; k++) s += Pm[i][k] * A[k][j];
-                    PA[i][j] = s;
+                    for (int k = 0; k < 3; k++) sm += (double)Pm[i][k] * A[k][j];
+                    PA[i][j] = sm;
                 }
 #pragma unroll
             for (int cc = 0; cc < L::NV; cc++) {
                 const int i = v_row(DIM, cc), j = v_col(DIM, cc);
-                double s = 0.0;
+                double sm = 0.0;
 #pragma unroll
-                for (int k = 0; k < 3; k++) s += PA[i][k] * Pm[k][j];
-                wi[L::IV + cc] = s;
+                for (int k = 0; k < 3; k++) sm += PA[i][k] * (double)Pm[k][j];
+                wi[L::IV + cc] = (R)sm;
             }
         }
         wi[L::IR] = rc;
-        double q[L::NVAR];
-        prim_to_cons<double, DIM, NMAT, SOLID>(g, wi, q);
+        R q[L::NVAR];
+        prim_to_cons<R, DIM, NMAT, SOLID>(g, wi, q);
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++)
-            if (v != L::IR) U[v * P + c] = (R)q[v];
+            if (v != L::IR) U[v * P + c] = q[v];
     }
 }
 
@@ -477,12 +481,13 @@ __global__ void __launch_bounds__(256) k_cfl(const void *Uv, double *partials, G
         cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
         State<R, DIM, NMAT, SOLID> s;
         state_from_prim<R, DIM, NMAT, SOLID>(g, w, s);
-        const double cs = sqrt((double)s.c2);
-        double sum = 0.0;
+        const R cs = m_sqrt(s.c2);
+        R sum = R(0);
 #pragma unroll
-        for (int d = 0; d < DIM; d++) sum += (fabs((double)s.u[d]) + cs) / g.dx[d];
-        if (!(sum == sum)) sum = __longlong_as_double(0x7ff0000000000000LL);   // NaN -> +inf: dt = 0
-        red[0] = fmax(red[0], sum);
+        for (int d = 0; d < DIM; d++) sum += (m_abs(s.u[d]) + cs) / gridc<R>(g).dx[d];
+        double sd = (double)sum;
+        if (!(sd == sd)) sd = __longlong_as_double(0x7ff0000000000000LL);   // NaN -> +inf: dt = 0
+        red[0] = fmax(red[0], sd);
     }
     block_reduce4<256>(red, sred);
     if (threadIdx.x == 0) partials[4 * blockIdx.x] = red[0];

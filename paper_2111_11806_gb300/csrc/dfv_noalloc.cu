@@ -114,6 +114,7 @@ extern "C" dfv_status dfv_compute_dt_noalloc(int dim, const int n[3], const doub
         m.Gamma0 = params[l].Gamma0;
         m.sigY = params[l].sigma_y;
     }
+    dfv::finish_params(p);
 
     double *scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return DFV_ERR_CUDA;
