@@ -155,8 +155,9 @@ dfv_status dfv_check(dfv_grid *g, int timeout_ms);
 /* Per-kernel device timing of steps, with CUDA events recorded on the grid's
  * stream around each launch.  enable = 1 clears the record and starts
  * recording; enable = 0 stops, synchronises the stream and returns in
- * ms_out[0..4] the summed device time of the seeding, stage-1, stage-2,
- * stage-3 and finalize launches, and in *steps_out the number of recorded
+ * ms_out[0..4] the summed device time of the seeding, stage-1, stage-2 and
+ * stage-3 launches and of the finalize (0: it runs in the last block of stage
+ * 3), and in *steps_out the number of recorded
  * steps (either output may be NULL).  While recording, dfv_run launches the
  * kernels of each step directly instead of replaying a graph. */
 dfv_status dfv_profile(dfv_grid *g, int enable, double ms_out[5], long long *steps_out);

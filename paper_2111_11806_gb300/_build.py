@@ -45,10 +45,17 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+# The FP32 translation units use the fast single-precision divide and square
+# root (double precision is unaffected); the FP32 form's accuracy target is a
+# relative L1 of 1e-4 against the FP64 solution.
+FP32_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
+
+
 def _compile(src, extra):
     obj = os.path.join(OBJDIR, os.path.basename(src).replace(".cu", ".o"))
-    if _stale(obj, [src] + headers()):
-        cmd = [nvcc()] + ARCH + FLAGS + list(extra) + ["-c", src, "-o", obj + ".tmp"]
+    if _stale(obj, [src] + headers() + [os.path.abspath(__file__)]):
+        flags = FP32_FLAGS if "_f32_" in os.path.basename(src) else []
+        cmd = [nvcc()] + ARCH + FLAGS + flags + list(extra) + ["-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))

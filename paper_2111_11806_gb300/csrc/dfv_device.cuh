@@ -30,6 +30,7 @@ template <class T>
 struct MatC {
     int kind;
     T Gam;          // Grueneisen coefficient (gamma - 1 for the gases)
+    T invGam;       // 1 / Gam
     T pref0;        // constant p_ref of the gases (-gamma p_inf, 0)
     T rho0, K0, G0, alpha, beta, sigY;
     int has_rho0;
@@ -40,6 +41,7 @@ struct GridC {
     T lo[3], dx[3], inv_dx[3];
     T dxmin, dV;
     T beta, cosh_b, sinh_b, tanh_b;   // THINC constants
+    T inv_sinh_b;
     T phi_guard;
 };
 
@@ -67,6 +69,7 @@ __host__ inline void fill_consts(const GridP &g, MatC<T> *mc, GridC<T> &gc)
         const MatP &m = g.mat[l];
         mc[l].kind = m.kind;
         mc[l].Gam = (T)(m.kind == 2 ? m.Gamma0 : m.gamma - 1.0);
+        mc[l].invGam = (T)(1.0 / (m.kind == 2 ? m.Gamma0 : m.gamma - 1.0));
         mc[l].pref0 = (m.kind == 1) ? (T)(-m.gamma * m.pinf) : T(0);
         mc[l].rho0 = (T)m.rho0;
         mc[l].K0 = (T)m.K0;
@@ -87,6 +90,7 @@ __host__ inline void fill_consts(const GridP &g, MatC<T> *mc, GridC<T> &gc)
     gc.cosh_b = (T)g.cosh_b;
     gc.sinh_b = (T)g.sinh_b;
     gc.tanh_b = (T)g.tanh_b;
+    gc.inv_sinh_b = (T)(1.0 / g.sinh_b);
     gc.phi_guard = (T)g.phi_guard;
 }
 
@@ -126,6 +130,7 @@ struct Ctl {
     int auto_dt;              // 1: the finalize kernel sets the next dt from cfl
     unsigned int err;         // bit 0: rho<=0/NaN in an update, bit 1: c^2<=0/NaN
     int steps;
+    unsigned int ticket;      // blocks of the last stage that have written their partials
 };
 
 enum { ERR_STATE = 1u, ERR_SOUND = 2u };
@@ -356,24 +361,27 @@ __device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, S
     T rhoe = T(0), den = T(0), Gn = T(0), Sn = T(0), Yn = T(0);
 #pragma unroll
     for (int l = 0; l < NMAT; l++) {
-        const Ref<T> r = mat_ref<T>(matc<T>(g, l), rhol[l], J2);
+        const MatC<T> &m = matc<T>(g, l);
+        const Ref<T> r = mat_ref<T>(m, rhol[l], J2);
+        const T iG = m.invGam;
+        const T irl = T(1) / rhol[l];
         if (s.ar[l] != T(0)) rhoe += s.ar[l] * r.eref;
-        rhoe += s.phi[l] * (s.p - r.pref) / r.Gam;
-        den += s.phi[l] / r.Gam;
-        Gn += s.phi[l] * r.G / r.Gam;
-        Sn += s.phi[l] * matc<T>(g, l).sigY / r.Gam;
-        const T rl = rhol[l];
-        const T a2 = r.Gam * s.p / rl + (s.p - r.pref) / rl + r.dpref - r.Gam * rl * r.deref;
-        const T c2l = a2 + T(4) / T(3) * r.G / rl;
-        if (s.ar[l] != T(0)) Yn += (s.ar[l] / s.rho) * c2l / r.Gam;
+        rhoe += s.phi[l] * (s.p - r.pref) * iG;
+        den += s.phi[l] * iG;
+        Gn += s.phi[l] * r.G * iG;
+        Sn += s.phi[l] * m.sigY * iG;
+        const T a2 = (r.Gam * s.p + (s.p - r.pref)) * irl + r.dpref - r.Gam * rhol[l] * r.deref;
+        const T c2l = a2 + T(4) / T(3) * r.G * irl;
+        if (s.ar[l] != T(0)) Yn += s.ar[l] * c2l * iG;
     }
     T ke = T(0);
 #pragma unroll
     for (int a = 0; a < DIM; a++) ke += T(0.5) * s.rho * s.u[a] * s.u[a];
+    const T iden = T(1) / den;
     s.rhoE = rhoe + ke;
-    s.G = Gn / den;
-    s.sigY = Sn / den;
-    s.c2 = Yn / den;
+    s.G = Gn * iden;
+    s.sigY = Sn * iden;
+    s.c2 = Yn / s.rho * iden;
 }
 
 template <class T, int NMAT>
@@ -446,8 +454,9 @@ __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w
         rho += ar[l];
     }
     T u[DIM];
+    const T irho = T(1) / rho;
 #pragma unroll
-    for (int a = 0; a < DIM; a++) u[a] = q[L::IMOM + a] / rho;
+    for (int a = 0; a < DIM; a++) u[a] = q[L::IMOM + a] * irho;
     T J2 = T(0);
     if (SOLID) {
         double A[3][3], H[3][3], j2;
@@ -465,10 +474,11 @@ __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w
     for (int l = 0; l < NMAT; l++) {
         const T phc = phi_clip(phi[l]);
         rhol[l] = (NMAT == 1) ? rho : phasic_density<T>(g, l, ar[l], phc);
-        const Ref<T> r = mat_ref<T>(matc<T>(g, l), rhol[l], J2);
+        const MatC<T> &m = matc<T>(g, l);
+        const Ref<T> r = mat_ref<T>(m, rhol[l], J2);
         if (ar[l] != T(0)) num -= ar[l] * r.eref;
-        num += phc * r.pref / r.Gam;
-        den += phc / r.Gam;
+        num += phc * r.pref * m.invGam;
+        den += phc * m.invGam;
     }
 #pragma unroll
     for (int l = 0; l < NMAT - 1; l++) w[L::IPHI + l] = phi[l];
@@ -540,7 +550,7 @@ __device__ __forceinline__ bool thinc(const GridP &g, T qm, T q0, T qp, T &fm, T
     if (!(C > T(1e-8) && C < T(1) - T(1e-8))) return false;
     const GridC<T> &gc = gridc<T>(g);
     const T B = m_exp(th * gc.beta * (T(2) * C - T(1)));
-    const T ty = (gc.cosh_b - B) / gc.sinh_b;
+    const T ty = (gc.cosh_b - B) * gc.inv_sinh_b;
     const T tb = gc.tanh_b;
     const T t1 = (tb - ty) / (T(1) - tb * ty);
     fm = qmin + T(0.5) * dq * (T(1) - th * ty);

