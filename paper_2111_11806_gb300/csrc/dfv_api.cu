@@ -73,7 +73,8 @@ struct Layout {
 
 long long stage_blocks(int dim, const int n[3])
 {
-    // tile shapes of dfv_kernels.cuh
+    // the smallest tile of dfv_kernels.cuh per dimension: an upper bound on the
+    // number of stage blocks of either precision
     const int tx = dim == 1 ? 256 : 32, ty = dim == 1 ? 1 : (dim == 2 ? 8 : 4), tz = dim == 3 ? 2 : 1;
     const long long bx = (n[0] + tx - 1) / tx;
     const long long by = dim >= 2 ? (n[1] + ty - 1) / ty : 1;
@@ -142,6 +143,7 @@ __global__ void k_set_body(Ctl *c, double v0, double v1, double v2, double x0, d
     c->x[2] = x2;
     c->mass = mass;
     c->dynamic = dynamic;
+    dfv::ctl_sync_v(c);
 }
 
 __global__ void k_set_run(Ctl *c, double cfl, double t_end)
@@ -303,7 +305,6 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
     g->U1 = g->ws + L.off_U1;
     g->U3 = g->ws + L.off_U3;
     g->staging = (double *)(g->ws + L.off_stage);
-    g->nb_stage = L.nb_stage;
     g->nb_cfl = L.nb_cfl;
 
     GridP &p = g->g;
@@ -332,6 +333,10 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
     p.tanh_b = std::tanh(p.beta);
     p.phi_guard = 1e-14;
     dfv::finish_params(p);
+    {
+        const dim3 sg = ops->stage_grid(p);
+        g->nb_stage = (long long)sg.x * sg.y * sg.z;
+    }
 
     cudaError_t e = ops->prepare();
     if (e != cudaSuccess) {

@@ -131,7 +131,32 @@ struct Ctl {
     unsigned int err;         // bit 0: rho<=0/NaN in an update, bit 1: c^2<=0/NaN
     int steps;
     unsigned int ticket;      // blocks of the last stage that have written their partials
+    float dtf, vf[3];         // dt and v in single precision, kept equal to (float)dt, (float)v
 };
+
+// dt and body velocity in the compute precision
+template <class T>
+__device__ __forceinline__ T ctl_dt(const Ctl *c);
+template <>
+__device__ __forceinline__ double ctl_dt<double>(const Ctl *c) { return c->dt; }
+template <>
+__device__ __forceinline__ float ctl_dt<float>(const Ctl *c) { return c->dtf; }
+template <class T>
+__device__ __forceinline__ T ctl_v(const Ctl *c, int d);
+template <>
+__device__ __forceinline__ double ctl_v<double>(const Ctl *c, int d) { return c->v[d]; }
+template <>
+__device__ __forceinline__ float ctl_v<float>(const Ctl *c, int d) { return c->vf[d]; }
+
+__device__ __forceinline__ void ctl_set_dt(Ctl *c, double dt)
+{
+    c->dt = dt;
+    c->dtf = (float)dt;
+}
+__device__ __forceinline__ void ctl_sync_v(Ctl *c)
+{
+    for (int d = 0; d < 3; d++) c->vf[d] = (float)c->v[d];
+}
 
 enum { ERR_STATE = 1u, ERR_SOUND = 2u };
 
@@ -358,6 +383,20 @@ __device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, S
 #pragma unroll
             for (int b = 0; b < DIM; b++) s.H[a][b] = (T)H[a][b];
     }
+    if (NMAT == 1) {
+        // single material: the mixture rules reduce to the material's own closure
+        const MatC<T> &m = matc<T>(g, 0);
+        const Ref<T> r = mat_ref<T>(m, rhol[0], J2);
+        const T irl = T(1) / rhol[0];
+        T ke = T(0);
+#pragma unroll
+        for (int a = 0; a < DIM; a++) ke += T(0.5) * s.rho * s.u[a] * s.u[a];
+        s.rhoE = s.ar[0] * r.eref + (s.p - r.pref) * m.invGam + ke;
+        s.G = r.G;
+        s.sigY = m.sigY;
+        s.c2 = (r.Gam * s.p + (s.p - r.pref)) * irl + r.dpref - r.Gam * rhol[0] * r.deref + T(4) / T(3) * r.G * irl;
+        return;
+    }
     T rhoe = T(0), den = T(0), Gn = T(0), Sn = T(0), Yn = T(0);
 #pragma unroll
     for (int l = 0; l < NMAT; l++) {
@@ -470,6 +509,19 @@ __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w
     for (int a = 0; a < DIM; a++) ke += T(0.5) * rho * u[a] * u[a];
     T num = q[L::IE] - ke, den = T(0);
     T rhol[NMAT];
+    if (NMAT == 1) {
+        const MatC<T> &m = matc<T>(g, 0);
+        const Ref<T> r = mat_ref<T>(m, rho, J2);
+#pragma unroll
+        for (int a = 0; a < DIM; a++) w[L::IMOM + a] = u[a];
+        w[L::IAR] = rho;
+        // p = p_ref + Gamma (rho e - rho e_ref)   (eq:MieGruneisenEOS)
+        w[L::IE] = r.pref + r.Gam * (num - rho * r.eref);
+#pragma unroll
+        for (int c = 0; c < L::NV; c++) w[L::IV + c] = q[L::IV + c];
+        w[L::IR] = q[L::IR];
+        return;
+    }
 #pragma unroll
     for (int l = 0; l < NMAT; l++) {
         const T phc = phi_clip(phi[l]);

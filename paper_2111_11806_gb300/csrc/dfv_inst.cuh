@@ -10,7 +10,7 @@ namespace dfv {
 template <class R, int DIM, int NMAT, bool SOLID>
 struct Impl {
     using L = Lay<DIM, NMAT, SOLID>;
-    using TL = Tile<DIM>;
+    using TL = Tile<DIM, (int)sizeof(R)>;
 
     static dim3 stage_grid(const GridP &g)
     {

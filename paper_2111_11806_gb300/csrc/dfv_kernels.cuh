@@ -17,24 +17,32 @@ namespace dfv {
 
 // ------------------------------------------------------------ tiling
 
-template <int DIM>
+// Tile of one CTA: TX x TY x TZ cells, with one thread per face of the
+// largest face sweep (the extra warp covers the tile's closing faces).  The
+// FP32 2-D form uses a taller tile (less halo recomputation per cell); the
+// FP64 form keeps 32 x 8 so that its larger register footprint fits.
+template <int DIM, int W>
 struct Tile;
-template <>
-struct Tile<1> {
+template <int W>
+struct Tile<1, W> {
     static constexpr int TX = 256, TY = 1, TZ = 1, THREADS = 288;
 };
 template <>
-struct Tile<2> {
-    static constexpr int TX = 32, TY = 8, TZ = 1, THREADS = 288;
+struct Tile<2, 4> {
+    static constexpr int TX = 32, TY = 16, TZ = 1, THREADS = 544;
 };
 template <>
-struct Tile<3> {
+struct Tile<2, 8> {
+    static constexpr int TX = 32, TY = 8, TZ = 1, THREADS = 288;
+};
+template <int W>
+struct Tile<3, W> {
     static constexpr int TX = 32, TY = 4, TZ = 2, THREADS = 384;
 };
 
-template <int DIM>
+template <int DIM, int W>
 struct Box {
-    using TL = Tile<DIM>;
+    using TL = Tile<DIM, W>;
     static constexpr int HX = 3, HY = DIM >= 2 ? 3 : 0, HZ = DIM >= 3 ? 3 : 0;
     static constexpr int BX = TL::TX + 2 * HX, BY = TL::TY + 2 * HY, BZ = TL::TZ + 2 * HZ;
     static constexpr int N = BX * BY * BZ;
@@ -49,7 +57,7 @@ struct Box {
 template <class R, int DIM, int NMAT, bool SOLID>
 struct StageSmem {
     using L = Lay<DIM, NMAT, SOLID>;
-    using B = Box<DIM>;
+    using B = Box<DIM, (int)sizeof(R)>;
     static constexpr size_t bytes =
         ((sizeof(R) * ((size_t)L::NVAR * B::N + (size_t)L::NF * B::MAXF) + 7) & ~(size_t)7) + 4 * 32 * sizeof(double);
 };
@@ -91,21 +99,12 @@ __device__ __forceinline__ R rk_combine(int stage, R un, R in, const Acc<R> &D, 
         const R y = in - dt * D.hi;
         return stage == 1 ? y : ca * un + cb * y;
     } else {
+        // y = in - dt*(hi + lo) with a single rounding of the product and sum
+        // (fused multiply-add), the low part of the compensated sum folded in
         const float fdt = (float)dt;
-        // y = in - dt*(hi+lo), kept as (y, ey)
-        const float p = fdt * (float)D.hi;
-        const float pe = fmaf(fdt, (float)D.hi, -p);
-        float y, ey;
-        two_sum((float)in, -p, y, ey);
-        ey += -pe - fdt * (float)D.lo;
-        if (stage == 1) return (R)(y + ey);
-        const float a = (float)ca * (float)un;
-        const float ae = fmaf((float)ca, (float)un, -a);
-        const float b = (float)cb * y;
-        const float be = fmaf((float)cb, y, -b);
-        float s, se;
-        two_sum(a, b, s, se);
-        return (R)(s + (se + ae + be + (float)cb * ey));
+        const float y = fmaf(-fdt, (float)D.hi, fmaf(-fdt, (float)D.lo, (float)in));
+        if (stage == 1) return (R)y;
+        return (R)fmaf((float)cb, y, (float)ca * (float)un);
     }
 }
 
@@ -165,11 +164,13 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
     if (mode & 2)
         for (int d = 0; d < 3; d++) ctl->force[d] = red[1 + d];
     if (mode & 4) {
-        if (ctl->dynamic && ctl->mass > 0.0)
+        if (ctl->dynamic && ctl->mass > 0.0) {
             for (int d = 0; d < 3; d++) {
                 ctl->v[d] += ctl->dt * ctl->force[d] / ctl->mass;
                 ctl->x[d] += ctl->dt * ctl->v[d];
             }
+            ctl_sync_v(ctl);
+        }
         ctl->t += ctl->dt;
         ctl->steps += 1;
     }
@@ -182,7 +183,7 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
         double dt = ctl->cfl / ctl->smax;
         if (ctl->t_end > 0.0) dt = fmin(dt, fmax(ctl->t_end - ctl->t, 0.0));
         if (!(dt == dt)) dt = 0.0;
-        ctl->dt = dt;
+        ctl_set_dt(ctl, dt);
     }
 }
 
@@ -211,8 +212,8 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
                                       Acc<R> *Dacc)
 {
     using L = Lay<DIM, NMAT, SOLID>;
-    using B = Box<DIM>;
-    using TL = Tile<DIM>;
+    using B = Box<DIM, (int)sizeof(R)>;
+    using TL = Tile<DIM, (int)sizeof(R)>;
     constexpr int EX = TL::TX + (D == 0), EY = TL::TY + (D == 1), EZ = TL::TZ + (D == 2);
     constexpr int NFACE = EX * EY * EZ;
     constexpr int SD = B::stride(D);
@@ -261,11 +262,11 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
 }
 
 template <class R, int DIM, int NMAT, bool SOLID, int STAGE>
-__global__ void __launch_bounds__(Tile<DIM>::THREADS) k_stage(StageArgs a, GridP g)
+__global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(StageArgs a, GridP g)
 {
     using L = Lay<DIM, NMAT, SOLID>;
-    using B = Box<DIM>;
-    using TL = Tile<DIM>;
+    using B = Box<DIM, (int)sizeof(R)>;
+    using TL = Tile<DIM, (int)sizeof(R)>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sW = reinterpret_cast<R *>(smem_raw);
     R *sF = sW + (size_t)L::NVAR * B::N;
@@ -301,8 +302,8 @@ __global__ void __launch_bounds__(Tile<DIM>::THREADS) k_stage(StageArgs a, GridP
     const int lx = threadIdx.x % TL::TX, ly = (threadIdx.x / TL::TX) % TL::TY, lz = threadIdx.x / (TL::TX * TL::TY);
     const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
     const bool inside = own && gx < g.n[0] && gy < g.n[1] && gz < g.n[2];
-    const R dt = (R)a.ctl->dt;
-    R vr[3] = {(R)a.ctl->v[0], (R)a.ctl->v[1], (R)a.ctl->v[2]};
+    const R dt = ctl_dt<R>(a.ctl);
+    R vr[3] = {ctl_v<R>(a.ctl, 0), ctl_v<R>(a.ctl, 1), ctl_v<R>(a.ctl, 2)};
 
     Acc<R> Dacc[L::NVAR];
 #pragma unroll
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++) Pm[i][j] = (i == j ? R(1) : R(0)) - R(2) * nv[i] * nv[j];
-        const R vn = (R)ctl->v[0] * nv[0] + (R)ctl->v[1] * nv[1] + (R)ctl->v[2] * nv[2];
+        const R vn = ctl_v<R>(ctl, 0) * nv[0] + ctl_v<R>(ctl, 1) * nv[1] + ctl_v<R>(ctl, 2) * nv[2];
         R u[3] = {R(0), R(0), R(0)}, unew[3];
 #pragma unroll
         for (int a = 0; a < DIM; a++) u[a] = wi[L::IMOM + a];
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(256) k_cfl(const void *Uv, double *partials, G
     if (threadIdx.x == 0) partials[4 * blockIdx.x] = red[0];
 }
 
-static __global__ void k_set_dt(Ctl *ctl, double dt) { ctl->dt = dt; }
+static __global__ void k_set_dt(Ctl *ctl, double dt) { ctl_set_dt(ctl, dt); }
 
 // ------------------------------------------------------------ conversions
 

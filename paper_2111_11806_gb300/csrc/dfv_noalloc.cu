@@ -56,6 +56,7 @@ __global__ void k_noalloc_init_ctl(dfv::Ctl *c, double v0, double v1, double v2)
     c->v[0] = v0;
     c->v[1] = v1;
     c->v[2] = v2;
+    dfv::ctl_sync_v(c);
 }
 
 }  // namespace
