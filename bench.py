@@ -28,6 +28,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -45,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -216,6 +220,52 @@ def time_steps(torch, g, stream, flush, steps, profile):
     return ms, launches, prof
 
 
+def run_batched(torch, B, W, stream, args):
+    """Batched workload: per-step CUDA-event timing of graph replays, per-phase
+    profile for the stage-kernel roofline, and the plain FP64 batch."""
+    peak, peak_kind = measured_peaks()
+    wls = [W.ellipse_instance(i) for i in range(args.batch_count)]
+    cells = int(sum(int(np.prod(wl.n)) for wl in wls))
+    out = {"workload": "ellipses_%d_instances_128-512sq_fp32" % args.batch_count, "cells": cells}
+    for prec, key in ((B.DFV_FP32, "fp32"), (B.DFV_FP64, "fp64")):
+        bt = B.Batch(wls, precision=prec, stream=stream)
+        bt.set_all_fields()
+        choice = bt.autotune(trial_steps=2, cfl=0.8)
+        bt.run(3, 0.8)
+        k = 30 if prec == B.DFV_FP32 else 4
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = bt.launch_count()
+        stream.synchronize()
+        e0.record(stream)
+        bt.run(k, 0.8)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = bt.launch_count() - n0
+        bt.profile(True)
+        bt.run(3, 0.8)
+        pms, pn = bt.profile(False)
+        w = 4 if prec == B.DFV_FP32 else 8
+        nvar = bt.nvar
+        stage_ms = float(pms[1] + pms[2] + pms[3]) / pn
+        achieved = 8 * nvar * w * cells / (stage_ms * 1e-3) / 1e9
+        rec = {"value": cells * k / (ms * 1e-3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
+               "autotune": {"ctas_per_sm": choice[0], "schedule": ["instance-order static", "largest-first static",
+                                                                    "largest-first dynamic"][choice[1]]},
+               "gpu_launches": int(launches),
+               "phase_ms_per_step": {"seed": pms[0] / pn, "stage1": pms[1] / pn, "stage2": pms[2] / pn,
+                                     "stage3": pms[3] / pn},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "peak_kind": peak_kind,
+                            "kernel": "k_batch_stage (3 launches per step)",
+                            "algorithmic_bytes_per_step": 8 * nvar * w * cells}}
+        out[key] = rec
+        del bt
+        torch.cuda.synchronize()
+    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def run_ours(args):
     rank, world, local = dist_env()
     import numpy as np
@@ -287,6 +337,14 @@ def run_ours(args):
     e2e_val = world * jobs * job_steps * N_CELL / e2e_s
     bytes_io = nvar * N_CELL * 8
 
+    # --- batched form: 256 independent instances of {128..512}^2 (about 27 M
+    # cells, 0.54 GB per FP32 state copy: larger than L2, so no flush is needed),
+    # persistent launches over the (instance, tile) work list in a CUDA graph,
+    # schedule chosen by the autotuner
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(torch, B, W, stream, args)
+
     clk = clocks.stop() if clocks else None
 
     # --- accuracy of the FP32 form after the timed steps: relative L1 of the
@@ -340,6 +398,7 @@ def run_ours(args):
                                "stage2": prof32[0][2] / prof32[1], "stage3": prof32[0][3] / prof32[1],
                                "finalize": prof32[0][4] / prof32[1]},
         "cpu_baseline": cpu,
+        "batched": batched,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io / job_steps,
                 "d2h_bytes_per_step": bytes_io / job_steps,
                 "job": "set_fields(host) + %d steps + get_fields(host), %d jobs" % (job_steps, jobs)},

@@ -167,6 +167,56 @@ dfv_status dfv_launch_count(const dfv_grid *g, long long *count);
 
 dfv_status dfv_destroy(dfv_grid *g);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent 2-D fluid instances of different sizes (own grid, rigid
+ * body velocity and time step) advanced together: each phase of a step
+ * (seeding, the three RK stages) is one persistent launch over a work list of
+ * (instance, tile) items, and a step is captured once into a CUDA graph.  Each
+ * instance follows exactly the single-grid algorithm above with its own dt.
+ * Materials are shared by all instances.  Field layout per instance as for a
+ * grid (index i selects the instance). */
+typedef struct {
+    int n[3];           /* cells per direction (n[2] unused) */
+    double lo[3], hi[3];
+    int bc[6];
+    double v_body[3];   /* rigid-body velocity (static bodies: 0) */
+} dfv_instance_desc;
+
+typedef struct dfv_batch dfv_batch;
+
+/* Workspace bytes of a batch (dim must be 2; fluids only, opt->solid = 0). */
+dfv_status dfv_batch_workspace_bytes(int dim, int count, const dfv_instance_desc *desc, int precision,
+                                     const dfv_options *opt, size_t *bytes);
+/* Create a batch of `count` instances in the caller's workspace (256-byte
+ * aligned device memory of at least dfv_batch_workspace_bytes). */
+dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, int precision,
+                            const dfv_options *opt, void *workspace, size_t workspace_bytes, void *stream,
+                            dfv_batch **out);
+/* Add material number k (ideal or stiffened gas) to every instance. */
+dfv_status dfv_batch_add_material(dfv_batch *b, int kind, const dfv_material_params *p);
+/* Initial primitive fields of instance i (FP64 planes, host or device). */
+dfv_status dfv_batch_set_fields(dfv_batch *b, int i, const double *prim, int on_device);
+dfv_status dfv_batch_get_fields(dfv_batch *b, int i, double *out, int which, int on_device);
+/* `steps` steps of every instance, each with its own dt = cfl / (its CFL
+ * bound), clipped to t_end when t_end > 0; no host synchronisation. */
+dfv_status dfv_batch_run(dfv_batch *b, int steps, double cfl, double t_end);
+/* Time trial steps of every (CTAs per SM, item schedule) candidate and keep
+ * the fastest; the fields and times are restored afterwards.  choice_out (may
+ * be NULL) receives {ctas_per_sm, schedule}: 0 instance order with static
+ * round-robin assignment, 1 largest instances first, static, 2 largest
+ * instances first from a dynamic queue. */
+dfv_status dfv_batch_autotune(dfv_batch *b, int trial_steps, double cfl, int choice_out[2]);
+/* Set the persistent grid (CTAs per SM, clipped to the occupancy limit) and
+ * the schedule explicitly. */
+dfv_status dfv_batch_set_schedule(dfv_batch *b, int ctas_per_sm, int schedule);
+/* Simulated time and current dt of instance i (synchronises). */
+dfv_status dfv_batch_get_time(dfv_batch *b, int i, double *t, double *dt);
+/* Per-phase event timing of steps (seed, stage 1, 2, 3), like dfv_profile. */
+dfv_status dfv_batch_profile(dfv_batch *b, int enable, double ms_out[4], long long *steps_out);
+dfv_status dfv_batch_launch_count(const dfv_batch *b, long long *count);
+dfv_status dfv_batch_destroy(dfv_batch *b);
+const char *dfv_batch_last_error(const dfv_batch *b);
+
 /* Largest grid (cells) that dfv_compute_dt_noalloc accepts. */
 #define DFV_NOALLOC_MAX_CELLS (16LL * 1024 * 1024)
 

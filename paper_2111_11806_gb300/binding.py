@@ -24,7 +24,11 @@ MAT_KIND = {"ideal": 0, "stiffened": 1, "romenskii": 2}
 
 EXPORTS = ("dfv_workspace_bytes", "dfv_create_grid", "dfv_add_material", "dfv_set_fields", "dfv_get_fields",
            "dfv_set_body", "dfv_get_body", "dfv_compute_dt", "dfv_step", "dfv_run", "dfv_check",
-           "dfv_profile", "dfv_launch_count", "dfv_destroy", "dfv_last_error", "dfv_compute_dt_noalloc")
+           "dfv_profile", "dfv_launch_count", "dfv_destroy", "dfv_last_error", "dfv_compute_dt_noalloc",
+           "dfv_batch_workspace_bytes", "dfv_batch_create", "dfv_batch_add_material", "dfv_batch_set_fields",
+           "dfv_batch_get_fields", "dfv_batch_run", "dfv_batch_autotune", "dfv_batch_set_schedule",
+           "dfv_batch_get_time", "dfv_batch_profile", "dfv_batch_launch_count", "dfv_batch_destroy",
+           "dfv_batch_last_error")
 
 
 class dfv_material_params(ctypes.Structure):
@@ -35,6 +39,11 @@ class dfv_material_params(ctypes.Structure):
 class dfv_options(ctypes.Structure):
     _fields_ = [("nmat", ctypes.c_int), ("solid", ctypes.c_int), ("use_thinc", ctypes.c_int),
                 ("thinc_beta", ctypes.c_double)]
+
+
+class dfv_instance_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("bc", ctypes.c_int * 6), ("v_body", ctypes.c_double * 3)]
 
 
 class DfvError(RuntimeError):
@@ -71,13 +80,30 @@ def load(path: str = LIB_PATH):
     L.dfv_profile.argtypes = [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]
     L.dfv_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
     L.dfv_destroy.argtypes = [_vp]
+    _bp = ctypes.POINTER(dfv_instance_desc)
+    L.dfv_batch_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, _bp, ctypes.c_int, ctypes.POINTER(dfv_options),
+                                            ctypes.POINTER(ctypes.c_size_t)]
+    L.dfv_batch_create.argtypes = [ctypes.c_int, ctypes.c_int, _bp, ctypes.c_int, ctypes.POINTER(dfv_options), _vp,
+                                   ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]
+    L.dfv_batch_add_material.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(dfv_material_params)]
+    L.dfv_batch_set_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int]
+    L.dfv_batch_get_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int]
+    L.dfv_batch_run.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.dfv_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _ip]
+    L.dfv_batch_set_schedule.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    L.dfv_batch_get_time.argtypes = [_vp, ctypes.c_int, _dp, _dp]
+    L.dfv_batch_profile.argtypes = [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]
+    L.dfv_batch_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.dfv_batch_destroy.argtypes = [_vp]
+    L.dfv_batch_last_error.argtypes = [_vp]
+    L.dfv_batch_last_error.restype = ctypes.c_char_p
     L.dfv_compute_dt_noalloc.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.c_int, ctypes.POINTER(dfv_options),
                                          _ip, ctypes.POINTER(dfv_material_params), _vp, ctypes.c_longlong, _dp,
                                          ctypes.c_double, _vp, _dp]
     L.dfv_last_error.argtypes = [_vp]
     L.dfv_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name != "dfv_last_error":
+        if name not in ("dfv_last_error", "dfv_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -287,4 +313,129 @@ class Grid:
     def launch_count(self):
         c = ctypes.c_longlong()
         _check(load().dfv_launch_count(self._h, ctypes.byref(c)), self._h, "dfv_launch_count")
+        return c.value
+
+
+def _bcheck(status, handle, what):
+    if status != DFV_OK:
+        m = load().dfv_batch_last_error(handle) if handle else b""
+        raise DfvError("%s: %s %s" % (what, DFV_ERR.get(status, status), m.decode() if m else ""))
+
+
+class Batch:
+    """A batch of independent 2-D instances (dfv_batch_*): each workload in
+    `workloads` (same materials, fluid, 2-D) becomes one instance with its own
+    grid, body velocity and time step.  Device memory: one torch workspace."""
+
+    def __init__(self, workloads, precision=DFV_FP32, use_thinc=True, thinc_beta=1.6, device="cuda:0",
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise DfvError("a CUDA device is required (no CPU fallback)")
+        L = load()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.wls = list(workloads)
+        self.count = len(self.wls)
+        mats = self.wls[0].materials
+        self.nmat = len(mats)
+        self.precision = precision
+        descs = (dfv_instance_desc * self.count)()
+        for i, wl in enumerate(self.wls):
+            assert wl.dim == 2 and not wl.solid and len(wl.materials) == self.nmat
+            d = descs[i]
+            for k in range(2):
+                d.n[k] = wl.n[k]
+                d.lo[k] = wl.lo[k]
+                d.hi[k] = wl.hi[k]
+                d.bc[2 * k] = d.bc[2 * k + 1] = DFV_BC_PERIODIC if wl.periodic[k] else DFV_BC_TRANSMISSIVE
+            d.n[2] = 1
+            for k in range(3):
+                d.v_body[k] = wl.body_v[k] if k < len(wl.body_v) else 0.0
+        self._descs = descs
+        opt = dfv_options(self.nmat, 0, int(bool(use_thinc)), float(thinc_beta))
+        nbytes = ctypes.c_size_t()
+        _check(L.dfv_batch_workspace_bytes(2, self.count, descs, precision, ctypes.byref(opt), ctypes.byref(nbytes)),
+               None, "dfv_batch_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) & ~255
+        h = _vp()
+        with torch.cuda.device(self.device):
+            _check(L.dfv_batch_create(2, self.count, descs, precision, ctypes.byref(opt), _vp(aligned),
+                                      nbytes.value, _vp(self.stream.cuda_stream), ctypes.byref(h)),
+                   None, "dfv_batch_create")
+        self._h = h
+        for m in mats:
+            _bcheck(L.dfv_batch_add_material(self._h, MAT_KIND[m["kind"]], ctypes.byref(material_struct(m))),
+                    self._h, "dfv_batch_add_material")
+        self.cells = [int(np.prod(wl.n)) for wl in self.wls]
+        self.total_cells = int(sum(self.cells))
+        self.nvar = (self.nmat - 1) + self.nmat + 2 + 1 + 1
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                self.stream.synchronize()
+            except Exception:
+                pass
+            load().dfv_batch_destroy(h)
+            self._h = None
+
+    def _ctx(self):
+        return self.torch.cuda.device(self.device)
+
+    def set_fields(self, i, prim):
+        a = np.ascontiguousarray(np.asarray(prim, dtype=np.float64))
+        with self._ctx():
+            _bcheck(load().dfv_batch_set_fields(self._h, int(i), _vp(a.ctypes.data), 0), self._h,
+                    "dfv_batch_set_fields")
+
+    def set_all_fields(self):
+        for i, wl in enumerate(self.wls):
+            self.set_fields(i, wl.prim)
+
+    def get_fields(self, i, which=DFV_FIELDS_CONSERVED):
+        a = np.zeros((self.nvar, self.cells[i]))
+        with self._ctx():
+            _bcheck(load().dfv_batch_get_fields(self._h, int(i), _vp(a.ctypes.data), which, 0), self._h,
+                    "dfv_batch_get_fields")
+        return a
+
+    def run(self, steps, cfl, t_end=0.0):
+        with self._ctx():
+            _bcheck(load().dfv_batch_run(self._h, int(steps), float(cfl), float(t_end or 0.0)), self._h,
+                    "dfv_batch_run")
+
+    def autotune(self, trial_steps=3, cfl=0.8):
+        c = (ctypes.c_int * 2)()
+        with self._ctx():
+            _bcheck(load().dfv_batch_autotune(self._h, int(trial_steps), float(cfl), c), self._h,
+                    "dfv_batch_autotune")
+        return int(c[0]), int(c[1])
+
+    def set_schedule(self, ctas_per_sm, schedule):
+        _bcheck(load().dfv_batch_set_schedule(self._h, int(ctas_per_sm), int(schedule)), self._h,
+                "dfv_batch_set_schedule")
+
+    def time(self, i):
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        with self._ctx():
+            _bcheck(load().dfv_batch_get_time(self._h, int(i), ctypes.byref(t), ctypes.byref(dt)), self._h,
+                    "dfv_batch_get_time")
+        return t.value, dt.value
+
+    def profile(self, enable):
+        ms = np.zeros(4)
+        n = ctypes.c_longlong()
+        with self._ctx():
+            _bcheck(load().dfv_batch_profile(self._h, int(bool(enable)), ms.ctypes.data_as(_dp), ctypes.byref(n)),
+                    self._h, "dfv_batch_profile")
+        return ms, n.value
+
+    def launch_count(self):
+        c = ctypes.c_longlong()
+        _bcheck(load().dfv_batch_launch_count(self._h, ctypes.byref(c)), self._h, "dfv_batch_launch_count")
         return c.value

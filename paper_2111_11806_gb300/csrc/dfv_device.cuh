@@ -383,7 +383,7 @@ __device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, S
 #pragma unroll
             for (int b = 0; b < DIM; b++) s.H[a][b] = (T)H[a][b];
     }
-    if (NMAT == 1) {
+    if constexpr (NMAT == 1) {
         // single material: the mixture rules reduce to the material's own closure
         const MatC<T> &m = matc<T>(g, 0);
         const Ref<T> r = mat_ref<T>(m, rhol[0], J2);
@@ -509,7 +509,7 @@ __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w
     for (int a = 0; a < DIM; a++) ke += T(0.5) * rho * u[a] * u[a];
     T num = q[L::IE] - ke, den = T(0);
     T rhol[NMAT];
-    if (NMAT == 1) {
+    if constexpr (NMAT == 1) {
         const MatC<T> &m = matc<T>(g, 0);
         const Ref<T> r = mat_ref<T>(m, rho, J2);
 #pragma unroll

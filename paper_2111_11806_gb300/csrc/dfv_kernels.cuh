@@ -261,8 +261,12 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
     __syncthreads();
 }
 
+// One tile of one SSP-RK3 stage, executed by a whole CTA: (tbx, tby, tbz) is
+// the tile position in tile units, tile_id its index among the ntiles tiles of
+// the grid (partials slot; the last of them to finish runs the finalize).
 template <class R, int DIM, int NMAT, bool SOLID, int STAGE>
-__global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(StageArgs a, GridP g)
+__device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, int tbx, int tby, int tbz,
+                                           long long tile_id, long long ntiles)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     using B = Box<DIM, (int)sizeof(R)>;
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(St
     const R *un = reinterpret_cast<const R *>(a.un);
     R *out = reinterpret_cast<R *>(a.out);
     const long long P = g.pitch;
-    const int ox = blockIdx.x * TL::TX, oy = blockIdx.y * TL::TY, oz = blockIdx.z * TL::TZ;
+    const int ox = tbx * TL::TX, oy = tby * TL::TY, oz = tbz * TL::TZ;
 
     // 1. primitives of the tile and its halo (the corner regions are unused)
     for (int i = threadIdx.x; i < B::N; i += TL::THREADS) {
@@ -374,8 +378,7 @@ __global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(St
     if (STAGE == 3 || (STAGE == 1 && a.want_force)) {
         block_reduce4<TL::THREADS>(red, sred);
         if (threadIdx.x == 0) {
-            const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-            double *pp = a.partials + 4 * b;
+            double *pp = a.partials + 4 * tile_id;
             if (STAGE == 3) pp[0] = red[0];
             else {
                 pp[1] = red[1];
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(St
     if (STAGE == 3 && a.final_mode) {
         // the last block to finish reduces every block's partials (fixed order)
         __shared__ unsigned int s_last;
-        const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
+        const long long nb = ntiles;
         if (threadIdx.x == 0) {
             __threadfence();
             const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
@@ -403,6 +406,14 @@ __global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(St
     }
 }
 
+template <class R, int DIM, int NMAT, bool SOLID, int STAGE>
+__global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(StageArgs a, GridP g)
+{
+    const long long tile = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    const long long nt = (long long)gridDim.x * gridDim.y * gridDim.z;
+    stage_tile<R, DIM, NMAT, SOLID, STAGE>(g, a, blockIdx.x, blockIdx.y, blockIdx.z, tile, nt);
+}
+
 // --------------------------------------------------------------- seeding
 
 // Rigid seeding (Sec. 3.2, original variant), one thread per cell, in place:
@@ -415,16 +426,14 @@ __global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(St
 // independent of thread order.  Evaluated in the storage precision (FP64
 // closures below phi = 1e-6 as everywhere in the FP32 form).
 template <class R, int DIM, int NMAT, bool SOLID>
-__global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
+__device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, long long c)
 {
     using L = Lay<DIM, NMAT, SOLID>;
-    R *U = reinterpret_cast<R *>(Uv);
     const GridC<R> &gc = gridc<R>(g);
     const long long P = g.pitch;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
-         c += (long long)gridDim.x * blockDim.x) {
+    {
         const R rc = U[L::IR * P + c];
-        if (!(rc > R(0.5))) continue;
+        if (!(rc > R(0.5))) return;
         int ijk[3];
         ijk[0] = (int)(c % g.n[0]);
         ijk[1] = (int)((c / g.n[0]) % g.n[1]);
@@ -440,7 +449,7 @@ __global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
             gr[d] = (U[L::IR * P + ch] - U[L::IR * P + cl]) / (R(2) * gc.dx[d]);
         }
         const R gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-        if (!(gn * gc.dxmin > R(1e-10))) continue;
+        if (!(gn * gc.dxmin > R(1e-10))) return;
         const R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
         R wi[L::NVAR];
         bool found = false;
@@ -490,7 +499,7 @@ __global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
             }
             found = true;
         }
-        if (!found) continue;
+        if (!found) return;
         R Pm[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -536,6 +545,15 @@ __global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
         for (int v = 0; v < L::NVAR; v++)
             if (v != L::IR) U[v * P + c] = q[v];
     }
+}
+
+template <class R, int DIM, int NMAT, bool SOLID>
+__global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
+{
+    R *U = reinterpret_cast<R *>(Uv);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x)
+        seed_cell<R, DIM, NMAT, SOLID>(U, ctl, g, c);
 }
 
 // ------------------------------------------------------------------ CFL
