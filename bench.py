@@ -250,8 +250,9 @@ def run_batched(torch, B, W, stream, args):
         stage_ms = float(pms[1] + pms[2] + pms[3]) / pn
         achieved = 8 * nvar * w * cells / (stage_ms * 1e-3) / 1e9
         rec = {"value": cells * k / (ms * 1e-3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
-               "autotune": {"ctas_per_sm": choice[0], "schedule": ["instance-order static", "largest-first static",
-                                                                    "largest-first dynamic"][choice[1]]},
+               "autotune": {"ctas_per_sm": choice[0] if choice[0] > 0 else "one CTA per work item",
+                            "schedule": ["instance-order static", "largest-first static",
+                                         "largest-first dynamic"][choice[1]]},
                "gpu_launches": int(launches),
                "phase_ms_per_step": {"seed": pms[0] / pn, "stage1": pms[1] / pn, "stage2": pms[2] / pn,
                                      "stage3": pms[3] / pn},
@@ -264,6 +265,34 @@ def run_batched(torch, B, W, stream, args):
         torch.cuda.synchronize()
     out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
     return out
+
+
+def run_sphere(torch, B, W, stream):
+    """256^3 sphere workload, FP32: event-timed steps and the stage roofline."""
+    peak, peak_kind = measured_peaks()
+    wl = W.sphere_3d(256)
+    g = B.Grid.from_workload(wl, precision=B.DFV_FP32, stream=stream)
+    g.run(2, 0.8)
+    k = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    g.run(k, 0.8)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    g.profile(True)
+    g.run(3, 0.8)
+    pms, pn = g.profile(False)
+    stage_ms = float(pms[1] + pms[2] + pms[3]) / pn
+    achieved = 8 * wl.nvar * 4 * wl.ncell / (stage_ms * 1e-3) / 1e9
+    del g
+    return {"workload": "sphere_3d_256^3_mach2.5_fp32", "cells": wl.ncell, "value": wl.ncell * k / (ms * 1e-3),
+            "unit": UNIT, "steps": k, "ms_per_step": ms / k,
+            "phase_ms_per_step": {"seed": pms[0] / pn, "stage1": pms[1] / pn, "stage2": pms[2] / pn,
+                                  "stage3": pms[3] / pn},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "kernel": "k_stage 3-D, FP32"}}
 
 
 def run_ours(args):
@@ -345,6 +374,11 @@ def run_ours(args):
     if not args.no_batched:
         batched = run_batched(torch, B, W, stream, args)
 
+    # --- 3-D: Mach 2.5 shock over a rigid sphere, 256^3 cells (0.40 GB per FP32 state copy)
+    sphere = None
+    if not args.no_batched:
+        sphere = run_sphere(torch, B, W, stream)
+
     clk = clocks.stop() if clocks else None
 
     # --- accuracy of the FP32 form after the timed steps: relative L1 of the
@@ -399,6 +433,7 @@ def run_ours(args):
                                "finalize": prof32[0][4] / prof32[1]},
         "cpu_baseline": cpu,
         "batched": batched,
+        "sphere_3d": sphere,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io / job_steps,
                 "d2h_bytes_per_step": bytes_io / job_steps,
                 "job": "set_fields(host) + %d steps + get_fields(host), %d jobs" % (job_steps, jobs)},

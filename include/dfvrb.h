@@ -202,9 +202,10 @@ dfv_status dfv_batch_get_fields(dfv_batch *b, int i, double *out, int which, int
 dfv_status dfv_batch_run(dfv_batch *b, int steps, double cfl, double t_end);
 /* Time trial steps of every (CTAs per SM, item schedule) candidate and keep
  * the fastest; the fields and times are restored afterwards.  choice_out (may
- * be NULL) receives {ctas_per_sm, schedule}: 0 instance order with static
- * round-robin assignment, 1 largest instances first, static, 2 largest
- * instances first from a dynamic queue. */
+ * be NULL) receives {ctas_per_sm, schedule}: ctas_per_sm 0 launches one CTA per
+ * work item, k > 0 a persistent grid of k CTAs per SM; schedule 0 instance
+ * order with static round-robin assignment, 1 largest instances first,
+ * static, 2 largest instances first from a dynamic queue. */
 dfv_status dfv_batch_autotune(dfv_batch *b, int trial_steps, double cfl, int choice_out[2]);
 /* Set the persistent grid (CTAs per SM, clipped to the occupancy limit) and
  * the schedule explicitly. */

@@ -51,7 +51,7 @@ __device__ __forceinline__ void load_inst(const BatchInst *src, BatchInst *dst)
 }
 
 template <class R, int NMAT, int STAGE>
-__global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS) k_batch_stage(BatchArgs b)
+__global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_stage(BatchArgs b)
 {
     __shared__ BatchInst s_inst;
     __shared__ long long s_item;

@@ -165,8 +165,11 @@ BatchArgs args(dfv_batch *b, const void *in, const void *un, void *out, int fina
     return a;
 }
 
+// ctas_per_sm = 0: one CTA per work item (the hardware schedules them);
+// otherwise a persistent grid of ctas_per_sm CTAs per SM loops over the items.
 int grid_size(dfv_batch *b)
 {
+    if (b->ctas_per_sm <= 0) return (int)std::max(1LL, b->plan.nitems);
     const long long persistent = (long long)b->sm_count * b->ctas_per_sm;
     return (int)std::max(1LL, std::min(persistent, b->plan.nitems));
 }
@@ -505,7 +508,7 @@ dfv_status dfv_batch_autotune(dfv_batch *b, int trial_steps, double cfl, int cho
     const bool prof = b->prof;
     b->prof = false;
     for (int sched = 0; sched < 3; sched++)
-        for (int c = 1; c <= b->max_ctas; c++) {
+        for (int c = 0; c <= b->max_ctas; c++) {
             b->schedule = sched;
             b->ctas_per_sm = c;
             batch_step(b, false);   // warm
@@ -543,7 +546,7 @@ dfv_status dfv_batch_autotune(dfv_batch *b, int trial_steps, double cfl, int cho
 dfv_status dfv_batch_set_schedule(dfv_batch *b, int ctas_per_sm, int schedule)
 {
     if (!b) return DFV_ERR_ARG;
-    if (ctas_per_sm < 1 || schedule < 0 || schedule > 2)
+    if (ctas_per_sm < 0 || schedule < 0 || schedule > 2)
         return bfail(b, DFV_ERR_ARG, "dfv_batch_set_schedule: bad arguments");
     b->ctas_per_sm = std::min(ctas_per_sm, b->max_ctas);
     b->schedule = schedule;

@@ -36,7 +36,7 @@ def test_batch_instances_equal_single_grids(precision):
 
 
 @pytest.mark.parametrize("schedule", [0, 1, 2])
-@pytest.mark.parametrize("ctas", [1, 2])
+@pytest.mark.parametrize("ctas", [0, 1, 2])
 def test_batch_schedules_are_equivalent(schedule, ctas):
     wls = instances()
     ref = B.Batch(wls, precision=B.DFV_FP32)
@@ -77,7 +77,7 @@ def test_batch_autotune_restores_state():
     before = [b.get_fields(i) for i in range(len(wls))]
     t_before = [b.time(i)[0] for i in range(len(wls))]
     ctas, sched = b.autotune(trial_steps=2, cfl=0.8)
-    assert ctas >= 1 and sched in (0, 1, 2)
+    assert ctas >= 0 and sched in (0, 1, 2)
     for i in range(len(wls)):
         np.testing.assert_array_equal(b.get_fields(i), before[i])
         assert b.time(i)[0] == t_before[i]
