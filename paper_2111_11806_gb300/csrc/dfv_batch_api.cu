@@ -174,15 +174,20 @@ int grid_size(dfv_batch *b)
     return (int)std::max(1LL, std::min(persistent, b->plan.nitems));
 }
 
-// one launch of a phase, with the dynamic-queue reset when that schedule is used
+// one launch of a phase, with the dynamic-queue reset when that schedule is
+// used.  Seeding (phase 0) and the CFL reduction (phase 4) do little work per
+// item, so they always run one CTA per item and let the hardware overlap the
+// items' memory latency.
 dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out, int final_mode, int slot)
 {
     BatchArgs a = args(b, in, un, out, final_mode);
-    if (b->schedule == 2) {
+    const bool light = (ph == 0 || ph == 4);
+    if (b->schedule == 2 && !light) {
         a.queue = b->d_queue + slot;
         B_CU(b, cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), b->stream), "queue reset");
     }
-    B_CU(b, b->kern.launch(ph, grid_size(b), a, b->stream), "batch kernel");
+    const int grid = light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b);
+    B_CU(b, b->kern.launch(ph, grid, a, b->stream), "batch kernel");
     b->launches++;
     return DFV_OK;
 }
