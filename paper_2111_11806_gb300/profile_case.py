@@ -21,7 +21,10 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=0, help="run a batch of this many ellipse instances instead")
     args = ap.parse_args(argv)
+    if args.batch:
+        return run_batch(args)
     import torch
     import workloads as W
     from paper_2111_11806_gb300 import binding as B
@@ -41,6 +44,29 @@ def main(argv=None):
     print(json.dumps({"workload": wl.name, "precision": args.precision, "cells": wl.ncell, "steps": n,
                       "ms_per_step": {"seed": ms[0] / n, "stage1": ms[1] / n, "stage2": ms[2] / n,
                                       "stage3": ms[3] / n, "finalize": ms[4] / n}}))
+    return 0
+
+
+def run_batch(args):
+    import torch
+    import workloads as W
+    from paper_2111_11806_gb300 import binding as B
+    B.load()
+    wls = [W.ellipse_instance(i) for i in range(args.batch)]
+    prec = B.DFV_FP32 if args.precision == "fp32" else B.DFV_FP64
+    stream = torch.cuda.Stream()
+    bt = B.Batch(wls, precision=prec, stream=stream)
+    bt.set_all_fields()
+    bt.set_schedule(2, 2)
+    bt.run(1, 0.8)
+    bt.profile(True)
+    bt.run(args.steps, 0.8)
+    ms, n = bt.profile(False)
+    bt.time(0)
+    print(json.dumps({"workload": "batch_%d_ellipses" % args.batch, "precision": args.precision,
+                      "cells": bt.total_cells, "steps": n,
+                      "ms_per_step": {"seed": ms[0] / n, "stage1": ms[1] / n, "stage2": ms[2] / n,
+                                      "stage3": ms[3] / n}}))
     return 0
 
 
