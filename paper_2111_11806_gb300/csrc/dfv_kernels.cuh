@@ -195,6 +195,159 @@ static __global__ void __launch_bounds__(1024) k_finalize(Ctl *ctl, const double
     finalize_block<1024>(ctl, partials, nb_cfl, nb_force, mode, dim, dx0, dx1, dx2, sred);
 }
 
+// --------------------------------------------------------------- seeding
+
+// Rigid seeding (Sec. 3.2, original variant), one thread per cell, in place:
+// cells with r > 0.5 and |grad r| dx_min > 1e-10 get the outward normal
+// n = -grad r/|grad r| (Youngs, Sec. 3.3), probe points at 1.0, 1.5, ..., 4.0
+// dx_min along n, the first point whose 2^dim enclosing cell centres are in the
+// domain (wrapped if periodic) with r < 0.5 is interpolated multilinearly in
+// the primitives, and u <- (I - 2nn^T) u + 2 (v_r.n) n, V <- (I - 2nn^T) V (I - 2nn^T).
+// Only r < 0.5 cells are read and only r > 0.5 cells written, so the update is
+// independent of thread order.  Evaluated in the storage precision (FP64
+// closures below phi = 1e-6 as everywhere in the FP32 form).
+// The seeded conserved state of rigid cell c (Sec. 3.2), computed from the
+// fluid (r < 0.5) cells of U only; false when the cell is not seeded (r <= 0.5,
+// no gradient, or no valid probe point).
+template <class R, int DIM, int NMAT, bool SOLID>
+__device__ __noinline__ bool seed_compute(const R *U, const Ctl *ctl, const GridP &g, long long c, R *q)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    const GridC<R> &gc = gridc<R>(g);
+    const long long P = g.pitch;
+    {
+        const R rc = U[L::IR * P + c];
+        if (!(rc > R(0.5))) return false;
+        int ijk[3];
+        ijk[0] = (int)(c % g.n[0]);
+        ijk[1] = (int)((c / g.n[0]) % g.n[1]);
+        ijk[2] = (int)(c / ((long long)g.n[0] * g.n[1]));
+        R gr[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            int lo[3] = {ijk[0], ijk[1], ijk[2]}, hi[3] = {ijk[0], ijk[1], ijk[2]};
+            lo[d] = map_idx(ijk[d] - 1, g.n[d], g.periodic[d]);
+            hi[d] = map_idx(ijk[d] + 1, g.n[d], g.periodic[d]);
+            const long long cl = lo[0] + (long long)g.n[0] * (lo[1] + (long long)g.n[1] * lo[2]);
+            const long long ch = hi[0] + (long long)g.n[0] * (hi[1] + (long long)g.n[1] * hi[2]);
+            gr[d] = (U[L::IR * P + ch] - U[L::IR * P + cl]) / (R(2) * gc.dx[d]);
+        }
+        const R gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+        if (!(gn * gc.dxmin > R(1e-10))) return false;
+        const R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
+        R wi[L::NVAR];
+        bool found = false;
+        for (int step = 0; step < 7 && !found; step++) {
+            const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
+            int base[3] = {0, 0, 0};
+            R fr[3] = {R(0), R(0), R(0)};
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+                const R xp = gc.lo[d] + ((R)ijk[d] + R(0.5)) * gc.dx[d] + sd * nv[d];
+                const R fi = (xp - gc.lo[d]) / gc.dx[d] - R(0.5);
+                const R fl = floor(fi);
+                base[d] = (int)fl;
+                fr[d] = fi - fl;
+            }
+            long long cidx[1 << DIM];
+            R wts[1 << DIM];
+            bool ok = true;
+#pragma unroll
+            for (int m = 0; m < (1 << DIM); m++) {
+                int ci[3] = {0, 0, 0};
+                R wt = R(1);
+#pragma unroll
+                for (int d = 0; d < DIM; d++) {
+                    const int bit = (m >> d) & 1;
+                    int ii = base[d] + bit;
+                    if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
+                    else if (ii < 0 || ii > g.n[d] - 1) ok = false;
+                    ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
+                    wt *= bit ? fr[d] : (R(1) - fr[d]);
+                }
+                cidx[m] = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
+                wts[m] = wt;
+                if (ok && !(U[L::IR * P + cidx[m]] < R(0.5))) ok = false;
+            }
+            if (!ok) continue;
+#pragma unroll
+            for (int v = 0; v < L::NVAR; v++) wi[v] = R(0);
+#pragma unroll
+            for (int m = 0; m < (1 << DIM); m++) {
+                R q[L::NVAR], w[L::NVAR];
+#pragma unroll
+                for (int v = 0; v < L::NVAR; v++) q[v] = U[v * P + cidx[m]];
+                cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
+#pragma unroll
+                for (int v = 0; v < L::NVAR; v++) wi[v] += wts[m] * w[v];
+            }
+            found = true;
+        }
+        if (!found) return false;
+        R Pm[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) Pm[i][j] = (i == j ? R(1) : R(0)) - R(2) * nv[i] * nv[j];
+        const R vn = ctl_v<R>(ctl, 0) * nv[0] + ctl_v<R>(ctl, 1) * nv[1] + ctl_v<R>(ctl, 2) * nv[2];
+        R u[3] = {R(0), R(0), R(0)}, unew[3];
+#pragma unroll
+        for (int a = 0; a < DIM; a++) u[a] = wi[L::IMOM + a];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            unew[i] = R(2) * vn * nv[i];
+#pragma unroll
+            for (int j = 0; j < 3; j++) unew[i] += Pm[i][j] * u[j];
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; a++) wi[L::IMOM + a] = unew[a];
+        if (SOLID) {
+            double A[3][3], PA[3][3];
+            unpack_A<R, DIM, NMAT, SOLID>(wi, A);
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    double sm = 0.0;
+#pragma unroll
+                    for (int k = 0; k < 3; k++) sm += (double)Pm[i][k] * A[k][j];
+                    PA[i][j] = sm;
+                }
+#pragma unroll
+            for (int cc = 0; cc < L::NV; cc++) {
+                const int i = v_row(DIM, cc), j = v_col(DIM, cc);
+                double sm = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; k++) sm += PA[i][k] * (double)Pm[k][j];
+                wi[L::IV + cc] = (R)sm;
+            }
+        }
+        wi[L::IR] = rc;
+        prim_to_cons<R, DIM, NMAT, SOLID>(g, wi, q);
+        return true;
+    }
+}
+
+template <class R, int DIM, int NMAT, bool SOLID>
+__device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, long long c)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    R q[L::NVAR];
+    if (!seed_compute<R, DIM, NMAT, SOLID>(U, ctl, g, c, q)) return;
+#pragma unroll
+    for (int v = 0; v < L::NVAR; v++)
+        if (v != L::IR) U[v * g.pitch + c] = q[v];
+}
+
+template <class R, int DIM, int NMAT, bool SOLID>
+__global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
+{
+    R *U = reinterpret_cast<R *>(Uv);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x)
+        seed_cell<R, DIM, NMAT, SOLID>(U, ctl, g, c);
+}
+
 // --------------------------------------------------------------- stage
 
 struct StageArgs {
@@ -205,6 +358,8 @@ struct StageArgs {
     double *partials;   // 4 doubles per block
     int want_force;
     int final_mode;     // stage 3: finalize mode run by the last block (0: none)
+    int seed;           // stage 1: seed rigid cells while loading the tile and write
+                        // the seeded states of the tile's cells back to U^n
 };
 
 template <class R, int DIM, int NMAT, bool SOLID, int D>
@@ -296,6 +451,24 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
         R q[L::NVAR], w[L::NVAR];
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) q[v] = in[v * P + c];
+        if (STAGE == 1 && a.seed && q[L::IR] > R(0.5)) {
+            // rigid cell: its seeded state (Sec. 3.2) replaces it in the stencil;
+            // the tile's own cells are written back for stages 2 and 3
+            R qs[L::NVAR];
+            if (seed_compute<R, DIM, NMAT, SOLID>(in, a.ctl, g, c, qs)) {
+#pragma unroll
+                for (int v = 0; v < L::NVAR; v++)
+                    if (v != L::IR) q[v] = qs[v];
+                const bool mine = outside == 0 && ox + lx < g.n[0] && (DIM < 2 || oy + ly < g.n[1]) &&
+                                  (DIM < 3 || oz + lz < g.n[2]);
+                if (mine) {
+                    R *unw = const_cast<R *>(un);
+#pragma unroll
+                    for (int v = 0; v < L::NVAR; v++)
+                        if (v != L::IR) unw[v * P + c] = q[v];
+                }
+            }
+        }
         cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) sW[v * B::N + i] = w[v];
@@ -407,153 +580,11 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
 }
 
 template <class R, int DIM, int NMAT, bool SOLID, int STAGE>
-__global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(StageArgs a, GridP g)
+__global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS, (SOLID || NMAT > 1) ? 1 : 2) k_stage(StageArgs a, GridP g)
 {
     const long long tile = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     const long long nt = (long long)gridDim.x * gridDim.y * gridDim.z;
     stage_tile<R, DIM, NMAT, SOLID, STAGE>(g, a, blockIdx.x, blockIdx.y, blockIdx.z, tile, nt);
-}
-
-// --------------------------------------------------------------- seeding
-
-// Rigid seeding (Sec. 3.2, original variant), one thread per cell, in place:
-// cells with r > 0.5 and |grad r| dx_min > 1e-10 get the outward normal
-// n = -grad r/|grad r| (Youngs, Sec. 3.3), probe points at 1.0, 1.5, ..., 4.0
-// dx_min along n, the first point whose 2^dim enclosing cell centres are in the
-// domain (wrapped if periodic) with r < 0.5 is interpolated multilinearly in
-// the primitives, and u <- (I - 2nn^T) u + 2 (v_r.n) n, V <- (I - 2nn^T) V (I - 2nn^T).
-// Only r < 0.5 cells are read and only r > 0.5 cells written, so the update is
-// independent of thread order.  Evaluated in the storage precision (FP64
-// closures below phi = 1e-6 as everywhere in the FP32 form).
-template <class R, int DIM, int NMAT, bool SOLID>
-__device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, long long c)
-{
-    using L = Lay<DIM, NMAT, SOLID>;
-    const GridC<R> &gc = gridc<R>(g);
-    const long long P = g.pitch;
-    {
-        const R rc = U[L::IR * P + c];
-        if (!(rc > R(0.5))) return;
-        int ijk[3];
-        ijk[0] = (int)(c % g.n[0]);
-        ijk[1] = (int)((c / g.n[0]) % g.n[1]);
-        ijk[2] = (int)(c / ((long long)g.n[0] * g.n[1]));
-        R gr[3] = {R(0), R(0), R(0)};
-#pragma unroll
-        for (int d = 0; d < DIM; d++) {
-            int lo[3] = {ijk[0], ijk[1], ijk[2]}, hi[3] = {ijk[0], ijk[1], ijk[2]};
-            lo[d] = map_idx(ijk[d] - 1, g.n[d], g.periodic[d]);
-            hi[d] = map_idx(ijk[d] + 1, g.n[d], g.periodic[d]);
-            const long long cl = lo[0] + (long long)g.n[0] * (lo[1] + (long long)g.n[1] * lo[2]);
-            const long long ch = hi[0] + (long long)g.n[0] * (hi[1] + (long long)g.n[1] * hi[2]);
-            gr[d] = (U[L::IR * P + ch] - U[L::IR * P + cl]) / (R(2) * gc.dx[d]);
-        }
-        const R gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-        if (!(gn * gc.dxmin > R(1e-10))) return;
-        const R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
-        R wi[L::NVAR];
-        bool found = false;
-        for (int step = 0; step < 7 && !found; step++) {
-            const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
-            int base[3] = {0, 0, 0};
-            R fr[3] = {R(0), R(0), R(0)};
-#pragma unroll
-            for (int d = 0; d < DIM; d++) {
-                const R xp = gc.lo[d] + ((R)ijk[d] + R(0.5)) * gc.dx[d] + sd * nv[d];
-                const R fi = (xp - gc.lo[d]) / gc.dx[d] - R(0.5);
-                const R fl = floor(fi);
-                base[d] = (int)fl;
-                fr[d] = fi - fl;
-            }
-            long long cidx[1 << DIM];
-            R wts[1 << DIM];
-            bool ok = true;
-#pragma unroll
-            for (int m = 0; m < (1 << DIM); m++) {
-                int ci[3] = {0, 0, 0};
-                R wt = R(1);
-#pragma unroll
-                for (int d = 0; d < DIM; d++) {
-                    const int bit = (m >> d) & 1;
-                    int ii = base[d] + bit;
-                    if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
-                    else if (ii < 0 || ii > g.n[d] - 1) ok = false;
-                    ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
-                    wt *= bit ? fr[d] : (R(1) - fr[d]);
-                }
-                cidx[m] = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
-                wts[m] = wt;
-                if (ok && !(U[L::IR * P + cidx[m]] < R(0.5))) ok = false;
-            }
-            if (!ok) continue;
-#pragma unroll
-            for (int v = 0; v < L::NVAR; v++) wi[v] = R(0);
-#pragma unroll
-            for (int m = 0; m < (1 << DIM); m++) {
-                R q[L::NVAR], w[L::NVAR];
-#pragma unroll
-                for (int v = 0; v < L::NVAR; v++) q[v] = U[v * P + cidx[m]];
-                cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
-#pragma unroll
-                for (int v = 0; v < L::NVAR; v++) wi[v] += wts[m] * w[v];
-            }
-            found = true;
-        }
-        if (!found) return;
-        R Pm[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) Pm[i][j] = (i == j ? R(1) : R(0)) - R(2) * nv[i] * nv[j];
-        const R vn = ctl_v<R>(ctl, 0) * nv[0] + ctl_v<R>(ctl, 1) * nv[1] + ctl_v<R>(ctl, 2) * nv[2];
-        R u[3] = {R(0), R(0), R(0)}, unew[3];
-#pragma unroll
-        for (int a = 0; a < DIM; a++) u[a] = wi[L::IMOM + a];
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            unew[i] = R(2) * vn * nv[i];
-#pragma unroll
-            for (int j = 0; j < 3; j++) unew[i] += Pm[i][j] * u[j];
-        }
-#pragma unroll
-        for (int a = 0; a < DIM; a++) wi[L::IMOM + a] = unew[a];
-        if (SOLID) {
-            double A[3][3], PA[3][3];
-            unpack_A<R, DIM, NMAT, SOLID>(wi, A);
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) {
-                    double sm = 0.0;
-#pragma unroll
-                    for (int k = 0; k < 3; k++) sm += (double)Pm[i][k] * A[k][j];
-                    PA[i][j] = sm;
-                }
-#pragma unroll
-            for (int cc = 0; cc < L::NV; cc++) {
-                const int i = v_row(DIM, cc), j = v_col(DIM, cc);
-                double sm = 0.0;
-#pragma unroll
-                for (int k = 0; k < 3; k++) sm += PA[i][k] * (double)Pm[k][j];
-                wi[L::IV + cc] = (R)sm;
-            }
-        }
-        wi[L::IR] = rc;
-        R q[L::NVAR];
-        prim_to_cons<R, DIM, NMAT, SOLID>(g, wi, q);
-#pragma unroll
-        for (int v = 0; v < L::NVAR; v++)
-            if (v != L::IR) U[v * P + c] = q[v];
-    }
-}
-
-template <class R, int DIM, int NMAT, bool SOLID>
-__global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
-{
-    R *U = reinterpret_cast<R *>(Uv);
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
-         c += (long long)gridDim.x * blockDim.x)
-        seed_cell<R, DIM, NMAT, SOLID>(U, ctl, g, c);
 }
 
 // ------------------------------------------------------------------ CFL
