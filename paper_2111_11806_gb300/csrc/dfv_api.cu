@@ -223,7 +223,7 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false)
         }
         DFV_CU(g, cudaEventRecord(ev[0], g->stream), "event");
     }
-    // seeding (Sec. 3.2) runs inside stage 1, while it loads its tiles
+    DFV_CU(g, g->ops->seed(g->g, g->U, g->ctl, g->stream), "k_seed");
     if (rec) DFV_CU(g, cudaEventRecord(ev[1], g->stream), "event");
     DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, 0, g->stream),
            "k_stage<1>");
@@ -239,7 +239,7 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false)
         DFV_CU(g, cudaEventRecord(ev[5], g->stream), "event");
         g->ev_steps.push_back(ev);
     }
-    g->launches += 3;
+    g->launches += 4;
     return DFV_OK;
 }
 
@@ -528,7 +528,7 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
     for (int k = 0; k < steps; k++) {
         if (use_graph) {
             DFV_CU(g, cudaGraphLaunch(g->graph, g->stream), "graph launch");
-            g->launches += 3;
+            g->launches += 4;
         } else {
             s = launch_step(g, 8);
             if (s != DFV_OK) return s;

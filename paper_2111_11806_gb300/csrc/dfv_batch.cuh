@@ -75,7 +75,6 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_s
         a.partials = b.partials + 4 * I.part0;
         a.want_force = 0;
         a.final_mode = b.final_mode;
-        a.seed = (STAGE == 1) ? 1 : 0;
         stage_tile<R, 2, NMAT, false, STAGE>(I.g, a, w.y % I.tiles_x, w.y / I.tiles_x, 0, w.y, I.ntiles);
     }
 }

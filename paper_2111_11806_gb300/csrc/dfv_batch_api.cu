@@ -212,8 +212,8 @@ dfv_status batch_step(dfv_batch *b, bool capturing)
         for (auto &e : ev) e = take_ev(b);
         B_CU(b, cudaEventRecord(ev[0], b->stream), "event");
     }
-    // seeding (Sec. 3.2) runs inside stage 1, while it loads its tiles
-    dfv_status s = DFV_OK;
+    dfv_status s = phase(b, 0, b->U, b->U, b->U, 0, 0);
+    if (s != DFV_OK) return s;
     if (rec) B_CU(b, cudaEventRecord(ev[1], b->stream), "event");
     if ((s = phase(b, 1, b->U, b->U, b->U1, 0, 1)) != DFV_OK) return s;
     if (rec) B_CU(b, cudaEventRecord(ev[2], b->stream), "event");
@@ -485,7 +485,7 @@ dfv_status dfv_batch_run(dfv_batch *b, int steps, double cfl, double t_end)
     for (int k = 0; k < steps; k++) {
         if (use_graph) {
             B_CU(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
-            b->launches += 3;
+            b->launches += 4;
         } else if ((s = batch_step(b, false)) != DFV_OK) {
             return s;
         }

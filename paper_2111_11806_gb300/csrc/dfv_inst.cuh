@@ -52,7 +52,6 @@ struct Impl {
         a.partials = partials;
         a.want_force = want_force;
         a.final_mode = final_mode;
-        a.seed = (s == 1) ? 1 : 0;
         if (s == 1) return stage_s<1>(g, a, st);
         if (s == 2) return stage_s<2>(g, a, st);
         return stage_s<3>(g, a, st);

@@ -210,7 +210,7 @@ static __global__ void __launch_bounds__(1024) k_finalize(Ctl *ctl, const double
 // fluid (r < 0.5) cells of U only; false when the cell is not seeded (r <= 0.5,
 // no gradient, or no valid probe point).
 template <class R, int DIM, int NMAT, bool SOLID>
-__device__ __noinline__ bool seed_compute(const R *U, const Ctl *ctl, const GridP &g, long long c, R *q)
+__device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const GridP &g, long long c, R *q)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     const GridC<R> &gc = gridc<R>(g);
@@ -235,10 +235,45 @@ __device__ __noinline__ bool seed_compute(const R *U, const Ctl *ctl, const Grid
         const R gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
         if (!(gn * gc.dxmin > R(1e-10))) return false;
         const R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
-        R wi[L::NVAR];
-        bool found = false;
-        for (int step = 0; step < 7 && !found; step++) {
+        // Probe steps s = 1.0, 1.5, ..., 4.0 dx_min: the r values of all steps'
+        // enclosing cells are fetched first (independent loads, one memory
+        // round trip), then the first valid step is taken.
+        constexpr int NC = 1 << DIM;
+        int first = -1;
+        unsigned int valid = 0u;
+#pragma unroll
+        for (int step = 0; step < 7; step++) {
             const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
+            int base[3] = {0, 0, 0};
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+                const R xp = gc.lo[d] + ((R)ijk[d] + R(0.5)) * gc.dx[d] + sd * nv[d];
+                const R fi = (xp - gc.lo[d]) / gc.dx[d] - R(0.5);
+                base[d] = (int)floor(fi);
+            }
+            bool ok = true;
+            R rmax = R(0);
+#pragma unroll
+            for (int m = 0; m < NC; m++) {
+                int ci[3] = {0, 0, 0};
+#pragma unroll
+                for (int d = 0; d < DIM; d++) {
+                    int ii = base[d] + ((m >> d) & 1);
+                    if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
+                    else if (ii < 0 || ii > g.n[d] - 1) ok = false;
+                    ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
+                }
+                const R rv = U[L::IR * P + ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2])];
+                rmax = (rv < R(0.5)) ? rmax : R(1);
+            }
+            if (ok && rmax == R(0)) valid |= 1u << step;
+        }
+        if (!valid) return false;
+        first = __ffs(valid) - 1;
+        // interpolation at the chosen probe point
+        R wi[L::NVAR];
+        {
+            const R sd = (R(1) + R(0.5) * (R)first) * gc.dxmin;
             int base[3] = {0, 0, 0};
             R fr[3] = {R(0), R(0), R(0)};
 #pragma unroll
@@ -249,11 +284,10 @@ __device__ __noinline__ bool seed_compute(const R *U, const Ctl *ctl, const Grid
                 base[d] = (int)fl;
                 fr[d] = fi - fl;
             }
-            long long cidx[1 << DIM];
-            R wts[1 << DIM];
-            bool ok = true;
 #pragma unroll
-            for (int m = 0; m < (1 << DIM); m++) {
+            for (int v = 0; v < L::NVAR; v++) wi[v] = R(0);
+#pragma unroll
+            for (int m = 0; m < NC; m++) {
                 int ci[3] = {0, 0, 0};
                 R wt = R(1);
 #pragma unroll
@@ -261,29 +295,18 @@ __device__ __noinline__ bool seed_compute(const R *U, const Ctl *ctl, const Grid
                     const int bit = (m >> d) & 1;
                     int ii = base[d] + bit;
                     if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
-                    else if (ii < 0 || ii > g.n[d] - 1) ok = false;
-                    ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
+                    ci[d] = ii;
                     wt *= bit ? fr[d] : (R(1) - fr[d]);
                 }
-                cidx[m] = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
-                wts[m] = wt;
-                if (ok && !(U[L::IR * P + cidx[m]] < R(0.5))) ok = false;
-            }
-            if (!ok) continue;
-#pragma unroll
-            for (int v = 0; v < L::NVAR; v++) wi[v] = R(0);
-#pragma unroll
-            for (int m = 0; m < (1 << DIM); m++) {
+                const long long cc = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
                 R q[L::NVAR], w[L::NVAR];
 #pragma unroll
-                for (int v = 0; v < L::NVAR; v++) q[v] = U[v * P + cidx[m]];
+                for (int v = 0; v < L::NVAR; v++) q[v] = U[v * P + cc];
                 cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
 #pragma unroll
-                for (int v = 0; v < L::NVAR; v++) wi[v] += wts[m] * w[v];
+                for (int v = 0; v < L::NVAR; v++) wi[v] += wt * w[v];
             }
-            found = true;
         }
-        if (!found) return false;
         R Pm[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -358,8 +381,6 @@ struct StageArgs {
     double *partials;   // 4 doubles per block
     int want_force;
     int final_mode;     // stage 3: finalize mode run by the last block (0: none)
-    int seed;           // stage 1: seed rigid cells while loading the tile and write
-                        // the seeded states of the tile's cells back to U^n
 };
 
 template <class R, int DIM, int NMAT, bool SOLID, int D>
@@ -451,24 +472,6 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
         R q[L::NVAR], w[L::NVAR];
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) q[v] = in[v * P + c];
-        if (STAGE == 1 && a.seed && q[L::IR] > R(0.5)) {
-            // rigid cell: its seeded state (Sec. 3.2) replaces it in the stencil;
-            // the tile's own cells are written back for stages 2 and 3
-            R qs[L::NVAR];
-            if (seed_compute<R, DIM, NMAT, SOLID>(in, a.ctl, g, c, qs)) {
-#pragma unroll
-                for (int v = 0; v < L::NVAR; v++)
-                    if (v != L::IR) q[v] = qs[v];
-                const bool mine = outside == 0 && ox + lx < g.n[0] && (DIM < 2 || oy + ly < g.n[1]) &&
-                                  (DIM < 3 || oz + lz < g.n[2]);
-                if (mine) {
-                    R *unw = const_cast<R *>(un);
-#pragma unroll
-                    for (int v = 0; v < L::NVAR; v++)
-                        if (v != L::IR) unw[v * P + c] = q[v];
-                }
-            }
-        }
         cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) sW[v * B::N + i] = w[v];
@@ -580,7 +583,7 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
 }
 
 template <class R, int DIM, int NMAT, bool SOLID, int STAGE>
-__global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS, (SOLID || NMAT > 1) ? 1 : 2) k_stage(StageArgs a, GridP g)
+__global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(StageArgs a, GridP g)
 {
     const long long tile = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     const long long nt = (long long)gridDim.x * gridDim.y * gridDim.z;
