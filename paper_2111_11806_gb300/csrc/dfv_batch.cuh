@@ -79,33 +79,17 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_s
     }
 }
 
-// Rigid seeding of every instance, tile by tile (one thread per cell).
+// Rigid seeding of every instance: blockIdx.y is the instance, the blocks of
+// that row stride over its cells; the instance record is read through the
+// cache, and only by threads whose cell is rigid.
 template <class R, int NMAT>
-__global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS) k_batch_seed(BatchArgs b)
+__global__ void __launch_bounds__(256) k_batch_seed(BatchArgs b)
 {
-    using TL = Tile<2, (int)sizeof(R)>;
-    __shared__ BatchInst s_inst;
-    __shared__ long long s_item;
-    __shared__ int s_cur;
-    if (threadIdx.x == 0) s_cur = -1;
-    for (long long it = next_item(b, -1, &s_item); it < b.nitems; it = next_item(b, it, &s_item)) {
-        const int2 w = b.items[it];
-        __syncthreads();
-        if (s_cur != w.x) {
-            load_inst(&b.inst[w.x], &s_inst);
-            __syncthreads();
-            if (threadIdx.x == 0) s_cur = w.x;
-        }
-        __syncthreads();
-        const BatchInst &I = s_inst;
-        if (threadIdx.x < TL::TX * TL::TY) {
-            const int gx = (w.y % I.tiles_x) * TL::TX + threadIdx.x % TL::TX;
-            const int gy = (w.y / I.tiles_x) * TL::TY + threadIdx.x / TL::TX;
-            if (gx < I.g.n[0] && gy < I.g.n[1])
-                seed_cell<R, 2, NMAT, false>(reinterpret_cast<R *>(const_cast<void *>(b.in)) + I.off, I.ctl, I.g,
-                                             gx + (long long)I.g.n[0] * gy);
-        }
-    }
+    const BatchInst &I = b.inst[blockIdx.y];
+    R *U = reinterpret_cast<R *>(const_cast<void *>(b.in)) + I.off;
+    const long long nc = I.g.ncell;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x)
+        seed_cell<R, 2, NMAT, false>(U, I.ctl, I.g, c);
 }
 
 // CFL wave speed of every instance's stored state; the last tile of each
@@ -216,7 +200,7 @@ struct BK {
     static cudaError_t launch(int phase, int grid, const BatchArgs &a, cudaStream_t st)
     {
         switch (phase) {
-        case 0: k_batch_seed<R, NMAT><<<grid, threads, 0, st>>>(a); break;
+        case 0: k_batch_seed<R, NMAT><<<dim3(32, grid), 256, 0, st>>>(a); break;
         case 1: k_batch_stage<R, NMAT, 1><<<grid, threads, smem, st>>>(a); break;
         case 2: k_batch_stage<R, NMAT, 2><<<grid, threads, smem, st>>>(a); break;
         case 3: k_batch_stage<R, NMAT, 3><<<grid, threads, smem, st>>>(a); break;

@@ -186,7 +186,8 @@ dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out
         a.queue = b->d_queue + slot;
         B_CU(b, cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), b->stream), "queue reset");
     }
-    const int grid = light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b);
+    // seeding: one row of blocks per instance; CFL: one CTA per item
+    const int grid = ph == 0 ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
     B_CU(b, b->kern.launch(ph, grid, a, b->stream), "batch kernel");
     b->launches++;
     return DFV_OK;
