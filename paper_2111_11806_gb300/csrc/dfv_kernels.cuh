@@ -137,6 +137,24 @@ __device__ __forceinline__ void block_reduce4(double v[4], double *scratch /* 4*
     }
 }
 
+// Block maximum of one value per thread (fixed order; result in thread 0).
+template <int THREADS, class T>
+__device__ __forceinline__ T block_max(T v, T *scratch /* 32 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = m_max(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        constexpr int NW = (THREADS + 31) / 32;
+        T r = scratch[0];
+        for (int w = 1; w < NW; w++) r = m_max(r, scratch[w]);
+        v = r;
+    }
+    return v;
+}
+
 // ------------------------------------------------------------ finalize
 
 // mode bit 0: reduce the CFL partials (nb_cfl blocks) into ctl->smax
@@ -152,13 +170,16 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     if (mode & 1)
         for (long long b = threadIdx.x; b < nb_cfl; b += THREADS) red[0] = fmax(red[0], partials[4 * b]);
-    if (mode & 2)
+    if (mode & 2) {
         for (long long b = threadIdx.x; b < nb_force; b += THREADS) {
             red[1] += partials[4 * b + 1];
             red[2] += partials[4 * b + 2];
             red[3] += partials[4 * b + 3];
         }
-    block_reduce4<THREADS>(red, sred);
+        block_reduce4<THREADS>(red, sred);
+    } else {
+        red[0] = block_max<THREADS, double>(red[0], sred);
+    }
     if (threadIdx.x != 0) return;
     const double dxs[3] = {dx0, dx1, dx2};
     if (mode & 2)
@@ -494,6 +515,7 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
     if constexpr (DIM >= 3) sweep<R, DIM, NMAT, SOLID, 2>(g, sW, sF, vr[2], own, lx, ly, lz, Dacc);
 
     double red[4] = {0.0, 0.0, 0.0, 0.0};
+    R smax_cell = R(0);
     if (inside) {
         const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
         const int bcell = ((lz + B::HZ) * B::BY + (ly + B::HY)) * B::BX + (lx + B::HX);
@@ -548,19 +570,22 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
             R sum = R(0);
 #pragma unroll
             for (int d = 0; d < DIM; d++) sum += (m_abs(s.u[d]) + cs) / gridc<R>(g).dx[d];
-            red[0] = (double)sum;
+            smax_cell = sum;
         }
     }
-    if (STAGE == 3 || (STAGE == 1 && a.want_force)) {
+    if (STAGE == 3) {
+        // block maximum in the compute precision (the per-cell values are R)
+        R *sr = reinterpret_cast<R *>(sred);
+        const R m = block_max<TL::THREADS, R>(smax_cell, sr);
+        if (threadIdx.x == 0) a.partials[4 * tile_id] = (double)m;
+    }
+    if (STAGE == 1 && a.want_force) {
         block_reduce4<TL::THREADS>(red, sred);
         if (threadIdx.x == 0) {
             double *pp = a.partials + 4 * tile_id;
-            if (STAGE == 3) pp[0] = red[0];
-            else {
-                pp[1] = red[1];
-                pp[2] = red[2];
-                pp[3] = red[3];
-            }
+            pp[1] = red[1];
+            pp[2] = red[2];
+            pp[3] = red[3];
         }
     }
     if (STAGE == 3 && a.final_mode) {
