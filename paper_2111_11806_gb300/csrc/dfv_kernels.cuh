@@ -421,6 +421,12 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
         R wL[L::NVAR], wR[L::NVAR];
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) {
+            if (v == L::IR && vr == R(0)) {
+                // the upwind r flux (Sec. 3.1) vanishes for a body at rest in
+                // this direction, whatever the face values of r
+                wL[v] = wR[v] = R(0);
+                continue;
+            }
             R s[6];
 #pragma unroll
             for (int k = 0; k < 6; k++) s[k] = sW[v * B::N + bc + (k - 3) * SD];
