@@ -46,6 +46,7 @@ def lib():
             L.o_nvar.argtypes = [ctypes.c_void_p]
             L.o_set_material.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 9
             L.o_set_options.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
+            L.o_set_variants.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
             for name in ("o_set_prim", "o_get_prim", "o_set_cons", "o_get_cons", "o_compute_D"):
                 getattr(L, name).argtypes = [ctypes.c_void_p, _dp]
             L.o_set_body.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_int]
@@ -105,9 +106,10 @@ class Oracle:
         self.ncell = int(np.prod(self.n))
 
     @classmethod
-    def from_workload(cls, wl, use_thinc=True, thinc_beta=1.6):
+    def from_workload(cls, wl, use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0):
         o = cls(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, wl.solid, wl.periodic)
         o.set_options(use_thinc, thinc_beta)
+        o.set_variants(hllc_lm, seed_variant)
         o.set_prim(wl.prim)
         o.set_body(wl.body_v, wl.body_x, wl.body_mass, wl.body_dynamic)
         return o
@@ -126,6 +128,10 @@ class Oracle:
 
     def set_options(self, use_thinc=True, thinc_beta=1.6):
         lib().o_set_options(self._h, int(bool(use_thinc)), float(thinc_beta))
+
+    def set_variants(self, hllc_lm=False, seed_variant=0):
+        """HLLC-LM flux (True/False) and seeding variant (0 original, 1 Riemann)."""
+        lib().o_set_variants(self._h, int(bool(hllc_lm)), int(seed_variant))
 
     def set_prim(self, prim):
         a = _arr(prim).reshape(self.nvar, self.ncell)

@@ -30,6 +30,7 @@
  * Parity status of each part: pinned by the tests under tests/ that run
  * without a GPU (closed forms, invariants, exact Riemann solutions).
  */
+#define _DEFAULT_SOURCE
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -62,6 +63,8 @@ typedef struct {
     double thinc_beta;
     int use_thinc;
     double phi_guard;
+    int hllc_lm;        /* 1: low-Mach HLLC-LM dissipation in the star region */
+    int seed_variant;   /* 0: original seeding, 1: Riemann-problem based (Sec. 3.2) */
 } ostate;
 
 /* ---------------------------------------------------------------- helpers */
@@ -556,7 +559,47 @@ void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *
             ut_star[a] = up->t.u[a];
         }
     }
-    if (region == 0 || region == 3) {
+    if ((region == 1 || region == 2) && s->hllc_lm) {
+        /* HLLC-LM [reading: the paper uses it for the cylinder test without
+         * giving it; the published low-Mach form]: the centred HLLC flux
+         *   F = (F_L + F_R)/2 + [phi S_L (U*_L - U_L) + |S*| (U*_L - U*_R) + phi S_R (U*_R - U_R)]/2
+         * with phi = sin(min(1, Ma/0.1) pi/2), Ma = max(|u_L|/c_L, |u_R|/c_R) taken
+         * with the velocity normal to the face;
+         * phi = 1 is the HLLC flux.  Tangential tractions as below. */
+        double Ma = fmax(fabs(uL) / L.c, fabs(uR) / R.c);
+        double phi = sin(fmin(1.0, Ma / 0.1) * M_PI / 2.0);
+        oface *side[2] = {&L, &R};
+        double Sside[2] = {SL, SR};
+        double Fa[2][OMAXV], Us[2][OMAXV];
+        double work_ts = 0.0;
+        for (int a = 0; a < 3; a++)
+            if (a != d) work_ts += ut_star[a] * sig_t[a];
+        for (int k = 0; k < 2; k++) {
+            oface *Kk = side[k];
+            double SKk = Sside[k], uKk = Kk->t.u[d];
+            double chi = (SKk - uKk) / (SKk - Ss);
+            for (int v = nthermo_lo; v <= nthermo_hi; v++) Fa[k][v] = Kk->F[v];
+            double work_t = 0.0;
+            for (int a = 0; a < 3; a++) {
+                if (a == d) continue;
+                double sK = 2.0 * Kk->t.G * Kk->t.devH[a][d];
+                if (a < s->dim) Fa[k][s->imom + a] += sK;
+                work_t += Kk->t.u[a] * sK;
+            }
+            Fa[k][s->iE] += work_t;
+            for (int l = 0; l < N; l++) Us[k][s->iar + l] = Kk->t.ar[l] * chi;
+            for (int a = 0; a < s->dim; a++) Us[k][s->imom + a] = Kk->t.rho * chi * (a == d ? Ss : Kk->t.u[a]);
+            double EK = Kk->t.rhoE / Kk->t.rho;
+            Us[k][s->iE] = Kk->t.rho * chi * (EK + (Ss - uKk) * (Ss + Kk->T / (Kk->t.rho * (SKk - uKk))));
+        }
+        for (int v = nthermo_lo; v <= nthermo_hi; v++)
+            F[v] = 0.5 * (Fa[0][v] + Fa[1][v]) +
+                   0.5 * (phi * SL * (Us[0][v] - L.U[v]) + fabs(Ss) * (Us[0][v] - Us[1][v]) +
+                          phi * SR * (Us[1][v] - R.U[v]));
+        for (int a = 0; a < s->dim; a++)
+            if (a != d) F[s->imom + a] -= sig_t[a];
+        F[s->iE] -= work_ts;
+    } else if (region == 0 || region == 3) {
         for (int v = nthermo_lo; v <= nthermo_hi; v++) F[v] = K->F[v];
     } else {
         /* HLLC on the advective part with the normal traction; the
@@ -750,6 +793,46 @@ static void grad_r(const ostate *s, const double *U, const int ijk[3], double g[
     }
 }
 
+/* Riemann-problem-based seeding (Sec. 3.2, step 5, second option): the cell
+ * takes the right star state of the HLLC problem along the normal n between
+ * the reflected state (left) and the interpolated state (right), here solved
+ * frame-free: normal velocity u.n, tangential velocity u - (u.n) n, normal
+ * traction T = p - 2G n.devH.n, Davis wave speeds and the contact speed S* as
+ * in o_hllc; the star state keeps the right state's volume fractions, stretch
+ * tensor and tangential velocity.  wnew: reflected primitives, wint:
+ * interpolated primitives; q: conserved output. */
+static void riemann_seed(const ostate *s, const double nrm[3], const double *wnew, const double *wint, double *q)
+{
+    othermo tl, tr;
+    thermo_from_prim(s, wnew, &tl);
+    thermo_from_prim(s, wint, &tr);
+    double unL = 0.0, unR = 0.0, TnL = 0.0, TnR = 0.0;
+    for (int a = 0; a < 3; a++) {
+        unL += tl.u[a] * nrm[a];
+        unR += tr.u[a] * nrm[a];
+        for (int b = 0; b < 3; b++) {
+            TnL += nrm[a] * tl.devH[a][b] * nrm[b];
+            TnR += nrm[a] * tr.devH[a][b] * nrm[b];
+        }
+    }
+    TnL = tl.p - 2.0 * tl.G * TnL;
+    TnR = tr.p - 2.0 * tr.G * TnR;
+    double cL = sqrt(tl.c2), cR = sqrt(tr.c2);
+    double SL = fmin(unL - cL, unR - cR), SR = fmax(unL + cL, unR + cR);
+    double Ss = (TnR - TnL + tl.rho * unL * (SL - unL) - tr.rho * unR * (SR - unR)) /
+                (tl.rho * (SL - unL) - tr.rho * (SR - unR));
+    double chi = (SR - unR) / (SR - Ss);
+    int N = s->nmat;
+    for (int l = 0; l < N - 1; l++) q[s->iphi + l] = tr.phi[l];
+    for (int l = 0; l < N; l++) q[s->iar + l] = tr.ar[l] * chi;
+    double rs = tr.rho * chi;
+    for (int a = 0; a < s->dim; a++) q[s->imom + a] = rs * (Ss * nrm[a] + (tr.u[a] - unR * nrm[a]));
+    double ER = tr.rhoE / tr.rho;
+    q[s->iE] = rs * (ER + (Ss - unR) * (Ss + TnR / (tr.rho * (SR - unR))));
+    for (int c = 0; c < s->nv; c++) q[s->iV + c] = wint[s->iV + c];
+    q[s->ir] = wint[s->ir];
+}
+
 /* The rigid seeding routine, original variant (Sec. 3.2, boxed routine),
  * applied once at the start of the step:
  *  1. in every cell with r > 0.5, the outward normal n = -grad r/|grad r|
@@ -830,6 +913,9 @@ void o_seed(ostate *s)
                     found = 1;
                 }
                 if (!found) continue;
+                double wref[OMAXV];     /* the interpolated state, before reflection */
+                for (int v = 0; v < nv; v++) wref[v] = wint[v];
+                wref[s->ir] = s->U[s->ir * nc + c];
                 /* reflect */
                 double P[3][3];
                 for (int a = 0; a < 3; a++)
@@ -861,7 +947,8 @@ void o_seed(ostate *s)
                 }
                 wint[s->ir] = s->U[s->ir * nc + c];
                 double q[OMAXV];
-                prim_to_cons(s, wint, q);
+                if (s->seed_variant == 1) riemann_seed(s, nrm, wint, wref, q);
+                else prim_to_cons(s, wint, q);
                 for (int v = 0; v < nv; v++) s->U[v * nc + c] = q[v];
             }
 }
@@ -1094,6 +1181,13 @@ void o_set_options(void *h, int use_thinc, double thinc_beta)
     ostate *s = (ostate *)h;
     s->use_thinc = use_thinc;
     s->thinc_beta = thinc_beta;
+}
+
+void o_set_variants(void *h, int hllc_lm, int seed_variant)
+{
+    ostate *s = (ostate *)h;
+    s->hllc_lm = hllc_lm;
+    s->seed_variant = seed_variant;
 }
 
 void o_set_prim(void *h, const double *prim)
