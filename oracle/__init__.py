@@ -46,7 +46,14 @@ def lib():
             L.o_nvar.argtypes = [ctypes.c_void_p]
             L.o_set_material.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 9
             L.o_set_options.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
-            L.o_set_variants.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+            L.o_set_variants.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.o_set_walls.argtypes = [ctypes.c_void_p, _ip]
+            L.o_seed_normals.argtypes = [ctypes.c_void_p, _dp]
+            L.o_cut_fraction.argtypes = [ctypes.c_double] * 7
+            L.o_cut_fraction.restype = ctypes.c_double
+            L.o_cut_alpha.argtypes = [ctypes.c_double] * 7
+            L.o_cut_alpha.restype = ctypes.c_double
+            L.o_elvira.argtypes = [_dp, ctypes.c_double, ctypes.c_double, _dp]
             for name in ("o_set_prim", "o_get_prim", "o_set_cons", "o_get_cons", "o_compute_D"):
                 getattr(L, name).argtypes = [ctypes.c_void_p, _dp]
             L.o_set_body.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_int]
@@ -106,10 +113,12 @@ class Oracle:
         self.ncell = int(np.prod(self.n))
 
     @classmethod
-    def from_workload(cls, wl, use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0):
+    def from_workload(cls, wl, use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0, normal_method=0,
+                      probe_mode=0):
         o = cls(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, wl.solid, wl.periodic)
         o.set_options(use_thinc, thinc_beta)
-        o.set_variants(hllc_lm, seed_variant)
+        o.set_variants(hllc_lm, seed_variant, normal_method, probe_mode)
+        o.set_walls(getattr(wl, "walls", (0,) * 6))
         o.set_prim(wl.prim)
         o.set_body(wl.body_v, wl.body_x, wl.body_mass, wl.body_dynamic)
         return o
@@ -129,9 +138,21 @@ class Oracle:
     def set_options(self, use_thinc=True, thinc_beta=1.6):
         lib().o_set_options(self._h, int(bool(use_thinc)), float(thinc_beta))
 
-    def set_variants(self, hllc_lm=False, seed_variant=0):
-        """HLLC-LM flux (True/False) and seeding variant (0 original, 1 Riemann)."""
-        lib().o_set_variants(self._h, int(bool(hllc_lm)), int(seed_variant))
+    def set_variants(self, hllc_lm=False, seed_variant=0, normal_method=0, probe_mode=0):
+        """HLLC-LM flux (True/False), seeding variant (0 original, 1 Riemann),
+        normal method (0 Youngs, 1 ELVIRA in 2-D), probe (0 stepped, 1 fixed 1.5 dx)."""
+        lib().o_set_variants(self._h, int(bool(hllc_lm)), int(seed_variant), int(normal_method), int(probe_mode))
+
+    def set_walls(self, walls):
+        """Reflective walls: walls[2d], walls[2d+1] for the low / high side of direction d."""
+        a = np.zeros(6, dtype=np.int32)
+        a[: len(walls)] = [int(bool(x)) for x in walls]
+        lib().o_set_walls(self._h, a.ctypes.data_as(_ip))
+
+    def seed_normals(self):
+        a = np.zeros((3, self.ncell))
+        lib().o_seed_normals(self._h, _p(a))
+        return a
 
     def set_prim(self, prim):
         a = _arr(prim).reshape(self.nvar, self.ncell)
@@ -230,6 +251,23 @@ def thinc(qm, q0, qp, beta=1.6):
     fm, fp = ctypes.c_double(), ctypes.c_double()
     ok = lib().o_thinc(qm, q0, qp, beta, ctypes.byref(fm), ctypes.byref(fp))
     return (fm.value, fp.value) if ok else None
+
+
+def cut_fraction(n, alpha, x0, y0, hx, hy):
+    """Fraction of the rectangle [x0,x0+hx]x[y0,y0+hy] on the side n.x <= alpha."""
+    return lib().o_cut_fraction(float(n[0]), float(n[1]), float(alpha), float(x0), float(y0), float(hx), float(hy))
+
+
+def cut_alpha(n, f, x0, y0, hx, hy):
+    return lib().o_cut_alpha(float(n[0]), float(n[1]), float(f), float(x0), float(y0), float(hx), float(hy))
+
+
+def elvira(block, hx=1.0, hy=1.0):
+    """ELVIRA outward normal of the centre of a 3x3 block of r, block[l][k] = r(i+k-1, j+l-1)."""
+    b = _arr(block).ravel().copy()
+    out = np.zeros(2)
+    lib().o_elvira(_p(b), float(hx), float(hy), _p(out))
+    return out
 
 
 def sym_eig3(B):

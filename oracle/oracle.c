@@ -65,6 +65,10 @@ typedef struct {
     double phi_guard;
     int hllc_lm;        /* 1: low-Mach HLLC-LM dissipation in the star region */
     int seed_variant;   /* 0: original seeding, 1: Riemann-problem based (Sec. 3.2) */
+    int normal_method;  /* 0: Youngs, 1: ELVIRA (2-D) (Sec. 3.3) */
+    int probe_mode;     /* 0: stepped probe 1.0..4.0 dx, 1: fixed 1.5 dx (Sec. 3.2) */
+    int reflect[3][2];  /* reflective wall on the low / high side of direction d */
+    double *seed_n;     /* normal used by the last seeding per cell (3 planes) */
 } ostate;
 
 /* ---------------------------------------------------------------- helpers */
@@ -89,6 +93,16 @@ static int map_index(const ostate *s, int d, int i)
 }
 
 static double phi_clip(double f);
+
+/* Reflective wall: the halo cell i < 0 mirrors cell -1-i, the halo cell
+ * i > n-1 mirrors cell 2n-1-i (clamped to the grid when n < 3). */
+static int mirror_index(int n, int i)
+{
+    int m = i < 0 ? -1 - i : 2 * n - 1 - i;
+    if (m < 0) m = 0;
+    if (m > n - 1) m = n - 1;
+    return m;
+}
 
 static void mat_zero(double M[3][3])
 {
@@ -517,6 +531,15 @@ static void face_state(const ostate *s, int d, const double *w, oface *f)
  *   us[3]   face velocity u* of the state at x/t = 0 (normal: u_L, S* or u_R;
  *           tangential: upwind by S*, tie to the left),
  *   vrow[3] V*_{d b}, the row d of the upwind (by S*) face V. */
+/* The value at x/t = 0 of a quantity carried by the contact: the left value
+ * when S* > 0, the right one when S* < 0, and [reading] their mean when
+ * S* = 0, so that the face of two mirror-image states (a wall) gets the
+ * mirror-symmetric value. */
+static double upwind(double Ss, double xl, double xr)
+{
+    return Ss > 0.0 ? xl : (Ss < 0.0 ? xr : 0.5 * (xl + xr));
+}
+
 void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *F, double us[3], double vrow[3])
 {
     oface L, R;
@@ -539,7 +562,6 @@ void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *
     K = (region <= 1) ? &L : &R;
     SK = (region <= 1) ? SL : SR;
     int nthermo_lo = s->iar, nthermo_hi = s->iE; /* ar .. rhoE inclusive */
-    oface *up = (Ss >= 0.0) ? &L : &R;
     /* tangential traction and velocity at the face: the linear shear-wave
      * Riemann problem, sigma -/+ Z u constant along the right/left shear
      * characteristics, Z = sqrt(rho G) [reading: the paper's HLLD resolves
@@ -556,7 +578,7 @@ void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *
             ut_star[a] = (ZL * L.t.u[a] + ZR * R.t.u[a] + sR - sL) / (ZL + ZR);
         } else {
             sig_t[a] = 0.0;
-            ut_star[a] = up->t.u[a];
+            ut_star[a] = upwind(Ss, L.t.u[a], R.t.u[a]);
         }
     }
     if ((region == 1 || region == 2) && s->hllc_lm) {
@@ -632,16 +654,29 @@ void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *
     else if (region == 3) us[d] = uR;
     else us[d] = Ss;
     /* volume fractions: phi* upwind by S*, conservative part phi* u*_d */
-    for (int l = 0; l < N - 1; l++) F[s->iphi + l] = up->t.phi[l] * us[d];
+    for (int l = 0; l < N - 1; l++) F[s->iphi + l] = upwind(Ss, L.t.phi[l], R.t.phi[l]) * us[d];
     /* stretch tensor: F(V_ab) = V*_ab u*_d - V*_db u*_a */
-    for (int b = 0; b < 3; b++) vrow[b] = up->t.A[d][b];
+    for (int b = 0; b < 3; b++) vrow[b] = upwind(Ss, L.t.A[d][b], R.t.A[d][b]);
     for (int c = 0; c < s->nv; c++) {
         int a = s->vmap[c][0], b = s->vmap[c][1];
-        F[s->iV + c] = up->t.A[a][b] * us[d] - up->t.A[d][b] * us[a];
+        F[s->iV + c] = upwind(Ss, L.t.A[a][b], R.t.A[a][b]) * us[d] - vrow[b] * us[a];
     }
 }
 
 /* ------------------------------------------------------ spatial operator */
+
+/* The mirror image of a primitive state in a wall normal to direction d:
+ * velocity and stretch tensor transformed by the reflection P = I - 2 e_d e_d^T
+ * (u_d changes sign; V_ab changes sign when exactly one of a, b is d); the
+ * scalars are even. */
+static void reflect_prim(const ostate *s, int d, double *w)
+{
+    w[s->imom + d] = -w[s->imom + d];
+    for (int c = 0; c < s->nv; c++) {
+        int a = s->vmap[c][0], b = s->vmap[c][1];
+        if ((a == d) != (b == d)) w[s->iV + c] = -w[s->iV + c];
+    }
+}
 
 /* D(U) of eq:spat_op (Sec. 3.1): for every direction d, the pencil of
  * primitives is reconstructed (MUSCL on all primitives; BVD-THINC on every
@@ -685,11 +720,13 @@ static void compute_D(ostate *s, const double *U, double *D)
                 /* gather the pencil with its halo of 3 */
                 for (int i = -3; i < n + 3; i++) {
                     int idx[3];
-                    idx[d] = map_index(s, d, i);
+                    int wall = (i < 0 && s->reflect[d][0]) || (i > n - 1 && s->reflect[d][1]);
+                    idx[d] = wall ? mirror_index(n, i) : map_index(s, d, i);
                     idx[e1] = j1;
                     idx[e2] = j2;
                     long c = cell_index(s, idx[0], idx[1], idx[2]);
                     for (int v = 0; v < nv; v++) P[(i + 3) * nv + v] = s->W[v * nc + c];
+                    if (wall) reflect_prim(s, d, &P[(i + 3) * nv]);
                 }
                 /* MUSCL and THINC face values of cells -2..n+1 */
                 for (int i = -2; i < n + 2; i++) {
@@ -833,42 +870,163 @@ static void riemann_seed(const ostate *s, const double nrm[3], const double *wne
     q[s->ir] = wint[s->ir];
 }
 
-/* The rigid seeding routine, original variant (Sec. 3.2, boxed routine),
- * applied once at the start of the step:
- *  1. in every cell with r > 0.5, the outward normal n = -grad r/|grad r|
- *     (Youngs); cells with |grad r| dx_min <= 1e-10 are left alone [reading];
- *  2. stepped probe: points at s = 1.0, 1.5, ..., 4.0 dx_min along n
- *     [reading: step dx/2]; the first point whose 2^dim enclosing cell centres
- *     all lie in the domain (or wrap, for periodic directions) and have r < 0.5
- *     is taken; the primitives are interpolated multilinearly there; no valid
- *     point -> the cell is unchanged;
+/* ------------------------------------------------ ELVIRA normal (2-D) */
+
+/* Fraction of the rectangle [x0, x0+hx] x [y0, y0+hy] lying on the side
+ * nx x + ny y <= alpha of a line: the rectangle's polygon clipped by the
+ * half-plane (one Sutherland-Hodgman pass), its area by the shoelace formula,
+ * divided by hx hy. */
+double o_cut_fraction(double nx, double ny, double alpha, double x0, double y0, double hx, double hy)
+{
+    double px[4] = {x0, x0 + hx, x0 + hx, x0}, py[4] = {y0, y0, y0 + hy, y0 + hy};
+    double qx[8], qy[8];
+    int nq = 0;
+    for (int k = 0; k < 4; k++) {
+        int kn = (k + 1) % 4;
+        double dk = nx * px[k] + ny * py[k] - alpha;
+        double dn = nx * px[kn] + ny * py[kn] - alpha;
+        if (dk <= 0.0) {
+            qx[nq] = px[k];
+            qy[nq] = py[k];
+            nq++;
+        }
+        if ((dk < 0.0 && dn > 0.0) || (dk > 0.0 && dn < 0.0)) {
+            double t = dk / (dk - dn);
+            qx[nq] = px[k] + t * (px[kn] - px[k]);
+            qy[nq] = py[k] + t * (py[kn] - py[k]);
+            nq++;
+        }
+    }
+    double a2 = 0.0;
+    for (int k = 0; k < nq; k++) {
+        int kn = (k + 1) % nq;
+        a2 += qx[k] * qy[kn] - qx[kn] * qy[k];
+    }
+    return fabs(0.5 * a2) / (hx * hy);
+}
+
+/* The line position alpha at which the rectangle holds the fraction f on the
+ * side n.x <= alpha: bisection between the least and the largest n.x over
+ * its corners, between which the fraction rises monotonically from 0 to 1. */
+double o_cut_alpha(double nx, double ny, double f, double x0, double y0, double hx, double hy)
+{
+    double cx[4] = {x0, x0 + hx, x0 + hx, x0}, cy[4] = {y0, y0, y0 + hy, y0 + hy};
+    double lo = nx * cx[0] + ny * cy[0], hi = lo;
+    for (int k = 1; k < 4; k++) {
+        double a = nx * cx[k] + ny * cy[k];
+        lo = fmin(lo, a);
+        hi = fmax(hi, a);
+    }
+    if (f <= 0.0) return lo;
+    if (f >= 1.0) return hi;
+    for (int it = 0; it < 400; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (o_cut_fraction(nx, ny, mid, x0, y0, hx, hy) < f) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* ELVIRA normal (Sec. 3.3; Pilliod & Puckett's method) of a cell from the
+ * 3x3 block b[3 (l+1) + (k+1)] = r of cell (i+k, j+l), cell sizes hx, hy.
+ * Candidate lines come from the two height functions of the block: the column
+ * sums of r (interface height y as a function of x) and the row sums (x as a
+ * function of y), each differenced backward, centrally and forward.  A column
+ * slope m gives the normal (-m, s_y), a row slope m the normal (s_x, -m), with
+ * s_y = -1 when the top row holds more r than the bottom row (else +1), s_x
+ * likewise from the right and left columns, so that every candidate points
+ * away from r = 1.  Each candidate line is placed to hold the centre cell's r;
+ * the candidate whose line reproduces the nine values of r best (least sum of
+ * squared differences) is returned as an outward unit normal.  [reading] An
+ * earlier candidate wins ties within 1e-12, in the order central column,
+ * central row, backward column, forward column, backward row, forward row. */
+void o_elvira(const double b[9], double hx, double hy, double nrm[2])
+{
+    double h[3], g[3];
+    for (int k = 0; k < 3; k++) h[k] = (b[k] + b[3 + k] + b[6 + k]) * hy;
+    for (int l = 0; l < 3; l++) g[l] = (b[3 * l] + b[3 * l + 1] + b[3 * l + 2]) * hx;
+    double sy = (g[2] > g[0]) ? -1.0 : 1.0;
+    double sx = (h[2] > h[0]) ? -1.0 : 1.0;
+    double mcol[3] = {(h[2] - h[0]) / (2.0 * hx), (h[1] - h[0]) / hx, (h[2] - h[1]) / hx};
+    double mrow[3] = {(g[2] - g[0]) / (2.0 * hy), (g[1] - g[0]) / hy, (g[2] - g[1]) / hy};
+    double cand[6][2] = {{-mcol[0], sy}, {sx, -mrow[0]}, {-mcol[1], sy},
+                         {-mcol[2], sy}, {sx, -mrow[1]}, {sx, -mrow[2]}};
+    double best = 0.0;
+    for (int c = 0; c < 6; c++) {
+        double len = sqrt(cand[c][0] * cand[c][0] + cand[c][1] * cand[c][1]);
+        double nx = cand[c][0] / len, ny = cand[c][1] / len;
+        double alpha = o_cut_alpha(nx, ny, b[4], -0.5 * hx, -0.5 * hy, hx, hy);
+        double err = 0.0;
+        for (int l = 0; l < 3; l++)
+            for (int k = 0; k < 3; k++) {
+                double f = o_cut_fraction(nx, ny, alpha, (k - 1.5) * hx, (l - 1.5) * hy, hx, hy);
+                err += (f - b[3 * l + k]) * (f - b[3 * l + k]);
+            }
+        if (c == 0 || err < best - 1e-12) {
+            best = err;
+            nrm[0] = nx;
+            nrm[1] = ny;
+        }
+    }
+}
+
+/* The rigid seeding routine (Sec. 3.2, boxed routine), applied once at the
+ * start of the step to the state U0 it starts from:
+ *  1. in every cell with r > 0.5, the outward normal: Youngs, n = -grad r/|grad r|
+ *     with central differences, or (2-D option) the ELVIRA normal of the 3x3
+ *     block of r; cells with |grad r| dx_min <= 1e-10 are left alone [reading];
+ *  2. the probe point, stepped or fixed:
+ *     stepped: s = 1.0, 1.5, ..., 4.0 dx_min along n [reading: step dx/2]; the
+ *     first point whose 2^dim enclosing cell centres all lie in the domain (or
+ *     wrap, for periodic directions) and have r < 0.5 is taken; no valid point
+ *     -> the cell is unchanged;
+ *     fixed: s = 1.5 dx_min, enclosing cells clamped into the domain (wrapped
+ *     if periodic), whatever their r [reading];
+ *     the primitives of U0 are interpolated multilinearly at the point;
  *  3-5. reflection in the frame of n, written frame-free with the Householder
  *     matrix P = I - 2 n n^T (R P R^T = diag(-1,1,1) in the rotated frame):
  *     u_new = P u_int + 2 (v_r . n) n,  V_new = P V_int P; scalars are copied;
- *     the new state replaces the cell (r is kept).
- * Reads touch only r < 0.5 cells and writes only r > 0.5 cells, so the result
- * does not depend on the loop order. */
+ *     the original variant puts the new state in the cell (r is kept), the
+ *     Riemann-problem variant the right HLLC star state of (new, interpolated).
+ * Every seeded state is computed from U0 alone [reading: all cells seeded at
+ * once], so the result does not depend on the loop order. */
 void o_seed(ostate *s)
 {
     long nc = s->ncell;
     int nv = s->nvar;
     double dxmin = s->dx[0];
     for (int d = 1; d < s->dim; d++) dxmin = fmin(dxmin, s->dx[d]);
+    double *U0 = (double *)malloc(sizeof(double) * nv * nc);
+    memcpy(U0, s->U, sizeof(double) * nv * nc);
+    memset(s->seed_n, 0, sizeof(double) * 3 * nc);
     for (int k = 0; k < s->n[2]; k++)
         for (int j = 0; j < s->n[1]; j++)
             for (int i = 0; i < s->n[0]; i++) {
                 long c = cell_index(s, i, j, k);
-                if (!(s->U[s->ir * nc + c] > 0.5)) continue;
+                if (!(U0[s->ir * nc + c] > 0.5)) continue;
                 int ijk[3] = {i, j, k};
                 double g[3];
-                grad_r(s, s->U, ijk, g);
+                grad_r(s, U0, ijk, g);
                 double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
                 if (!(gn * dxmin > 1e-10)) continue;
                 double nrm[3] = {-g[0] / gn, -g[1] / gn, -g[2] / gn};
+                if (s->normal_method == 1 && s->dim == 2) {
+                    double blk[9], n2[2];
+                    for (int l = -1; l <= 1; l++)
+                        for (int m = -1; m <= 1; m++)
+                            blk[3 * (l + 1) + (m + 1)] =
+                                U0[s->ir * nc + cell_index(s, map_index(s, 0, i + m), map_index(s, 1, j + l), 0)];
+                    o_elvira(blk, s->dx[0], s->dx[1], n2);
+                    nrm[0] = n2[0];
+                    nrm[1] = n2[1];
+                    nrm[2] = 0.0;
+                }
                 int found = 0;
                 double wint[OMAXV];
-                for (int step = 0; step < 7 && !found; step++) {
-                    double sdist = (1.0 + 0.5 * step) * dxmin;
+                int nsteps = s->probe_mode == 1 ? 1 : 7;
+                for (int step = 0; step < nsteps && !found; step++) {
+                    double sdist = (s->probe_mode == 1 ? 1.5 : 1.0 + 0.5 * step) * dxmin;
                     int base[3];
                     double frac[3];
                     for (int d = 0; d < 3; d++) {
@@ -891,14 +1049,14 @@ void o_seed(ostate *s)
                         for (int d = 0; d < s->dim; d++) {
                             int bit = (m >> d) & 1;
                             int ii = base[d] + bit;
-                            if (s->periodic[d]) ii = map_index(s, d, ii);
+                            if (s->periodic[d] || s->probe_mode == 1) ii = map_index(s, d, ii);
                             else if (ii < 0 || ii > s->n[d] - 1) { ok = 0; break; }
                             ci[d] = ii;
                             wt *= bit ? frac[d] : (1.0 - frac[d]);
                         }
                         if (!ok) break;
                         long cc = cell_index(s, ci[0], ci[1], ci[2]);
-                        if (!(s->U[s->ir * nc + cc] < 0.5)) ok = 0;
+                        if (s->probe_mode == 0 && !(U0[s->ir * nc + cc] < 0.5)) ok = 0;
                         cidx[m] = cc;
                         wts[m] = wt;
                     }
@@ -906,16 +1064,17 @@ void o_seed(ostate *s)
                     for (int v = 0; v < nv; v++) wint[v] = 0.0;
                     for (int m = 0; m < ncorner; m++) {
                         double q[OMAXV], w[OMAXV];
-                        for (int v = 0; v < nv; v++) q[v] = s->U[v * nc + cidx[m]];
+                        for (int v = 0; v < nv; v++) q[v] = U0[v * nc + cidx[m]];
                         cons_to_prim(s, q, w);
                         for (int v = 0; v < nv; v++) wint[v] += wts[m] * w[v];
                     }
                     found = 1;
                 }
                 if (!found) continue;
+                for (int d = 0; d < 3; d++) s->seed_n[d * nc + c] = nrm[d];
                 double wref[OMAXV];     /* the interpolated state, before reflection */
                 for (int v = 0; v < nv; v++) wref[v] = wint[v];
-                wref[s->ir] = s->U[s->ir * nc + c];
+                wref[s->ir] = U0[s->ir * nc + c];
                 /* reflect */
                 double P[3][3];
                 for (int a = 0; a < 3; a++)
@@ -945,12 +1104,13 @@ void o_seed(ostate *s)
                         }
                     vbar_pack(s, C, wint);
                 }
-                wint[s->ir] = s->U[s->ir * nc + c];
+                wint[s->ir] = U0[s->ir * nc + c];
                 double q[OMAXV];
                 if (s->seed_variant == 1) riemann_seed(s, nrm, wint, wref, q);
                 else prim_to_cons(s, wint, q);
                 for (int v = 0; v < nv; v++) s->U[v * nc + c] = q[v];
             }
+    free(U0);
 }
 
 /* Pressure force on the body [not in the paper, which imposes v_r (Sec. 2.3);
@@ -1149,6 +1309,7 @@ void *o_create(int dim, const int n[3], const double lo[3], const double hi[3], 
     s->U1 = (double *)calloc(1, sz);
     s->U3 = (double *)calloc(1, sz);
     s->D = (double *)calloc(1, sz);
+    s->seed_n = (double *)calloc(3 * (size_t)s->ncell, sizeof(double));
     s->W = (double *)calloc(1, sz);
     s->mask = (unsigned char *)calloc(s->ncell, 1);
     s->thinc_beta = 1.6;
@@ -1161,7 +1322,7 @@ void o_destroy(void *h)
 {
     ostate *s = (ostate *)h;
     if (!s) return;
-    free(s->U); free(s->Un); free(s->U1); free(s->U3); free(s->D); free(s->W); free(s->mask);
+    free(s->U); free(s->Un); free(s->U1); free(s->U3); free(s->D); free(s->W); free(s->mask); free(s->seed_n);
     free(s);
 }
 
@@ -1183,11 +1344,30 @@ void o_set_options(void *h, int use_thinc, double thinc_beta)
     s->thinc_beta = thinc_beta;
 }
 
-void o_set_variants(void *h, int hllc_lm, int seed_variant)
+void o_set_variants(void *h, int hllc_lm, int seed_variant, int normal_method, int probe_mode)
 {
     ostate *s = (ostate *)h;
     s->hllc_lm = hllc_lm;
     s->seed_variant = seed_variant;
+    s->normal_method = normal_method;
+    s->probe_mode = probe_mode;
+}
+
+/* Reflective walls: refl[2 d] / refl[2 d + 1] for the low / high side of a
+ * non-periodic direction d. */
+void o_set_walls(void *h, const int refl[6])
+{
+    ostate *s = (ostate *)h;
+    for (int d = 0; d < 3; d++)
+        for (int e = 0; e < 2; e++) s->reflect[d][e] = (d < s->dim && !s->periodic[d]) ? (refl[2 * d + e] != 0) : 0;
+}
+
+/* The normal each cell used in the last seeding (3 planes; 0 where the cell
+ * was not seeded). */
+void o_seed_normals(void *h, double *out)
+{
+    ostate *s = (ostate *)h;
+    memcpy(out, s->seed_n, sizeof(double) * 3 * (size_t)s->ncell);
 }
 
 void o_set_prim(void *h, const double *prim)

@@ -57,6 +57,7 @@ class Workload:
     cfl: float = 0.8
     steps: int = 1
     t_end: Optional[float] = None
+    walls: tuple = (0, 0, 0, 0, 0, 0)   # reflective wall on the low / high side of each direction
 
     @property
     def nmat(self) -> int:
