@@ -33,8 +33,8 @@
  *    xx,xy,yx,yy,zz).  With N = 1 there is no phi plane and the single
  *    density plane is rho.
  *  - Boundaries: bc[2*d] / bc[2*d+1] for the low / high side of direction d:
- *    DFV_BC_TRANSMISSIVE (zero-gradient halo) or DFV_BC_PERIODIC (both sides
- *    of a direction must then be periodic).
+ *    DFV_BC_TRANSMISSIVE (zero-gradient halo), DFV_BC_REFLECTIVE (slip wall)
+ *    or DFV_BC_PERIODIC (both sides of a direction must then be periodic).
  */
 #ifndef DFVRB_H
 #define DFVRB_H
@@ -63,6 +63,9 @@ typedef int dfv_status;
 
 #define DFV_BC_TRANSMISSIVE 0
 #define DFV_BC_PERIODIC 1
+#define DFV_BC_REFLECTIVE 2   /* slip wall: the halo mirrors the interior with the
+                                 normal velocity and the stretch components with
+                                 exactly one normal index negated */
 
 #define DFV_MAT_IDEAL 0       /* p = (gamma-1) rho e                  (Sec. 2.1.3) */
 #define DFV_MAT_STIFFENED 1   /* p = (gamma-1) rho e - gamma p_inf (Mie-Grueneisen form) */
@@ -90,6 +93,22 @@ typedef struct {
     int solid;           /* 1: carry the stretch tensor V (elastoplastic) */
     int use_thinc;       /* 1: MUSCL-BVD-THINC on phi and r (Sec. 3.1); 0: MUSCL only */
     double thinc_beta;   /* THINC steepness (1.6) */
+    int hllc_lm;         /* 1: HLLC-LM flux (the low-Mach HLLC variant the paper
+                            names for its cylinder test): the acoustic dissipation
+                            of the star regions scaled by sin(min(1, Ma/0.1) pi/2),
+                            Ma the larger face-normal Mach number; 0: HLLC */
+    int seed_variant;    /* rigid seeding (Sec. 3.2, step 5): 0 the reflected
+                            state; 1 the right star state of the HLLC problem
+                            along the body normal between the reflected (left)
+                            and the interpolated (right) state, whose normal
+                            velocity is the body's */
+    int normal_method;   /* body normal (Sec. 3.3): 0 Youngs, -grad r/|grad r|;
+                            1 ELVIRA from the 3x3 block of r (2-D grids only,
+                            else DFV_ERR_UNSUPPORTED) */
+    int probe_mode;      /* probe (Sec. 3.2, step 2): 0 stepped, 1.0 .. 4.0 dx_min
+                            until the 2^dim enclosing cells have r < 0.5; 1 fixed
+                            1.5 dx_min whatever their r (seeded from the
+                            step-start state: one extra launch per step) */
 } dfv_options;
 
 typedef struct dfv_grid dfv_grid;

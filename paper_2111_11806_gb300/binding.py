@@ -18,7 +18,7 @@ DFV_ERR = {-1: "DFV_ERR_ARG", -2: "DFV_ERR_CUDA", -3: "DFV_ERR_NONPHYSICAL", -4:
            -5: "DFV_ERR_WORKSPACE", -6: "DFV_ERR_UNSUPPORTED", -7: "DFV_ERR_TOO_LARGE"}
 DFV_NOALLOC_MAX_CELLS = 16 * 1024 * 1024
 DFV_FP64, DFV_FP32 = 0, 1
-DFV_BC_TRANSMISSIVE, DFV_BC_PERIODIC = 0, 1
+DFV_BC_TRANSMISSIVE, DFV_BC_PERIODIC, DFV_BC_REFLECTIVE = 0, 1, 2
 DFV_FIELDS_CONSERVED, DFV_FIELDS_PRIMITIVE = 0, 1
 MAT_KIND = {"ideal": 0, "stiffened": 1, "romenskii": 2}
 
@@ -38,7 +38,8 @@ class dfv_material_params(ctypes.Structure):
 
 class dfv_options(ctypes.Structure):
     _fields_ = [("nmat", ctypes.c_int), ("solid", ctypes.c_int), ("use_thinc", ctypes.c_int),
-                ("thinc_beta", ctypes.c_double)]
+                ("thinc_beta", ctypes.c_double), ("hllc_lm", ctypes.c_int), ("seed_variant", ctypes.c_int),
+                ("normal_method", ctypes.c_int), ("probe_mode", ctypes.c_int)]
 
 
 class dfv_instance_desc(ctypes.Structure):
@@ -147,7 +148,8 @@ def workspace_bytes(dim, n, nmat, solid, precision) -> int:
 
 
 def compute_dt_noalloc(dim, n, lo, hi, materials, cons_ptr, plane_pitch, cfl, precision=DFV_FP64, solid=False,
-                       v_body=(0.0, 0.0, 0.0), stream=0, use_thinc=True, thinc_beta=1.6):
+                       v_body=(0.0, 0.0, 0.0), stream=0, use_thinc=True, thinc_beta=1.6, hllc_lm=False,
+                       seed_variant=0, normal_method=0, probe_mode=0):
     """dfv_compute_dt_noalloc: the CFL dt of a conserved state the caller
     holds on the device (cons_ptr: device address of the planes, plane_pitch
     elements apart), computed with the library's fixed scratch array instead
@@ -156,7 +158,8 @@ def compute_dt_noalloc(dim, n, lo, hi, materials, cons_ptr, plane_pitch, cfl, pr
     L = load()
     n3 = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - dim)))
     lo3, hi3 = _d3(lo), _d3(hi)
-    opt = dfv_options(len(materials), int(bool(solid)), int(bool(use_thinc)), float(thinc_beta))
+    opt = dfv_options(len(materials), int(bool(solid)), int(bool(use_thinc)), float(thinc_beta), int(bool(hllc_lm)),
+                      int(seed_variant), int(normal_method), int(probe_mode))
     kinds = (ctypes.c_int * len(materials))(*[MAT_KIND[m["kind"]] for m in materials])
     params = (dfv_material_params * len(materials))(*[material_struct(m) for m in materials])
     vb = _d3(v_body)
@@ -168,13 +171,29 @@ def compute_dt_noalloc(dim, n, lo, hi, materials, cons_ptr, plane_pitch, cfl, pr
     return dt.value
 
 
+def bc_codes(dim, periodic=None, walls=None):
+    """bc[6] of dfv_create_grid: periodic directions, else a reflective wall
+    where walls[2d + side] is set, else transmissive."""
+    per = list(periodic or [0] * dim)
+    wal = list(walls or [0] * 6)
+    out = [DFV_BC_TRANSMISSIVE] * 6
+    for d in range(dim):
+        for side in range(2):
+            if per[d]:
+                out[2 * d + side] = DFV_BC_PERIODIC
+            elif wal[2 * d + side]:
+                out[2 * d + side] = DFV_BC_REFLECTIVE
+    return out
+
+
 class Grid:
     """One grid of the CUDA library.  Device memory: one torch uint8 tensor
     (the workspace), owned by this object.  Stream: torch's current stream on
     `device` unless one is given."""
 
     def __init__(self, dim, n, lo, hi, materials, solid=False, precision=DFV_FP64, periodic=None,
-                 use_thinc=True, thinc_beta=1.6, device="cuda:0", stream=None):
+                 use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0, normal_method=0, probe_mode=0,
+                 walls=None, device="cuda:0", stream=None):
         import torch
         if not torch.cuda.is_available():
             raise DfvError("a CUDA device is required (no CPU fallback)")
@@ -193,13 +212,12 @@ class Grid:
             self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         base = self.workspace.data_ptr()
         aligned = (base + 255) & ~255
-        per = list(periodic or [0] * dim)
-        bc = (ctypes.c_int * 6)(*sum(([DFV_BC_PERIODIC] * 2 if p else [DFV_BC_TRANSMISSIVE] * 2 for p in per), []),
-                                *([0] * (6 - 2 * dim)))
+        bc = (ctypes.c_int * 6)(*bc_codes(dim, periodic, walls))
         n3 = (ctypes.c_int * 3)(*(list(self.n) + [1] * (3 - dim)))
         lo3 = _d3(lo)
         hi3 = _d3(hi)
-        opt = dfv_options(self.nmat, int(self.solid), int(bool(use_thinc)), float(thinc_beta))
+        opt = dfv_options(self.nmat, int(self.solid), int(bool(use_thinc)), float(thinc_beta), int(bool(hllc_lm)),
+                          int(seed_variant), int(normal_method), int(probe_mode))
         h = _vp()
         with torch.cuda.device(self.device):
             st = L.dfv_create_grid(dim, n3, lo3.ctypes.data_as(_dp), hi3.ctypes.data_as(_dp), bc, precision,
@@ -217,7 +235,7 @@ class Grid:
     @classmethod
     def from_workload(cls, wl, precision=DFV_FP64, **kw):
         g = cls(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, solid=wl.solid, precision=precision,
-                periodic=wl.periodic, **kw)
+                periodic=wl.periodic, walls=getattr(wl, "walls", None), **kw)
         g.set_fields(wl.prim)
         g.set_body(wl.body_v, wl.body_x, wl.body_mass, wl.body_dynamic)
         return g
@@ -327,8 +345,8 @@ class Batch:
     `workloads` (same materials, fluid, 2-D) becomes one instance with its own
     grid, body velocity and time step.  Device memory: one torch workspace."""
 
-    def __init__(self, workloads, precision=DFV_FP32, use_thinc=True, thinc_beta=1.6, device="cuda:0",
-                 stream=None):
+    def __init__(self, workloads, precision=DFV_FP32, use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0,
+                 normal_method=0, probe_mode=0, device="cuda:0", stream=None):
         import torch
         if not torch.cuda.is_available():
             raise DfvError("a CUDA device is required (no CPU fallback)")
@@ -348,12 +366,15 @@ class Batch:
                 d.n[k] = wl.n[k]
                 d.lo[k] = wl.lo[k]
                 d.hi[k] = wl.hi[k]
-                d.bc[2 * k] = d.bc[2 * k + 1] = DFV_BC_PERIODIC if wl.periodic[k] else DFV_BC_TRANSMISSIVE
+            codes = bc_codes(2, wl.periodic, getattr(wl, "walls", None))
+            for k in range(4):
+                d.bc[k] = codes[k]
             d.n[2] = 1
             for k in range(3):
                 d.v_body[k] = wl.body_v[k] if k < len(wl.body_v) else 0.0
         self._descs = descs
-        opt = dfv_options(self.nmat, 0, int(bool(use_thinc)), float(thinc_beta))
+        opt = dfv_options(self.nmat, 0, int(bool(use_thinc)), float(thinc_beta), int(bool(hllc_lm)), int(seed_variant),
+                          int(normal_method), int(probe_mode))
         nbytes = ctypes.c_size_t()
         _check(L.dfv_batch_workspace_bytes(2, self.count, descs, precision, ctypes.byref(opt), ctypes.byref(nbytes)),
                None, "dfv_batch_workspace_bytes")

@@ -223,7 +223,7 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false)
         }
         DFV_CU(g, cudaEventRecord(ev[0], g->stream), "event");
     }
-    DFV_CU(g, g->ops->seed(g->g, g->U, g->ctl, g->stream), "k_seed");
+    DFV_CU(g, g->ops->seed(g->g, g->U, g->U1, g->ctl, g->stream), "k_seed");
     if (rec) DFV_CU(g, cudaEventRecord(ev[1], g->stream), "event");
     DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, 0, g->stream),
            "k_stage<1>");
@@ -239,7 +239,7 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false)
         DFV_CU(g, cudaEventRecord(ev[5], g->stream), "event");
         g->ev_steps.push_back(ev);
     }
-    g->launches += 4;
+    g->launches += g->g.probe_mode == 1 ? 5 : 4;
     return DFV_OK;
 }
 
@@ -282,8 +282,11 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
     for (int d = 0; d < dim; d++) {
         if ((bcs[2 * d] == DFV_BC_PERIODIC) != (bcs[2 * d + 1] == DFV_BC_PERIODIC)) return DFV_ERR_ARG;
         for (int s = 0; s < 2; s++)
-            if (bcs[2 * d + s] != DFV_BC_PERIODIC && bcs[2 * d + s] != DFV_BC_TRANSMISSIVE) return DFV_ERR_ARG;
+            if (bcs[2 * d + s] != DFV_BC_PERIODIC && bcs[2 * d + s] != DFV_BC_TRANSMISSIVE &&
+                bcs[2 * d + s] != DFV_BC_REFLECTIVE)
+                return DFV_ERR_ARG;
     }
+    if (opt->normal_method == 1 && dim != 2) return DFV_ERR_UNSUPPORTED;
     const Ops *ops = pick_ops(precision, dim, opt->nmat, opt->solid ? 1 : 0);
     if (!ops) return DFV_ERR_UNSUPPORTED;
     const Layout L = plan(dim, n3, opt->nmat, opt->solid ? 1 : 0, precision);
@@ -316,6 +319,7 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
     for (int d = 0; d < 3; d++) {
         p.n[d] = n3[d];
         p.periodic[d] = (d < dim) ? (bcs[2 * d] == DFV_BC_PERIODIC) : 0;
+        for (int s = 0; s < 2; s++) p.wall[d][s] = (d < dim) ? (bcs[2 * d + s] == DFV_BC_REFLECTIVE) : 0;
         p.lo[d] = d < dim ? lo[d] : 0.0;
         p.dx[d] = d < dim ? (hi[d] - lo[d]) / n3[d] : 1.0;
         p.inv_dx[d] = 1.0 / p.dx[d];
@@ -326,12 +330,8 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
         }
     }
     p.pitch = L.pitch;
-    p.use_thinc = opt->use_thinc ? 1 : 0;
-    p.beta = opt->thinc_beta > 0.0 ? opt->thinc_beta : 1.6;
-    p.cosh_b = std::cosh(p.beta);
-    p.sinh_b = std::sinh(p.beta);
-    p.tanh_b = std::tanh(p.beta);
-    p.phi_guard = 1e-14;
+    dfv::apply_options(p, opt->use_thinc, opt->thinc_beta, opt->hllc_lm, opt->seed_variant,
+                       opt->normal_method, opt->probe_mode);
     dfv::finish_params(p);
     {
         const dim3 sg = ops->stage_grid(p);

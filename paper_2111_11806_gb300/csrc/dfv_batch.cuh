@@ -82,14 +82,20 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_s
 // Rigid seeding of every instance: blockIdx.y is the instance, the blocks of
 // that row stride over its cells; the instance record is read through the
 // cache, and only by threads whose cell is rigid.
-template <class R, int NMAT>
+// MODE 0: in place; 1: seeded states into the scratch planes b.out; 2: the
+// scratch into U (the fixed probe reads the step-start state only).
+template <class R, int NMAT, int MODE>
 __global__ void __launch_bounds__(256) k_batch_seed(BatchArgs b)
 {
     const BatchInst &I = b.inst[blockIdx.y];
     R *U = reinterpret_cast<R *>(const_cast<void *>(b.in)) + I.off;
+    R *S = reinterpret_cast<R *>(b.out) + I.off;
     const long long nc = I.g.ncell;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x)
-        seed_cell<R, 2, NMAT, false>(U, I.ctl, I.g, c);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+        if (MODE == 0) seed_cell<R, 2, NMAT, false>(U, I.ctl, I.g, c);
+        else if (MODE == 1) seed_cell_to<R, 2, NMAT, false>(U, S, I.ctl, I.g, c);
+        else seed_apply<R, 2, NMAT, false>(U, S, I.g, c);
+    }
 }
 
 // CFL wave speed of every instance's stored state; the last tile of each
@@ -196,11 +202,13 @@ struct BK {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_stage<R, NMAT, 3>, threads, smem);
         return std::max(1, std::min(a, b));
     }
-    // phase: 0 seed, 1..3 stages, 4 CFL
+    // phase: 0 seed in place, 1..3 stages, 4 CFL, 5 / 6 seed to scratch / apply
     static cudaError_t launch(int phase, int grid, const BatchArgs &a, cudaStream_t st)
     {
         switch (phase) {
-        case 0: k_batch_seed<R, NMAT><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        case 0: k_batch_seed<R, NMAT, 0><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        case 5: k_batch_seed<R, NMAT, 1><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        case 6: k_batch_seed<R, NMAT, 2><<<dim3(32, grid), 256, 0, st>>>(a); break;
         case 1: k_batch_stage<R, NMAT, 1><<<grid, threads, smem, st>>>(a); break;
         case 2: k_batch_stage<R, NMAT, 2><<<grid, threads, smem, st>>>(a); break;
         case 3: k_batch_stage<R, NMAT, 3><<<grid, threads, smem, st>>>(a); break;

@@ -181,13 +181,14 @@ int grid_size(dfv_batch *b)
 dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out, int final_mode, int slot)
 {
     BatchArgs a = args(b, in, un, out, final_mode);
-    const bool light = (ph == 0 || ph == 4);
+    const bool light = (ph == 0 || ph == 4 || ph == 5 || ph == 6);
     if (b->schedule == 2 && !light) {
         a.queue = b->d_queue + slot;
         B_CU(b, cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), b->stream), "queue reset");
     }
     // seeding: one row of blocks per instance; CFL: one CTA per item
-    const int grid = ph == 0 ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
+    const bool seeding = (ph == 0 || ph == 5 || ph == 6);
+    const int grid = seeding ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
     B_CU(b, b->kern.launch(ph, grid, a, b->stream), "batch kernel");
     b->launches++;
     return DFV_OK;
@@ -213,7 +214,14 @@ dfv_status batch_step(dfv_batch *b, bool capturing)
         for (auto &e : ev) e = take_ev(b);
         B_CU(b, cudaEventRecord(ev[0], b->stream), "event");
     }
-    dfv_status s = phase(b, 0, b->U, b->U, b->U, 0, 0);
+    dfv_status s;
+    if (b->opt.probe_mode == 1) {
+        // the fixed probe may read rigid cells: seed from the step-start state via U1
+        if ((s = phase(b, 5, b->U, b->U, b->U1, 0, 0)) != DFV_OK) return s;
+        s = phase(b, 6, b->U, b->U, b->U1, 0, 0);
+    } else {
+        s = phase(b, 0, b->U, b->U, b->U, 0, 0);
+    }
     if (s != DFV_OK) return s;
     if (rec) B_CU(b, cudaEventRecord(ev[1], b->stream), "event");
     if ((s = phase(b, 1, b->U, b->U, b->U1, 0, 1)) != DFV_OK) return s;
@@ -289,7 +297,9 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     for (int i = 0; i < count; i++)
         for (int d = 0; d < 2; d++)
             if (!(desc[i].hi[d] > desc[i].lo[d]) ||
-                ((desc[i].bc[2 * d] == DFV_BC_PERIODIC) != (desc[i].bc[2 * d + 1] == DFV_BC_PERIODIC))) {
+                ((desc[i].bc[2 * d] == DFV_BC_PERIODIC) != (desc[i].bc[2 * d + 1] == DFV_BC_PERIODIC)) ||
+                desc[i].bc[2 * d] < DFV_BC_TRANSMISSIVE || desc[i].bc[2 * d] > DFV_BC_REFLECTIVE ||
+                desc[i].bc[2 * d + 1] < DFV_BC_TRANSMISSIVE || desc[i].bc[2 * d + 1] > DFV_BC_REFLECTIVE) {
                 delete b;
                 return DFV_ERR_ARG;
             }
@@ -325,6 +335,7 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
         for (int d = 0; d < 3; d++) {
             p.n[d] = d < 2 ? desc[i].n[d] : 1;
             p.periodic[d] = d < 2 ? (desc[i].bc[2 * d] == DFV_BC_PERIODIC) : 0;
+            for (int s = 0; s < 2; s++) p.wall[d][s] = d < 2 ? (desc[i].bc[2 * d + s] == DFV_BC_REFLECTIVE) : 0;
             p.lo[d] = d < 2 ? desc[i].lo[d] : 0.0;
             p.dx[d] = d < 2 ? (desc[i].hi[d] - desc[i].lo[d]) / p.n[d] : 1.0;
             p.inv_dx[d] = 1.0 / p.dx[d];
@@ -335,12 +346,8 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
             }
         }
         p.pitch = (p.ncell + 63) / 64 * 64;
-        p.use_thinc = opt->use_thinc ? 1 : 0;
-        p.beta = opt->thinc_beta > 0.0 ? opt->thinc_beta : 1.6;
-        p.cosh_b = std::cosh(p.beta);
-        p.sinh_b = std::sinh(p.beta);
-        p.tanh_b = std::tanh(p.beta);
-        p.phi_guard = 1e-14;
+        dfv::apply_options(p, opt->use_thinc, opt->thinc_beta, opt->hllc_lm, opt->seed_variant,
+                       opt->normal_method, opt->probe_mode);
         I.off = P.inst_off[i];
         I.part0 = P.inst_part0[i];
         I.tiles_x = P.tiles_x[i];

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace dfv {
 
 // ------------------------------------------------------------------ params
@@ -54,6 +56,11 @@ struct GridP {
     double dV, dxmin;
     MatP mat[2];
     int use_thinc;
+    int hllc_lm;        // 1: low-Mach HLLC-LM dissipation in the star regions
+    int seed_variant;   // 0: reflected state (Sec. 3.2), 1: Riemann-problem star state
+    int normal_method;  // 0: Youngs, 1: ELVIRA (2-D) (Sec. 3.3)
+    int probe_mode;     // 0: stepped probe 1.0..4.0 dx, 1: fixed 1.5 dx (Sec. 3.2)
+    int wall[3][2];     // reflective wall on the low / high side of direction d
     double beta, cosh_b, sinh_b, tanh_b;   // THINC constants
     double phi_guard;
     MatC<double> mc_d[2];
@@ -92,6 +99,23 @@ __host__ inline void fill_consts(const GridP &g, MatC<T> *mc, GridC<T> &gc)
     gc.tanh_b = (T)g.tanh_b;
     gc.inv_sinh_b = (T)(1.0 / g.sinh_b);
     gc.phi_guard = (T)g.phi_guard;
+}
+
+// The scheme options of a grid: THINC on/off and its steepness (default 1.6),
+// the HLLC-LM flux, the seeding variant, the normal method and the probe.
+__host__ inline void apply_options(GridP &g, int use_thinc, double thinc_beta, int hllc_lm, int seed_variant,
+                                   int normal_method, int probe_mode)
+{
+    g.normal_method = normal_method == 1 ? 1 : 0;
+    g.probe_mode = probe_mode == 1 ? 1 : 0;
+    g.use_thinc = use_thinc ? 1 : 0;
+    g.beta = thinc_beta > 0.0 ? thinc_beta : 1.6;
+    g.cosh_b = std::cosh(g.beta);
+    g.sinh_b = std::sinh(g.beta);
+    g.tanh_b = std::tanh(g.beta);
+    g.hllc_lm = hllc_lm ? 1 : 0;
+    g.seed_variant = seed_variant == 1 ? 1 : 0;
+    g.phi_guard = 1e-14;
 }
 
 // Derive the per-precision constants from the double parameters; call after
@@ -192,6 +216,8 @@ __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_sin(double x) { return sin(x); }
+__device__ __forceinline__ float m_sin(float x) { return sinf(x); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
 __device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
@@ -210,6 +236,20 @@ __device__ __forceinline__ int map_idx(int i, int n, int periodic)
         return m < 0 ? m + n : m;
     }
     return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
+}
+
+// Halo index of direction d with reflective walls: a wall side mirrors (cell
+// -1-i below, 2n-1-i above, clamped into the grid when n < 3); *flip is set
+// when the cell is a mirror image.
+__device__ __forceinline__ int halo_idx(const GridP &g, int d, int i, bool *flip)
+{
+    const int n = g.n[d];
+    if ((i < 0 && g.wall[d][0]) || (i > n - 1 && g.wall[d][1])) {
+        *flip = true;
+        const int m = i < 0 ? -1 - i : 2 * n - 1 - i;
+        return m < 0 ? 0 : (m > n - 1 ? n - 1 : m);
+    }
+    return map_idx(i, n, g.periodic[d]);
 }
 
 // ------------------------------------------------------ material closure
@@ -642,6 +682,30 @@ __device__ __forceinline__ void recon_face(const GridP &g, const T *s, bool frac
 
 // ------------------------------------------------------------- Riemann
 
+// Left value for w = 1, right value for w = 0, the mean for w = 1/2 (exactly
+// xl or xr in the first two cases).
+template <class T>
+__device__ __forceinline__ T upwind_mix(T w, T xl, T xr)
+{
+    return w == T(1) ? xl : (w == T(0) ? xr : T(0.5) * (xl + xr));
+}
+
+// out += a (U*_K - U_K) on the partial densities, momenta and energy, for the
+// HLLC star state of side K (wave speed SK, normal traction TK, contact Ss).
+template <class T, int DIM, int NMAT, bool SOLID, int D>
+__device__ __forceinline__ void star_jump(const State<T, DIM, NMAT, SOLID> &K, T SK, T TK, T Ss, T a, T *out)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    const T uK = K.u[D];
+    const T chi = (SK - uK) / (SK - Ss);
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) out[L::IAR + l] += a * (K.ar[l] * chi - K.ar[l]);
+#pragma unroll
+    for (int b = 0; b < DIM; b++) out[L::IMOM + b] += a * (K.rho * chi * (b == D ? Ss : K.u[b]) - K.rho * K.u[b]);
+    const T EK = K.rhoE / K.rho;
+    out[L::IE] += a * (K.rho * chi * (EK + (Ss - uK) * (Ss + TK / (K.rho * (SK - uK)))) - K.rhoE);
+}
+
 // HLLC flux across a face normal to direction D (Sec. 3.1: Toro's HLLC; the
 // fluid pressure replaced by the normal traction T = p - 2G devH_DD for solids;
 // Davis wave speeds; partial densities scaled like the mixture density).
@@ -672,7 +736,10 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
     const T TK = (region <= 1) ? TL : TR;
     const T uK = K.u[D];
     const bool star = (region == 1 || region == 2);
-    const bool left = Ss >= T(0);
+    // quantities carried by the contact take the left value for S* > 0, the
+    // right one for S* < 0 and the mean of both at S* = 0 (mirror-symmetric
+    // at a wall face)
+    const T wlf = Ss > T(0) ? T(1) : (Ss < T(0) ? T(0) : T(0.5));
     // Tangential traction and velocity at the face: the linear shear-wave
     // Riemann problem (sigma -/+ Z u constant along the shear characteristics,
     // Z = sqrt(rho G)); a gas (Z = 0) transmits no shear.  Without shear
@@ -681,7 +748,7 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
         sig_t[a] = T(0);
-        ut[a] = left ? sl.u[a] : sr.u[a];
+        ut[a] = upwind_mix(wlf, sl.u[a], sr.u[a]);
     }
     if (SOLID) {
         const T ZL = m_sqrt(sl.rho * sl.G), ZR = m_sqrt(sr.rho * sr.G);
@@ -729,14 +796,26 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
         const T Us = K.rho * chi * (EK + (Ss - uK) * (Ss + TK / (K.rho * (SK - uK))));
         out[L::IE] = star ? (K.rhoE * uK - work_n) + SK * (Us - K.rhoE) - work_s : K.rhoE * uK - work;
     }
+    if (star && g.hllc_lm) {
+        // HLLC-LM (the published low-Mach form): the centred flux
+        // (F_L + F_R)/2 + [phi S_L (U*_L - U_L) + |S*| (U*_L - U*_R) + phi S_R (U*_R - U_R)]/2
+        // with phi = sin(min(1, Ma/0.1) pi/2), Ma the larger face-normal Mach
+        // number.  With the jump conditions across the three waves this is
+        // the HLLC flux above minus (1 - phi)/2 [S_L (U*_L - U_L) + S_R (U*_R - U_R)]
+        // on the partial densities, momenta and energy.
+        const T Ma = m_max(m_abs(uL) / cL, m_abs(uR) / cR);
+        const T ph = m_sin(m_min(T(1), Ma / T(0.1)) * T(3.14159265358979323846) / T(2));
+        const T k = T(-0.5) * (T(1) - ph);
+        star_jump<T, DIM, NMAT, SOLID, D>(sl, SL, TL, Ss, k * SL, out);
+        star_jump<T, DIM, NMAT, SOLID, D>(sr, SR, TR, Ss, k * SR, out);
+    }
     // interface state at x/t = 0
-    const T *wu = left ? wL : wR;
     T us[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; a++) us[a] = star ? ut[a] : K.u[a];
     us[D] = (region == 0) ? uL : ((region == 3) ? uR : Ss);
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; l++) out[L::IPHI + l] = wu[L::IPHI + l] * us[D];
+    for (int l = 0; l < NMAT - 1; l++) out[L::IPHI + l] = upwind_mix(wlf, wL[L::IPHI + l], wR[L::IPHI + l]) * us[D];
 #pragma unroll
     for (int c = 0; c < L::NV; c++) {
         const int a = v_row(DIM, c), b = v_col(DIM, c);
@@ -744,9 +823,9 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
         T vdb = T(0);
 #pragma unroll
         for (int cc = 0; cc < L::NV; cc++)
-            if (v_row(DIM, cc) == D && v_col(DIM, cc) == b) vdb = wu[L::IV + cc];
+            if (v_row(DIM, cc) == D && v_col(DIM, cc) == b) vdb = upwind_mix(wlf, wL[L::IV + cc], wR[L::IV + cc]);
         const T ua = (a < DIM) ? us[a] : T(0);
-        out[L::IV + c] = wu[L::IV + c] * us[D] - vdb * ua;
+        out[L::IV + c] = upwind_mix(wlf, wL[L::IV + c], wR[L::IV + c]) * us[D] - vdb * ua;
     }
     out[L::IR] = (vr > T(0)) ? wL[L::IR] * vr : ((vr < T(0)) ? wR[L::IR] * vr : T(0));
     out[L::NVAR] = us[D];
@@ -755,7 +834,7 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
         T vdb = T(0);
 #pragma unroll
         for (int cc = 0; cc < L::NV; cc++)
-            if (v_row(DIM, cc) == D && v_col(DIM, cc) == b) vdb = wu[L::IV + cc];
+            if (v_row(DIM, cc) == D && v_col(DIM, cc) == b) vdb = upwind_mix(wlf, wL[L::IV + cc], wR[L::IV + cc]);
         out[L::NVAR + 1 + b] = vdb;
     }
 }

@@ -57,9 +57,17 @@ struct Impl {
         return stage_s<3>(g, a, st);
     }
 
-    static cudaError_t seed(const GridP &g, void *U, const Ctl *ctl, cudaStream_t st)
+    // seeding; scratch: planes of the grid's layout free until stage 1
+    static cudaError_t seed(const GridP &g, void *U, void *scratch, const Ctl *ctl, cudaStream_t st)
     {
-        k_seed<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(U, ctl, g);
+        if (g.probe_mode == 1) {
+            k_seed<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 1);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            k_seed<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 2);
+        } else {
+            k_seed<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 0);
+        }
         return cudaGetLastError();
     }
 

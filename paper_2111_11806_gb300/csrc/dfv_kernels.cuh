@@ -227,6 +227,157 @@ static __global__ void __launch_bounds__(1024) k_finalize(Ctl *ctl, const double
 // Only r < 0.5 cells are read and only r > 0.5 cells written, so the update is
 // independent of thread order.  Evaluated in the storage precision (FP64
 // closures below phi = 1e-6 as everywhere in the FP32 form).
+// ------------------------------------------------------ ELVIRA (Sec. 3.3)
+
+// Fraction of the rectangle [x0, x0+hx] x [y0, y0+hy] on the side
+// nx x + ny y <= alpha: coefficients made non-negative by reflecting the
+// rectangle, scaled to the unit square, then the piecewise closed form of the
+// area of {m1 s + m2 t <= a} (m1 >= m2 >= 0): triangle, trapezoid, square less
+// a triangle.
+__device__ __forceinline__ double cut_area(double nx, double ny, double alpha, double x0, double y0, double hx,
+                                           double hy)
+{
+    double a = alpha - nx * x0 - ny * y0;
+    double m1 = nx * hx, m2 = ny * hy;
+    if (m1 < 0.0) {
+        a -= m1;
+        m1 = -m1;
+    }
+    if (m2 < 0.0) {
+        a -= m2;
+        m2 = -m2;
+    }
+    if (m1 < m2) {
+        const double t = m1;
+        m1 = m2;
+        m2 = t;
+    }
+    if (a <= 0.0) return 0.0;
+    if (a >= m1 + m2) return 1.0;
+    if (a < m2) return a * a / (2.0 * m1 * m2);
+    if (a <= m1) return (a - 0.5 * m2) / m1;
+    const double b = m1 + m2 - a;
+    return 1.0 - b * b / (2.0 * m1 * m2);
+}
+
+// The line position alpha that leaves the fraction f of the rectangle on the
+// side n.x <= alpha: the inverse of the closed form above.
+__device__ __forceinline__ double cut_alpha(double nx, double ny, double f, double x0, double y0, double hx,
+                                            double hy)
+{
+    double m1 = nx * hx, m2 = ny * hy;
+    double shift = nx * x0 + ny * y0;
+    if (m1 < 0.0) {
+        shift += m1;
+        m1 = -m1;
+    }
+    if (m2 < 0.0) {
+        shift += m2;
+        m2 = -m2;
+    }
+    if (m1 < m2) {
+        const double t = m1;
+        m1 = m2;
+        m2 = t;
+    }
+    double a;
+    if (f <= 0.0) a = 0.0;
+    else if (f >= 1.0) a = m1 + m2;
+    else if (f * 2.0 * m1 <= m2) a = sqrt(2.0 * m1 * m2 * f);
+    else if ((1.0 - f) * 2.0 * m1 <= m2) a = m1 + m2 - sqrt(2.0 * m1 * m2 * (1.0 - f));
+    else a = f * m1 + 0.5 * m2;
+    return a + shift;
+}
+
+// ELVIRA outward normal of a cell from the 3x3 block b[3 (l+1) + (k+1)] of r
+// (cell (i+k, j+l)), in FP64: six candidates from the column sums (height y
+// of x) and row sums (x of y), backward / central / forward differences, each
+// oriented away from r = 1; each candidate line holds the centre cell's r and
+// the one reproducing the nine values best (least squares) wins, an earlier
+// candidate on ties within 1e-12 (central column, central row, backward
+// column, forward column, backward row, forward row).
+__device__ __forceinline__ void elvira_normal(const double b[9], double hx, double hy, double nrm[2])
+{
+    double h[3], gs[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) h[k] = (b[k] + b[3 + k] + b[6 + k]) * hy;
+#pragma unroll
+    for (int l = 0; l < 3; l++) gs[l] = (b[3 * l] + b[3 * l + 1] + b[3 * l + 2]) * hx;
+    const double sy = (gs[2] > gs[0]) ? -1.0 : 1.0;
+    const double sx = (h[2] > h[0]) ? -1.0 : 1.0;
+    const double mc0 = (h[2] - h[0]) / (2.0 * hx), mc1 = (h[1] - h[0]) / hx, mc2 = (h[2] - h[1]) / hx;
+    const double mr0 = (gs[2] - gs[0]) / (2.0 * hy), mr1 = (gs[1] - gs[0]) / hy, mr2 = (gs[2] - gs[1]) / hy;
+    const double cx[6] = {-mc0, sx, -mc1, -mc2, sx, sx};
+    const double cy[6] = {sy, -mr0, sy, sy, -mr1, -mr2};
+    double best = 0.0;
+    for (int c = 0; c < 6; c++) {
+        const double len = sqrt(cx[c] * cx[c] + cy[c] * cy[c]);
+        const double nx = cx[c] / len, ny = cy[c] / len;
+        const double alpha = cut_alpha(nx, ny, b[4], -0.5 * hx, -0.5 * hy, hx, hy);
+        double err = 0.0;
+#pragma unroll
+        for (int l = 0; l < 3; l++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const double f = cut_area(nx, ny, alpha, (k - 1.5) * hx, (l - 1.5) * hy, hx, hy);
+                err += (f - b[3 * l + k]) * (f - b[3 * l + k]);
+            }
+        if (c == 0 || err < best - 1e-12) {
+            best = err;
+            nrm[0] = nx;
+            nrm[1] = ny;
+        }
+    }
+}
+
+// Riemann-problem seeding (Sec. 3.2, step 5, second option): the conserved
+// right star state of the HLLC problem along the normal n between the
+// reflected primitives wl (left) and the interpolated primitives wr (right):
+// normal velocities u.n, normal tractions T = p - 2G n.devH.n, Davis speeds,
+// contact speed S*; the star state keeps the right state's volume fractions,
+// tangential velocity, stretch tensor and r, so its normal velocity is S*,
+// which the symmetric problem makes the body's v.n.
+template <class R, int DIM, int NMAT, bool SOLID>
+__device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R *wl, const R *wr, R *q)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    State<R, DIM, NMAT, SOLID> sl, sr;
+    state_from_prim<R, DIM, NMAT, SOLID>(g, wl, sl);
+    state_from_prim<R, DIM, NMAT, SOLID>(g, wr, sr);
+    R unL = R(0), unR = R(0), HnL = R(0), HnR = R(0);
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        unL += sl.u[a] * nv[a];
+        unR += sr.u[a] * nv[a];
+        if (SOLID) {
+#pragma unroll
+            for (int b = 0; b < DIM; b++) {
+                HnL += nv[a] * sl.H[a][b] * nv[b];
+                HnR += nv[a] * sr.H[a][b] * nv[b];
+            }
+        }
+    }
+    const R TL = SOLID ? sl.p - R(2) * sl.G * HnL : sl.p;
+    const R TR = SOLID ? sr.p - R(2) * sr.G * HnR : sr.p;
+    const R cL = m_sqrt(sl.c2), cR = m_sqrt(sr.c2);
+    const R SL = m_min(unL - cL, unR - cR), SR = m_max(unL + cL, unR + cR);
+    const R Ss = (TR - TL + sl.rho * unL * (SL - unL) - sr.rho * unR * (SR - unR)) /
+                 (sl.rho * (SL - unL) - sr.rho * (SR - unR));
+    const R chi = (SR - unR) / (SR - Ss);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; l++) q[L::IPHI + l] = sr.phi[l];
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) q[L::IAR + l] = sr.ar[l] * chi;
+    const R rs = sr.rho * chi;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) q[L::IMOM + a] = rs * (Ss * nv[a] + (sr.u[a] - unR * nv[a]));
+    const R ER = sr.rhoE / sr.rho;
+    q[L::IE] = rs * (ER + (Ss - unR) * (Ss + TR / (sr.rho * (SR - unR))));
+#pragma unroll
+    for (int c = 0; c < L::NV; c++) q[L::IV + c] = wr[L::IV + c];
+    q[L::IR] = wr[L::IR];
+}
+
 // The seeded conserved state of rigid cell c (Sec. 3.2), computed from the
 // fluid (r < 0.5) cells of U only; false when the cell is not seeded (r <= 0.5,
 // no gradient, or no valid probe point).
@@ -255,15 +406,32 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
         }
         const R gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
         if (!(gn * gc.dxmin > R(1e-10))) return false;
-        const R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
+        R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
+        if (DIM == 2 && g.normal_method == 1) {
+            double blk[9], n2[2];
+#pragma unroll
+            for (int l = -1; l <= 1; l++)
+#pragma unroll
+                for (int k = -1; k <= 1; k++) {
+                    const int ii = map_idx(ijk[0] + k, g.n[0], g.periodic[0]);
+                    const int jj = map_idx(ijk[1] + l, g.n[1], g.periodic[1]);
+                    blk[3 * (l + 1) + (k + 1)] = (double)U[L::IR * P + ii + (long long)g.n[0] * jj];
+                }
+            elvira_normal(blk, g.dx[0], g.dx[1], n2);
+            nv[0] = (R)n2[0];
+            nv[1] = (R)n2[1];
+            nv[2] = R(0);
+        }
         // Probe steps s = 1.0, 1.5, ..., 4.0 dx_min: the r values of all steps'
         // enclosing cells are fetched first (independent loads, one memory
         // round trip), then the first valid step is taken.
         constexpr int NC = 1 << DIM;
         int first = -1;
         unsigned int valid = 0u;
+        const bool fixed = g.probe_mode == 1;
 #pragma unroll
         for (int step = 0; step < 7; step++) {
+            if (fixed) break;
             const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
             int base[3] = {0, 0, 0};
 #pragma unroll
@@ -289,9 +457,11 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
             }
             if (ok && rmax == R(0)) valid |= 1u << step;
         }
-        if (!valid) return false;
-        first = __ffs(valid) - 1;
-        // interpolation at the chosen probe point
+        if (!fixed && !valid) return false;
+        first = fixed ? 1 : __ffs(valid) - 1;     // step 1 of the ladder is the fixed 1.5 dx_min
+        // interpolation at the chosen probe point (corner cells clamped into
+        // the grid, wrapped if periodic: the fixed probe reads them whatever
+        // their r)
         R wi[L::NVAR];
         {
             const R sd = (R(1) + R(0.5) * (R)first) * gc.dxmin;
@@ -314,9 +484,7 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
 #pragma unroll
                 for (int d = 0; d < DIM; d++) {
                     const int bit = (m >> d) & 1;
-                    int ii = base[d] + bit;
-                    if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
-                    ci[d] = ii;
+                    ci[d] = map_idx(base[d] + bit, g.n[d], g.periodic[d]);
                     wt *= bit ? fr[d] : (R(1) - fr[d]);
                 }
                 const long long cc = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
@@ -327,6 +495,11 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
 #pragma unroll
                 for (int v = 0; v < L::NVAR; v++) wi[v] += wt * w[v];
             }
+        }
+        R wr[L::NVAR];      // the interpolated state, kept for the Riemann variant
+        if (g.seed_variant == 1) {
+#pragma unroll
+            for (int v = 0; v < L::NVAR; v++) wr[v] = wi[v];
         }
         R Pm[3][3];
 #pragma unroll
@@ -367,7 +540,12 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
             }
         }
         wi[L::IR] = rc;
-        prim_to_cons<R, DIM, NMAT, SOLID>(g, wi, q);
+        if (g.seed_variant == 1) {
+            wr[L::IR] = rc;
+            seed_star<R, DIM, NMAT, SOLID>(g, nv, wi, wr, q);
+        } else {
+            prim_to_cons<R, DIM, NMAT, SOLID>(g, wi, q);
+        }
         return true;
     }
 }
@@ -383,13 +561,47 @@ __device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, 
         if (v != L::IR) U[v * g.pitch + c] = q[v];
 }
 
+// Seeding from the step-start state when the probe may read rigid cells
+// (fixed probe): the seeded state of cell c goes to the scratch planes S,
+// whose r plane flags it (1 seeded, 0 not); seed_apply then copies it into U.
 template <class R, int DIM, int NMAT, bool SOLID>
-__global__ void __launch_bounds__(256) k_seed(void *Uv, const Ctl *ctl, GridP g)
+__device__ __forceinline__ void seed_cell_to(const R *U, R *S, const Ctl *ctl, const GridP &g, long long c)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    if (!(U[L::IR * g.pitch + c] > R(0.5))) return;
+    R q[L::NVAR];
+    const bool ok = seed_compute<R, DIM, NMAT, SOLID>(U, ctl, g, c, q);
+    if (ok) {
+#pragma unroll
+        for (int v = 0; v < L::NVAR; v++)
+            if (v != L::IR) S[v * g.pitch + c] = q[v];
+    }
+    S[L::IR * g.pitch + c] = ok ? R(1) : R(0);
+}
+
+template <class R, int DIM, int NMAT, bool SOLID>
+__device__ __forceinline__ void seed_apply(R *U, const R *S, const GridP &g, long long c)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    if (!(U[L::IR * g.pitch + c] > R(0.5)) || S[L::IR * g.pitch + c] != R(1)) return;
+#pragma unroll
+    for (int v = 0; v < L::NVAR; v++)
+        if (v != L::IR) U[v * g.pitch + c] = S[v * g.pitch + c];
+}
+
+// mode 0: in place (stepped probe: reads only r < 0.5 cells, writes only
+// r > 0.5 cells); 1: seeded states into the scratch S; 2: S into U.
+template <class R, int DIM, int NMAT, bool SOLID>
+__global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl, GridP g, int mode)
 {
     R *U = reinterpret_cast<R *>(Uv);
+    R *S = reinterpret_cast<R *>(Sv);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
-         c += (long long)gridDim.x * blockDim.x)
-        seed_cell<R, DIM, NMAT, SOLID>(U, ctl, g, c);
+         c += (long long)gridDim.x * blockDim.x) {
+        if (mode == 0) seed_cell<R, DIM, NMAT, SOLID>(U, ctl, g, c);
+        else if (mode == 1) seed_cell_to<R, DIM, NMAT, SOLID>(U, S, ctl, g, c);
+        else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
+    }
 }
 
 // --------------------------------------------------------------- stage
@@ -492,14 +704,25 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
         const int lx = bx - B::HX, ly = by - B::HY, lz = bz - B::HZ;
         const int outside = (lx < 0 || lx >= TL::TX) + (ly < 0 || ly >= TL::TY) + (lz < 0 || lz >= TL::TZ);
         if (outside > 1) continue;
-        const int gx = map_idx(ox + lx, g.n[0], g.periodic[0]);
-        const int gy = DIM >= 2 ? map_idx(oy + ly, g.n[1], g.periodic[1]) : 0;
-        const int gz = DIM >= 3 ? map_idx(oz + lz, g.n[2], g.periodic[2]) : 0;
+        bool fl[3] = {false, false, false};
+        const int gx = halo_idx(g, 0, ox + lx, &fl[0]);
+        const int gy = DIM >= 2 ? halo_idx(g, 1, oy + ly, &fl[1]) : 0;
+        const int gz = DIM >= 3 ? halo_idx(g, 2, oz + lz, &fl[2]) : 0;
         const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
         R q[L::NVAR], w[L::NVAR];
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) q[v] = in[v * P + c];
         cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
+        // mirror image behind a reflective wall: u_d and the stretch
+        // components with exactly one index d change sign
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            if (!fl[d]) continue;
+            w[L::IMOM + d] = -w[L::IMOM + d];
+#pragma unroll
+            for (int cc = 0; cc < L::NV; cc++)
+                if ((v_row(DIM, cc) == d) != (v_col(DIM, cc) == d)) w[L::IV + cc] = -w[L::IV + cc];
+        }
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) sW[v * B::N + i] = w[v];
     }

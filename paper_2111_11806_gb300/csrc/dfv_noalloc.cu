@@ -95,12 +95,8 @@ extern "C" dfv_status dfv_compute_dt_noalloc(int dim, const int n[3], const doub
     if (p.ncell > DFV_NOALLOC_MAX_CELLS) return DFV_ERR_TOO_LARGE;
     if (plane_pitch < p.ncell) return DFV_ERR_ARG;
     p.pitch = plane_pitch;
-    p.use_thinc = opt->use_thinc ? 1 : 0;
-    p.beta = opt->thinc_beta > 0.0 ? opt->thinc_beta : 1.6;
-    p.cosh_b = std::cosh(p.beta);
-    p.sinh_b = std::sinh(p.beta);
-    p.tanh_b = std::tanh(p.beta);
-    p.phi_guard = 1e-14;
+    dfv::apply_options(p, opt->use_thinc, opt->thinc_beta, opt->hllc_lm, opt->seed_variant,
+                       opt->normal_method, opt->probe_mode);
     for (int l = 0; l < opt->nmat; l++) {
         if (kinds[l] < DFV_MAT_IDEAL || kinds[l] > DFV_MAT_ROMENSKII) return DFV_ERR_ARG;
         dfv::MatP &m = p.mat[l];

@@ -27,14 +27,15 @@ def rel_l1(got, ref, wl):
     return np.abs(got - ref).sum(axis=1) / plane_scales(ref, wl)
 
 
-def run_both(wl, steps, precision, cfl=None, use_run=False):
+def run_both(wl, steps, precision, cfl=None, use_run=False, **variants):
     """Advance the oracle and the GPU grid `steps` steps with the oracle's dt
-    (dfv_step) or the device-computed dt (dfv_run); returns (oracle, grid)."""
+    (dfv_step) or the device-computed dt (dfv_run); returns (oracle, grid).
+    variants: hllc_lm, seed_variant, given to both sides."""
     from oracle import Oracle
     from paper_2111_11806_gb300 import binding as B
     cfl = wl.cfl if cfl is None else cfl
-    o = Oracle.from_workload(wl)
-    g = B.Grid.from_workload(wl, precision=precision)
+    o = Oracle.from_workload(wl, **variants)
+    g = B.Grid.from_workload(wl, precision=precision, **variants)
     if use_run:
         g.run(steps, cfl)
         for _ in range(steps):

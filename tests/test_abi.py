@@ -59,3 +59,27 @@ def test_product_fails_loudly_without_library(tmp_path):
         binding._lib = None
         binding.load(str(tmp_path / "missing.so"))
     binding._lib = None
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's size
+    and field offsets (a field added on one side only fails here)."""
+    from paper_2111_11806_gb300 import binding
+    structs = {"dfv_options": binding.dfv_options, "dfv_material_params": binding.dfv_material_params,
+               "dfv_instance_desc": binding.dfv_instance_desc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dfvrb.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = dict(line.rsplit(" ", 1) for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(out[name + " sizeof"]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(out[name + " " + field]) == getattr(cls, field).offset, (name, field)

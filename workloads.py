@@ -204,6 +204,35 @@ def wedge_distance(X, Y, apex=(0.06, 0.05), half_angle_deg=30.0):
     return np.where(proj >= 0.0, line, np.hypot(xi, eta))
 
 
+def wedge_2d(nx: int = 1200, mach: float = 10.0, angle_deg: float = 30.0) -> Workload:
+    """Shock reflection from a wedge (the paper's wedge tests): non-dimensional
+    ideal gas (gamma 1.4) at rest with rho 1.4, p 1 on [0,3]x[0,2], a planar
+    Mach `mach` shock at x = 0.25, a rigid wedge rising from the floor at
+    x = 0.5 at `angle_deg`; the floor y = 0 is a reflective wall, the other
+    sides transmissive.  nx = 1200 (ny = 800) is the resolution of the
+    paper's finest level (300x200 base with two refinements by 2); CFL 0.4."""
+    ny = nx * 2 // 3
+    lo, hi = (0.0, 0.0), (3.0, 2.0)
+    X, Y, _ = cell_centres((nx, ny), lo, hi)
+    dx = min(3.0 / nx, 2.0 / ny)
+    gas = dict(kind="ideal", gamma=1.4)
+    w, L = _empty_prim(2, 1, False, nx * ny)
+    rho1, p1 = 1.4, 1.0
+    rho2, u2, p2 = ideal_shock_state(mach, 1.4, rho1, p1)
+    post = X < 0.25
+    w[L["irho"]] = np.where(post, rho2, rho1)
+    w[L["iu"]] = np.where(post, u2, 0.0)
+    w[L["ip"]] = np.where(post, p2, p1)
+    th = math.radians(angle_deg)
+    sx, sy = X - 0.5, Y
+    along = sx * math.cos(th) + sy * math.sin(th)
+    above = -sx * math.sin(th) + sy * math.cos(th)
+    sd = np.where(along >= 0.0, above, np.hypot(sx, sy))     # signed distance, positive in the gas
+    w[L["ir"]] = rigid_profile(sd, dx)
+    return Workload("wedge_2d_%dx%d_mach%g_%gdeg" % (nx, ny, mach, angle_deg), 2, (nx, ny), lo, hi, (0, 0), [gas],
+                    False, w, cfl=0.4, steps=0, t_end=0.2 if mach >= 5 else 1.2, walls=(0, 0, 1, 0, 0, 0))
+
+
 def impact_2d(n: int = 1024, seed_index: int = 4) -> Workload:
     """Aluminium-like block [0.005,0.025]x[0.03,0.07] m moving at 400 m/s into
     a static rigid wedge (apex (0.06,0.05), half-angle 30 deg) on [0,0.1]^2,
