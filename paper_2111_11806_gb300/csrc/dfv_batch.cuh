@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_s
 // cache, and only by threads whose cell is rigid.
 // MODE 0: in place; 1: seeded states into the scratch planes b.out; 2: the
 // scratch into U (the fixed probe reads the step-start state only).
-template <class R, int NMAT, int MODE>
+template <class R, int NMAT, int MODE, int OPT>
 __global__ void __launch_bounds__(256) k_batch_seed(BatchArgs b)
 {
     const BatchInst &I = b.inst[blockIdx.y];
@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(256) k_batch_seed(BatchArgs b)
     R *S = reinterpret_cast<R *>(b.out) + I.off;
     const long long nc = I.g.ncell;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
-        if (MODE == 0) seed_cell<R, 2, NMAT, false>(U, I.ctl, I.g, c);
-        else if (MODE == 1) seed_cell_to<R, 2, NMAT, false>(U, S, I.ctl, I.g, c);
+        if (MODE == 0) seed_cell<R, 2, NMAT, false, OPT>(U, I.ctl, I.g, c);
+        else if (MODE == 1) seed_cell_to<R, 2, NMAT, false, OPT>(U, S, I.ctl, I.g, c);
         else seed_apply<R, 2, NMAT, false>(U, S, I.g, c);
     }
 }
@@ -202,13 +202,24 @@ struct BK {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_stage<R, NMAT, 3>, threads, smem);
         return std::max(1, std::min(a, b));
     }
-    // phase: 0 seed in place, 1..3 stages, 4 CFL, 5 / 6 seed to scratch / apply
-    static cudaError_t launch(int phase, int grid, const BatchArgs &a, cudaStream_t st)
+    template <int MODE>
+    static void seed(int opt, int grid, const BatchArgs &a, cudaStream_t st)
+    {
+        switch (opt) {
+        case 0: k_batch_seed<R, NMAT, MODE, 0><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        case 1: k_batch_seed<R, NMAT, MODE, 1><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        case 2: k_batch_seed<R, NMAT, MODE, 2><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        default: k_batch_seed<R, NMAT, MODE, 3><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        }
+    }
+    // phase: 0 seed in place, 1..3 stages, 4 CFL, 5 / 6 seed to scratch / apply;
+    // opt: the seeding option set (seed_opt)
+    static cudaError_t launch(int phase, int grid, const BatchArgs &a, int opt, cudaStream_t st)
     {
         switch (phase) {
-        case 0: k_batch_seed<R, NMAT, 0><<<dim3(32, grid), 256, 0, st>>>(a); break;
-        case 5: k_batch_seed<R, NMAT, 1><<<dim3(32, grid), 256, 0, st>>>(a); break;
-        case 6: k_batch_seed<R, NMAT, 2><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        case 0: seed<0>(opt, grid, a, st); break;
+        case 5: seed<1>(opt, grid, a, st); break;
+        case 6: k_batch_seed<R, NMAT, 2, 0><<<dim3(32, grid), 256, 0, st>>>(a); break;
         case 1: k_batch_stage<R, NMAT, 1><<<grid, threads, smem, st>>>(a); break;
         case 2: k_batch_stage<R, NMAT, 2><<<grid, threads, smem, st>>>(a); break;
         case 3: k_batch_stage<R, NMAT, 3><<<grid, threads, smem, st>>>(a); break;
@@ -221,7 +232,7 @@ struct BK {
 struct Kern {
     cudaError_t (*prepare)();
     int (*max_ctas_per_sm)();
-    cudaError_t (*launch)(int, int, const BatchArgs &, cudaStream_t);
+    cudaError_t (*launch)(int, int, const BatchArgs &, int, cudaStream_t);
 };
 
 template <class R>

@@ -95,6 +95,7 @@ Kern kernels_for(int precision, int nmat)
 
 struct dfv_batch {
     int count = 0, precision = 0, nmat_opt = 1, nmat = 0;
+    int seed_opt = 0;   // seeding option set of every instance (dfv::seed_opt)
     dfv_options opt{};
     Plan plan;
     std::vector<dfv_instance_desc> desc;
@@ -189,7 +190,7 @@ dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out
     // seeding: one row of blocks per instance; CFL: one CTA per item
     const bool seeding = (ph == 0 || ph == 5 || ph == 6);
     const int grid = seeding ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
-    B_CU(b, b->kern.launch(ph, grid, a, b->stream), "batch kernel");
+    B_CU(b, b->kern.launch(ph, grid, a, b->seed_opt, b->stream), "batch kernel");
     b->launches++;
     return DFV_OK;
 }
@@ -284,6 +285,7 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     b->precision = precision;
     b->opt = *opt;
     b->nmat_opt = opt->nmat;
+    b->seed_opt = (opt->normal_method == 1 ? 1 : 0) | (opt->seed_variant == 1 ? 2 : 0);
     b->desc.assign(desc, desc + count);
     if (!plan_batch(count, desc, precision, opt->nmat, b->plan)) {
         delete b;

@@ -217,6 +217,11 @@ __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_sin(double x) { return sin(x); }
+// products and sums rounded one by one (never fused into an FMA)
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float m_sin(float x) { return sinf(x); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
@@ -724,8 +729,12 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
     const T TR = SOLID ? sr.p - T(2) * sr.G * sr.H[D][D] : sr.p;
     const T SL = m_min(uL - cL, uR - cR);
     const T SR = m_max(uL + cL, uR + cR);
-    const T Ss = (TR - TL + sl.rho * uL * (SL - uL) - sr.rho * uR * (SR - uR)) /
-                 (sl.rho * (SL - uL) - sr.rho * (SR - uR));
+    // contact speed; the numerator's products are rounded one by one and
+    // summed left to right, so that mirror-image states (a wall face) give
+    // S* = 0 exactly
+    const T num = add_rn(add_rn(TR - TL, mul_rn(mul_rn(sl.rho, uL), SL - uL)),
+                         -mul_rn(mul_rn(sr.rho, uR), SR - uR));
+    const T Ss = num / (sl.rho * (SL - uL) - sr.rho * (SR - uR));
     int region;
     if (SL >= T(0)) region = 0;
     else if (Ss >= T(0)) region = 1;

@@ -57,18 +57,29 @@ struct Impl {
         return stage_s<3>(g, a, st);
     }
 
+    template <int OPT>
+    static cudaError_t seed_opt_k(const GridP &g, void *U, void *scratch, const Ctl *ctl, cudaStream_t st)
+    {
+        if (g.probe_mode == 1) {
+            k_seed<R, DIM, NMAT, SOLID, OPT><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 1);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            k_seed<R, DIM, NMAT, SOLID, OPT><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 2);
+        } else {
+            k_seed<R, DIM, NMAT, SOLID, OPT><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 0);
+        }
+        return cudaGetLastError();
+    }
+
     // seeding; scratch: planes of the grid's layout free until stage 1
     static cudaError_t seed(const GridP &g, void *U, void *scratch, const Ctl *ctl, cudaStream_t st)
     {
-        if (g.probe_mode == 1) {
-            k_seed<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 1);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            k_seed<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 2);
-        } else {
-            k_seed<R, DIM, NMAT, SOLID><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 0);
+        switch (seed_opt(g)) {
+        case 0: return seed_opt_k<0>(g, U, scratch, ctl, st);
+        case 1: return seed_opt_k<1>(g, U, scratch, ctl, st);
+        case 2: return seed_opt_k<2>(g, U, scratch, ctl, st);
+        default: return seed_opt_k<3>(g, U, scratch, ctl, st);
         }
-        return cudaGetLastError();
     }
 
     static cudaError_t cfl(const GridP &g, const void *U, double *partials, int nblocks, cudaStream_t st)

@@ -76,6 +76,8 @@ template <class R>
 struct Acc {
     R hi, lo;
     __device__ __forceinline__ void zero() { hi = R(0); lo = R(0); }
+    // first term: exact, no compensation needed
+    __device__ __forceinline__ void set(R x) { hi = x; lo = R(0); }
     __device__ __forceinline__ void add(R x)
     {
         if (sizeof(R) == 8) {
@@ -381,7 +383,9 @@ __device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R
 // The seeded conserved state of rigid cell c (Sec. 3.2), computed from the
 // fluid (r < 0.5) cells of U only; false when the cell is not seeded (r <= 0.5,
 // no gradient, or no valid probe point).
-template <class R, int DIM, int NMAT, bool SOLID>
+// OPT: bit 0 ELVIRA normals (2-D), bit 1 Riemann-problem variant; each option
+// set is its own kernel so that the plain seeding keeps its small footprint.
+template <class R, int DIM, int NMAT, bool SOLID, int OPT>
 __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const GridP &g, long long c, R *q)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -407,7 +411,7 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
         const R gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
         if (!(gn * gc.dxmin > R(1e-10))) return false;
         R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
-        if (DIM == 2 && g.normal_method == 1) {
+        if constexpr (DIM == 2 && (OPT & 1)) {
             double blk[9], n2[2];
 #pragma unroll
             for (int l = -1; l <= 1; l++)
@@ -497,7 +501,7 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
             }
         }
         R wr[L::NVAR];      // the interpolated state, kept for the Riemann variant
-        if (g.seed_variant == 1) {
+        if constexpr ((OPT & 2) != 0) {
 #pragma unroll
             for (int v = 0; v < L::NVAR; v++) wr[v] = wi[v];
         }
@@ -540,7 +544,7 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
             }
         }
         wi[L::IR] = rc;
-        if (g.seed_variant == 1) {
+        if constexpr ((OPT & 2) != 0) {
             wr[L::IR] = rc;
             seed_star<R, DIM, NMAT, SOLID>(g, nv, wi, wr, q);
         } else {
@@ -550,12 +554,12 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
     }
 }
 
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, bool SOLID, int OPT>
 __device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, long long c)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     R q[L::NVAR];
-    if (!seed_compute<R, DIM, NMAT, SOLID>(U, ctl, g, c, q)) return;
+    if (!seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, c, q)) return;
 #pragma unroll
     for (int v = 0; v < L::NVAR; v++)
         if (v != L::IR) U[v * g.pitch + c] = q[v];
@@ -564,13 +568,13 @@ __device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, 
 // Seeding from the step-start state when the probe may read rigid cells
 // (fixed probe): the seeded state of cell c goes to the scratch planes S,
 // whose r plane flags it (1 seeded, 0 not); seed_apply then copies it into U.
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, bool SOLID, int OPT>
 __device__ __forceinline__ void seed_cell_to(const R *U, R *S, const Ctl *ctl, const GridP &g, long long c)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     if (!(U[L::IR * g.pitch + c] > R(0.5))) return;
     R q[L::NVAR];
-    const bool ok = seed_compute<R, DIM, NMAT, SOLID>(U, ctl, g, c, q);
+    const bool ok = seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, c, q);
     if (ok) {
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++)
@@ -591,17 +595,23 @@ __device__ __forceinline__ void seed_apply(R *U, const R *S, const GridP &g, lon
 
 // mode 0: in place (stepped probe: reads only r < 0.5 cells, writes only
 // r > 0.5 cells); 1: seeded states into the scratch S; 2: S into U.
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, bool SOLID, int OPT>
 __global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl, GridP g, int mode)
 {
     R *U = reinterpret_cast<R *>(Uv);
     R *S = reinterpret_cast<R *>(Sv);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
-        if (mode == 0) seed_cell<R, DIM, NMAT, SOLID>(U, ctl, g, c);
-        else if (mode == 1) seed_cell_to<R, DIM, NMAT, SOLID>(U, S, ctl, g, c);
+        if (mode == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, c);
+        else if (mode == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, c);
         else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
     }
+}
+
+// The option set of a grid as the OPT template argument of the seeding.
+__host__ __device__ inline int seed_opt(const GridP &g)
+{
+    return (g.normal_method == 1 && g.dim == 2 ? 1 : 0) | (g.seed_variant == 1 ? 2 : 0);
 }
 
 // --------------------------------------------------------------- stage
@@ -670,7 +680,8 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
                                          : R(0);
                 snc = (R(2) / R(3) * sW[v * B::N + bcell] * dus - ua * dv) * inv;
             }
-            Dacc[v].add(div - snc);
+            if (D == 0) Dacc[v].set(div - snc);
+            else Dacc[v].add(div - snc);
         }
     }
     __syncthreads();

@@ -62,7 +62,8 @@ def test_variant_fp64_100_steps(name, make, var):
 FP32 = [
     ("cylinder_64_lm", lambda: W.cylinder_2d(64), 50, LM),
     ("impact_96_rs", lambda: W.impact_2d(96), 20, RS),
-    ("dynamic_body_128x64_both", lambda: W.dynamic_body_2d(128, 64), 30, BOTH),
+    ("dynamic_body_128x64_rs", lambda: W.dynamic_body_2d(128, 64), 30, RS),
+    ("cylinder_96x80_both", lambda: W.cylinder_2d(96, ny=80), 40, BOTH),
 ]
 
 
