@@ -61,12 +61,12 @@ struct Impl {
     static cudaError_t seed_opt_k(const GridP &g, void *U, void *scratch, const Ctl *ctl, cudaStream_t st)
     {
         if (g.probe_mode == 1) {
-            k_seed<R, DIM, NMAT, SOLID, OPT><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 1);
+            k_seed<R, DIM, NMAT, SOLID, OPT, 1><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
-            k_seed<R, DIM, NMAT, SOLID, OPT><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 2);
+            k_seed<R, DIM, NMAT, SOLID, 0, 2><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g);
         } else {
-            k_seed<R, DIM, NMAT, SOLID, OPT><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g, 0);
+            k_seed<R, DIM, NMAT, SOLID, OPT, 0><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g);
         }
         return cudaGetLastError();
     }

@@ -433,9 +433,9 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
         int first = -1;
         unsigned int valid = 0u;
         const bool fixed = g.probe_mode == 1;
+        if (!fixed) {
 #pragma unroll
         for (int step = 0; step < 7; step++) {
-            if (fixed) break;
             const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
             int base[3] = {0, 0, 0};
 #pragma unroll
@@ -460,6 +460,7 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
                 rmax = (rv < R(0.5)) ? rmax : R(1);
             }
             if (ok && rmax == R(0)) valid |= 1u << step;
+        }
         }
         if (!fixed && !valid) return false;
         first = fixed ? 1 : __ffs(valid) - 1;     // step 1 of the ladder is the fixed 1.5 dx_min
@@ -593,17 +594,17 @@ __device__ __forceinline__ void seed_apply(R *U, const R *S, const GridP &g, lon
         if (v != L::IR) U[v * g.pitch + c] = S[v * g.pitch + c];
 }
 
-// mode 0: in place (stepped probe: reads only r < 0.5 cells, writes only
+// MODE 0: in place (stepped probe: reads only r < 0.5 cells, writes only
 // r > 0.5 cells); 1: seeded states into the scratch S; 2: S into U.
-template <class R, int DIM, int NMAT, bool SOLID, int OPT>
-__global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl, GridP g, int mode)
+template <class R, int DIM, int NMAT, bool SOLID, int OPT, int MODE>
+__global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl, GridP g)
 {
     R *U = reinterpret_cast<R *>(Uv);
     R *S = reinterpret_cast<R *>(Sv);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
-        if (mode == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, c);
-        else if (mode == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, c);
+        if constexpr (MODE == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, c);
+        else if constexpr (MODE == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, c);
         else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
     }
 }
@@ -636,8 +637,37 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
     constexpr int EX = TL::TX + (D == 0), EY = TL::TY + (D == 1), EZ = TL::TZ + (D == 2);
     constexpr int NFACE = EX * EY * EZ;
     constexpr int SD = B::stride(D);
-    for (int item = threadIdx.x; item < NFACE; item += TL::THREADS) {
-        const int fx = item % EX, fy = (item / EX) % EY, fz = item / (EX * EY);
+    // Faces to threads: with 32-wide tiles every warp takes one row of 32
+    // faces (lane = x), and in the x sweep the warps past the last row take
+    // the rows' closing faces (x = 32); otherwise a flat index.
+    constexpr bool ROWS = TL::TX == 32 && DIM >= 2;
+    constexpr int NROW = TL::TY * TL::TZ;                   // rows of the tile
+    constexpr int ITEMS = ROWS ? TL::THREADS : NFACE;
+    static_assert(!ROWS || (D == 0 ? (NROW + (NROW + 31) / 32) * 32 <= TL::THREADS
+                                   : EY * EZ * 32 <= TL::THREADS), "a face without a thread");
+    for (int t = threadIdx.x; t < ITEMS; t += TL::THREADS) {
+        int fx, fy, fz;
+        if constexpr (ROWS) {
+            const int lane = t & 31, warp = t >> 5;
+            int row;
+            if (D == 0 && warp >= NROW) {
+                row = (warp - NROW) * 32 + lane;
+                fx = TL::TX;
+                if (row >= NROW) continue;
+            } else {
+                row = warp;
+                fx = lane;
+                if (row >= EY * EZ) continue;
+            }
+            fy = row % EY;
+            fz = row / EY;
+        } else {
+            if (t >= NFACE) continue;
+            fx = t % EX;
+            fy = (t / EX) % EY;
+            fz = t / (EX * EY);
+        }
+        const int item = (fz * EY + fy) * EX + fx;
         // box index of the cell on the right of the face
         const int bc = ((fz + B::HZ) * B::BY + (fy + B::HY)) * B::BX + (fx + B::HX);
         R wL[L::NVAR], wR[L::NVAR];
@@ -709,16 +739,23 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
     const long long P = g.pitch;
     const int ox = tbx * TL::TX, oy = tby * TL::TY, oz = tbz * TL::TZ;
 
-    // 1. primitives of the tile and its halo (the corner regions are unused)
+    // 1. primitives of the tile and its halo (the corner regions are unused);
+    // a tile whose halo lies inside the grid needs no boundary mapping
+    const bool interior = ox >= B::HX && ox + TL::TX + B::HX <= g.n[0] &&
+                          (DIM < 2 || (oy >= B::HY && oy + TL::TY + B::HY <= g.n[1])) &&
+                          (DIM < 3 || (oz >= B::HZ && oz + TL::TZ + B::HZ <= g.n[2]));
     for (int i = threadIdx.x; i < B::N; i += TL::THREADS) {
         const int bx = i % B::BX, by = (i / B::BX) % B::BY, bz = i / (B::BX * B::BY);
         const int lx = bx - B::HX, ly = by - B::HY, lz = bz - B::HZ;
         const int outside = (lx < 0 || lx >= TL::TX) + (ly < 0 || ly >= TL::TY) + (lz < 0 || lz >= TL::TZ);
         if (outside > 1) continue;
         bool fl[3] = {false, false, false};
-        const int gx = halo_idx(g, 0, ox + lx, &fl[0]);
-        const int gy = DIM >= 2 ? halo_idx(g, 1, oy + ly, &fl[1]) : 0;
-        const int gz = DIM >= 3 ? halo_idx(g, 2, oz + lz, &fl[2]) : 0;
+        int gx = ox + lx, gy = DIM >= 2 ? oy + ly : 0, gz = DIM >= 3 ? oz + lz : 0;
+        if (!interior) {
+            gx = halo_idx(g, 0, ox + lx, &fl[0]);
+            if (DIM >= 2) gy = halo_idx(g, 1, oy + ly, &fl[1]);
+            if (DIM >= 3) gz = halo_idx(g, 2, oz + lz, &fl[2]);
+        }
         const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
         R q[L::NVAR], w[L::NVAR];
 #pragma unroll

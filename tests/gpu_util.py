@@ -49,13 +49,10 @@ def run_both(wl, steps, precision, cfl=None, use_run=False, **variants):
 
 
 def same_kernel_bits(got, ref, wl, precision):
-    """Batch instance against the single-grid run of the same instance.
-    FP64: bit for bit.  FP32: the batch and single-grid stage kernels are
-    separate compilations of the same tile code, and the compiler may contract
-    a product and a sum into one FMA in one and not the other, so they agree to
-    FP32 rounding (relative L1 per plane <= 1e-6 after a few steps)."""
-    if precision == 0:
-        np.testing.assert_array_equal(got, ref)
-    else:
-        err = rel_l1(got, ref, wl)
-        assert np.all(err <= 1e-6), err
+    """Batch instance against the single-grid run of the same instance.  The
+    batch and single-grid kernels are separate compilations of the same tile
+    and seeding code, and the compiler may contract a product and a sum into
+    one FMA in one and not the other, so they agree to rounding: relative L1
+    per plane <= 1e-13 (FP64) or 1e-6 (FP32) after a few steps."""
+    err = rel_l1(got, ref, wl)
+    assert np.all(err <= (1e-13 if precision == 0 else 1e-6)), err

@@ -33,7 +33,7 @@ def test_batch_instances_equal_single_grids(precision):
         t = g.run(steps, 0.8)
         same_kernel_bits(b.get_fields(i), g.cons(), wl, precision)
         tb, _ = b.time(i)
-        assert tb == pytest.approx(t, rel=0 if precision == 0 else 1e-6)
+        assert tb == pytest.approx(t, rel=1e-13 if precision == 0 else 1e-6)
 
 
 @pytest.mark.parametrize("schedule", [0, 1, 2])
