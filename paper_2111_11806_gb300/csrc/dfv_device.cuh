@@ -146,6 +146,8 @@ __device__ __forceinline__ const GridC<float> &gridc<float>(const GridP &g) { re
 struct Ctl {
     double dt, t, t_end, cfl;
     double smax;              // max_cells sum_d (|u_d|+c)/dx_d of the last reduction
+    unsigned long long smax_acc;  // running maximum of the tiles of a stage-3 launch, as
+                                  // the bits of a non-negative double (0 between launches)
     double force[3];
     double v[3];
     double x[3];

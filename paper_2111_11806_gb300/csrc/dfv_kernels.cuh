@@ -170,6 +170,9 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
                                                double *sred)
 {
     double red[4] = {0.0, 0.0, 0.0, 0.0};
+    // tiles of a stage-3 launch fold their maximum into ctl->smax_acc instead
+    // of a partial (nb_cfl = 0 then): read it and leave it at 0
+    if ((mode & 1) && threadIdx.x == 0) red[0] = __longlong_as_double((long long)atomicExch(&ctl->smax_acc, 0ull));
     if (mode & 1)
         for (long long b = threadIdx.x; b < nb_cfl; b += THREADS) red[0] = fmax(red[0], partials[4 * b]);
     if (mode & 2) {
@@ -220,15 +223,6 @@ static __global__ void __launch_bounds__(1024) k_finalize(Ctl *ctl, const double
 
 // --------------------------------------------------------------- seeding
 
-// Rigid seeding (Sec. 3.2, original variant), one thread per cell, in place:
-// cells with r > 0.5 and |grad r| dx_min > 1e-10 get the outward normal
-// n = -grad r/|grad r| (Youngs, Sec. 3.3), probe points at 1.0, 1.5, ..., 4.0
-// dx_min along n, the first point whose 2^dim enclosing cell centres are in the
-// domain (wrapped if periodic) with r < 0.5 is interpolated multilinearly in
-// the primitives, and u <- (I - 2nn^T) u + 2 (v_r.n) n, V <- (I - 2nn^T) V (I - 2nn^T).
-// Only r < 0.5 cells are read and only r > 0.5 cells written, so the update is
-// independent of thread order.  Evaluated in the storage precision (FP64
-// closures below phi = 1e-6 as everywhere in the FP32 form).
 // ------------------------------------------------------ ELVIRA (Sec. 3.3)
 
 // Fraction of the rectangle [x0, x0+hx] x [y0, y0+hy] on the side
@@ -380,6 +374,18 @@ __device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R
     q[L::IR] = wr[L::IR];
 }
 
+// Rigid seeding (Sec. 3.2), one thread per cell: cells with r > 0.5 and
+// |grad r| dx_min > 1e-10 get the outward normal n = -grad r/|grad r| (Youngs,
+// Sec. 3.3) or the ELVIRA normal; the stepped probe tries points at 1.0, 1.5,
+// ..., 4.0 dx_min along n and takes the first whose 2^dim enclosing cell
+// centres are in the domain (wrapped if periodic) with r < 0.5, the fixed probe
+// takes 1.5 dx_min; the primitives are interpolated multilinearly there and
+// u <- (I - 2nn^T) u + 2 (v_r.n) n, V <- (I - 2nn^T) V (I - 2nn^T); the cell
+// gets that state (original variant) or the right HLLC star state between it
+// and the interpolated state (Riemann variant).  With the stepped probe only
+// r < 0.5 cells are read and only r > 0.5 cells written, so the update runs in
+// place independently of thread order.  Evaluated in the storage precision
+// (FP64 closures below phi = 1e-6 as everywhere in the FP32 form).
 // The seeded conserved state of rigid cell c (Sec. 3.2), computed from the
 // fluid (r < 0.5) cells of U only; false when the cell is not seeded (r <= 0.5,
 // no gradient, or no valid probe point).
@@ -851,10 +857,17 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
         }
     }
     if (STAGE == 3) {
-        // block maximum in the compute precision (the per-cell values are R)
+        // block maximum in the compute precision (the per-cell values are R),
+        // folded into the launch's running maximum: the bits of non-negative
+        // doubles order like the doubles, so an integer atomic max is exact
+        // and independent of the order of the tiles
         R *sr = reinterpret_cast<R *>(sred);
         const R m = block_max<TL::THREADS, R>(smax_cell, sr);
-        if (threadIdx.x == 0) a.partials[4 * tile_id] = (double)m;
+        if (threadIdx.x == 0) {
+            double md = (double)m;
+            if (!(md >= 0.0)) md = __longlong_as_double(0x7ff0000000000000LL);   // NaN -> +inf: dt = 0
+            atomicMax(&a.ctl->smax_acc, (unsigned long long)__double_as_longlong(md));
+        }
     }
     if (STAGE == 1 && a.want_force) {
         block_reduce4<TL::THREADS>(red, sred);
@@ -877,7 +890,7 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
         __syncthreads();
         if (s_last) {
             __threadfence();
-            finalize_block<TL::THREADS>(a.ctl, a.partials, nb, nb, a.final_mode, DIM, g.dx[0], g.dx[1], g.dx[2],
+            finalize_block<TL::THREADS>(a.ctl, a.partials, 0, nb, a.final_mode, DIM, g.dx[0], g.dx[1], g.dx[2],
                                         sred);
             if (threadIdx.x == 0) a.ctl->ticket = 0u;
         }
