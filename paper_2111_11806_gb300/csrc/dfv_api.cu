@@ -225,17 +225,18 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false)
     }
     DFV_CU(g, g->ops->seed(g->g, g->U, g->U1, g->ctl, g->stream), "k_seed");
     if (rec) DFV_CU(g, cudaEventRecord(ev[1], g->stream), "event");
-    DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, 0, g->stream),
+    DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, g->stream),
            "k_stage<1>");
     if (rec) DFV_CU(g, cudaEventRecord(ev[2], g->stream), "event");
-    DFV_CU(g, g->ops->stage(2, g->g, g->U1, g->U, g->U3, g->ctl, g->partials, 0, 0, g->stream), "k_stage<2>");
+    DFV_CU(g, g->ops->stage(2, g->g, g->U1, g->U, g->U3, g->ctl, g->partials, 0, g->stream), "k_stage<2>");
     if (rec) DFV_CU(g, cudaEventRecord(ev[3], g->stream), "event");
-    // stage 3's last block runs the finalize (CFL max, force sum, body update, next dt)
-    const int final_mode = 1 | (want_force ? 2 : 0) | 4 | mode_extra;
-    DFV_CU(g, g->ops->stage(3, g->g, g->U3, g->U, g->U, g->ctl, g->partials, 0, final_mode, g->stream),
-           "k_stage<3>");
+    DFV_CU(g, g->ops->stage(3, g->g, g->U3, g->U, g->U, g->ctl, g->partials, 0, g->stream), "k_stage<3>");
+    if (rec) DFV_CU(g, cudaEventRecord(ev[4], g->stream), "event");
+    // one block: CFL maximum (folded by the stage-3 tiles), force sum, body
+    // update, next dt
+    dfv_status fs = finalize(g, 1 | (want_force ? 2 : 0) | 4 | mode_extra, 0);
+    if (fs != DFV_OK) return fs;
     if (rec) {
-        DFV_CU(g, cudaEventRecord(ev[4], g->stream), "event");
         DFV_CU(g, cudaEventRecord(ev[5], g->stream), "event");
         g->ev_steps.push_back(ev);
     }

@@ -26,7 +26,8 @@ struct BatchArgs {
     const int2 *items;       // (instance, tile) in the order of the schedule
     long long nitems;
     double *partials;
-    int final_mode;          // finalize of each instance by its last tile (stage 3 / CFL)
+    int final_mode;          // finalize mode: by each instance's last tile (CFL phase) or
+                             // by the finalize phase after stage 3
     unsigned int *queue;     // dynamic schedule: next item counter (nullptr: static round-robin)
 };
 
@@ -74,7 +75,6 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_s
         a.ctl = I.ctl;
         a.partials = b.partials + 4 * I.part0;
         a.want_force = 0;
-        a.final_mode = b.final_mode;
         stage_tile<R, 2, NMAT, false, STAGE>(I.g, a, w.y % I.tiles_x, w.y / I.tiles_x, 0, w.y, I.ntiles);
     }
 }
@@ -160,6 +160,17 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS) k_batch_cfl(
     }
 }
 
+// Finalize of every instance after stage 3, one block per instance: its CFL
+// maximum (folded by its stage-3 tiles), time, step count and next dt.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_batch_finalize(BatchArgs b)
+{
+    __shared__ double sred[4 * 32];
+    const BatchInst &I = b.inst[blockIdx.x];
+    finalize_block<THREADS>(I.ctl, b.partials + 4 * I.part0, 0, 0, b.final_mode, 2, I.g.dx[0], I.g.dx[1],
+                            I.g.dx[2], sred);
+}
+
 static __global__ void k_batch_init_ctl(Ctl *ctl, int count, const double *v_body /* 3 per instance */)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
@@ -212,7 +223,8 @@ struct BK {
         default: k_batch_seed<R, NMAT, MODE, 3><<<dim3(32, grid), 256, 0, st>>>(a); break;
         }
     }
-    // phase: 0 seed in place, 1..3 stages, 4 CFL, 5 / 6 seed to scratch / apply;
+    // phase: 0 seed in place, 1..3 stages, 4 CFL, 5 / 6 seed to scratch / apply,
+    // 7 finalize after stage 3;
     // opt: the seeding option set (seed_opt)
     static cudaError_t launch(int phase, int grid, const BatchArgs &a, int opt, cudaStream_t st)
     {
@@ -220,6 +232,7 @@ struct BK {
         case 0: seed<0>(opt, grid, a, st); break;
         case 5: seed<1>(opt, grid, a, st); break;
         case 6: k_batch_seed<R, NMAT, 2, 0><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        case 7: k_batch_finalize<32><<<grid, 32, 0, st>>>(a); break;
         case 1: k_batch_stage<R, NMAT, 1><<<grid, threads, smem, st>>>(a); break;
         case 2: k_batch_stage<R, NMAT, 2><<<grid, threads, smem, st>>>(a); break;
         case 3: k_batch_stage<R, NMAT, 3><<<grid, threads, smem, st>>>(a); break;

@@ -182,13 +182,13 @@ int grid_size(dfv_batch *b)
 dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out, int final_mode, int slot)
 {
     BatchArgs a = args(b, in, un, out, final_mode);
-    const bool light = (ph == 0 || ph == 4 || ph == 5 || ph == 6);
+    const bool light = (ph == 0 || ph == 4 || ph == 5 || ph == 6 || ph == 7);
     if (b->schedule == 2 && !light) {
         a.queue = b->d_queue + slot;
         B_CU(b, cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), b->stream), "queue reset");
     }
     // seeding: one row of blocks per instance; CFL: one CTA per item
-    const bool seeding = (ph == 0 || ph == 5 || ph == 6);
+    const bool seeding = (ph == 0 || ph == 5 || ph == 6 || ph == 7);   // one block (row) per instance
     const int grid = seeding ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
     B_CU(b, b->kern.launch(ph, grid, a, b->seed_opt, b->stream), "batch kernel");
     b->launches++;
@@ -229,7 +229,8 @@ dfv_status batch_step(dfv_batch *b, bool capturing)
     if (rec) B_CU(b, cudaEventRecord(ev[2], b->stream), "event");
     if ((s = phase(b, 2, b->U1, b->U, b->U3, 0, 2)) != DFV_OK) return s;
     if (rec) B_CU(b, cudaEventRecord(ev[3], b->stream), "event");
-    if ((s = phase(b, 3, b->U3, b->U, b->U, 1 | 4 | 8, 3)) != DFV_OK) return s;
+    if ((s = phase(b, 3, b->U3, b->U, b->U, 0, 3)) != DFV_OK) return s;
+    if ((s = phase(b, 7, b->U, b->U, b->U, 1 | 4 | 8, 0)) != DFV_OK) return s;
     if (rec) {
         B_CU(b, cudaEventRecord(ev[4], b->stream), "event");
         b->ev_steps.push_back(ev);

@@ -42,7 +42,7 @@ struct Impl {
     }
 
     static cudaError_t stage(int s, const GridP &g, const void *in, const void *un, void *out, Ctl *ctl,
-                             double *partials, int want_force, int final_mode, cudaStream_t st)
+                             double *partials, int want_force, cudaStream_t st)
     {
         StageArgs a;
         a.in = in;
@@ -51,7 +51,6 @@ struct Impl {
         a.ctl = ctl;
         a.partials = partials;
         a.want_force = want_force;
-        a.final_mode = final_mode;
         if (s == 1) return stage_s<1>(g, a, st);
         if (s == 2) return stage_s<2>(g, a, st);
         return stage_s<3>(g, a, st);

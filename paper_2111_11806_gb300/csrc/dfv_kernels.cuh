@@ -630,7 +630,6 @@ struct StageArgs {
     Ctl *ctl;
     double *partials;   // 4 doubles per block
     int want_force;
-    int final_mode;     // stage 3: finalize mode run by the last block (0: none)
 };
 
 template <class R, int DIM, int NMAT, bool SOLID, int D>
@@ -876,23 +875,6 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
             pp[1] = red[1];
             pp[2] = red[2];
             pp[3] = red[3];
-        }
-    }
-    if (STAGE == 3 && a.final_mode) {
-        // the last block to finish reduces every block's partials (fixed order)
-        __shared__ unsigned int s_last;
-        const long long nb = ntiles;
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
-            s_last = (t == (unsigned int)(nb - 1)) ? 1u : 0u;
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            finalize_block<TL::THREADS>(a.ctl, a.partials, 0, nb, a.final_mode, DIM, g.dx[0], g.dx[1], g.dx[2],
-                                        sred);
-            if (threadIdx.x == 0) a.ctl->ticket = 0u;
         }
     }
 }

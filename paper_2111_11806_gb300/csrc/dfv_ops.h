@@ -19,7 +19,7 @@ struct Ops {
     dim3 (*stage_grid)(const GridP &);
     cudaError_t (*seed)(const GridP &, void *U, void *scratch, const Ctl *ctl, cudaStream_t);
     cudaError_t (*stage)(int stage, const GridP &, const void *in, const void *un, void *out, Ctl *ctl,
-                         double *partials, int want_force, int final_mode, cudaStream_t);
+                         double *partials, int want_force, cudaStream_t);
     cudaError_t (*cfl)(const GridP &, const void *U, double *partials, int nblocks, cudaStream_t);
     cudaError_t (*prim_to_cons)(const GridP &, const double *prim, long long ppitch, void *U, cudaStream_t);
     cudaError_t (*cons_to_prim)(const GridP &, const void *U, double *prim, long long ppitch, cudaStream_t);
