@@ -180,10 +180,10 @@ dfv_status read_ctl(dfv_grid *g, Ctl *h)
 // One-block finalize: nb_max partial blocks hold the CFL maxima.
 dfv_status finalize(dfv_grid *g, int mode, long long nb_max)
 {
-    dfv::k_finalize<<<1, 1024, 0, g->stream>>>(g->ctl, g->partials, nb_max, g->nb_stage, mode, g->dim, g->g.dx[0],
-                                                g->g.dx[1], g->g.dx[2]);
     g->launches++;
-    DFV_CU(g, cudaGetLastError(), "k_finalize");
+    DFV_CU(g, dfv::launch_pdl(dfv::k_finalize, dim3(1), dim3(1024), 0, g->stream, g->ctl, (const double *)g->partials,
+                              nb_max, g->nb_stage, mode, g->dim, g->g.dx[0], g->g.dx[1], g->g.dx[2]),
+           "k_finalize");
     return DFV_OK;
 }
 

@@ -54,6 +54,7 @@ __device__ __forceinline__ void load_inst(const BatchInst *src, BatchInst *dst)
 template <class R, int NMAT, int STAGE>
 __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_stage(BatchArgs b)
 {
+    pdl_enter();
     __shared__ BatchInst s_inst;
     __shared__ long long s_item;
     __shared__ int s_cur;
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_s
 template <class R, int NMAT, int MODE, int OPT>
 __global__ void __launch_bounds__(256) k_batch_seed(BatchArgs b)
 {
+    pdl_enter();
     const BatchInst &I = b.inst[blockIdx.y];
     R *U = reinterpret_cast<R *>(const_cast<void *>(b.in)) + I.off;
     R *S = reinterpret_cast<R *>(b.out) + I.off;
@@ -165,10 +167,14 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS) k_batch_cfl(
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_batch_finalize(BatchArgs b)
 {
+    pdl_enter();
     __shared__ double sred[4 * 32];
     const BatchInst &I = b.inst[blockIdx.x];
     finalize_block<THREADS>(I.ctl, b.partials + 4 * I.part0, 0, 0, b.final_mode, 2, I.g.dx[0], I.g.dx[1],
                             I.g.dx[2], sred);
+    // the stages of this step are complete: reset the dynamic-schedule counters
+    if (blockIdx.x == 0 && threadIdx.x == 0 && b.queue)
+        for (int k = 1; k <= 3; k++) b.queue[k] = 0u;
 }
 
 static __global__ void k_batch_init_ctl(Ctl *ctl, int count, const double *v_body /* 3 per instance */)
@@ -217,10 +223,10 @@ struct BK {
     static void seed(int opt, int grid, const BatchArgs &a, cudaStream_t st)
     {
         switch (opt) {
-        case 0: k_batch_seed<R, NMAT, MODE, 0><<<dim3(32, grid), 256, 0, st>>>(a); break;
-        case 1: k_batch_seed<R, NMAT, MODE, 1><<<dim3(32, grid), 256, 0, st>>>(a); break;
-        case 2: k_batch_seed<R, NMAT, MODE, 2><<<dim3(32, grid), 256, 0, st>>>(a); break;
-        default: k_batch_seed<R, NMAT, MODE, 3><<<dim3(32, grid), 256, 0, st>>>(a); break;
+        case 0: launch_pdl(k_batch_seed<R, NMAT, MODE, 0>, dim3(32, grid), dim3(256), 0, st, a); break;
+        case 1: launch_pdl(k_batch_seed<R, NMAT, MODE, 1>, dim3(32, grid), dim3(256), 0, st, a); break;
+        case 2: launch_pdl(k_batch_seed<R, NMAT, MODE, 2>, dim3(32, grid), dim3(256), 0, st, a); break;
+        default: launch_pdl(k_batch_seed<R, NMAT, MODE, 3>, dim3(32, grid), dim3(256), 0, st, a); break;
         }
     }
     // phase: 0 seed in place, 1..3 stages, 4 CFL, 5 / 6 seed to scratch / apply,
@@ -231,11 +237,11 @@ struct BK {
         switch (phase) {
         case 0: seed<0>(opt, grid, a, st); break;
         case 5: seed<1>(opt, grid, a, st); break;
-        case 6: k_batch_seed<R, NMAT, 2, 0><<<dim3(32, grid), 256, 0, st>>>(a); break;
-        case 7: k_batch_finalize<32><<<grid, 32, 0, st>>>(a); break;
-        case 1: k_batch_stage<R, NMAT, 1><<<grid, threads, smem, st>>>(a); break;
-        case 2: k_batch_stage<R, NMAT, 2><<<grid, threads, smem, st>>>(a); break;
-        case 3: k_batch_stage<R, NMAT, 3><<<grid, threads, smem, st>>>(a); break;
+        case 6: launch_pdl(k_batch_seed<R, NMAT, 2, 0>, dim3(32, grid), dim3(256), 0, st, a); break;
+        case 7: launch_pdl(k_batch_finalize<32>, dim3(grid), dim3(32), 0, st, a); break;
+        case 1: launch_pdl(k_batch_stage<R, NMAT, 1>, dim3(grid), dim3(threads), smem, st, a); break;
+        case 2: launch_pdl(k_batch_stage<R, NMAT, 2>, dim3(grid), dim3(threads), smem, st, a); break;
+        case 3: launch_pdl(k_batch_stage<R, NMAT, 3>, dim3(grid), dim3(threads), smem, st, a); break;
         default: k_batch_cfl<R, NMAT><<<grid, threads, 0, st>>>(a); break;
         }
         return cudaGetLastError();

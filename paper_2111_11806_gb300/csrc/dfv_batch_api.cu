@@ -175,18 +175,18 @@ int grid_size(dfv_batch *b)
     return (int)std::max(1LL, std::min(persistent, b->plan.nitems));
 }
 
-// one launch of a phase, with the dynamic-queue reset when that schedule is
-// used.  Seeding (phase 0) and the CFL reduction (phase 4) do little work per
-// item, so they always run one CTA per item and let the hardware overlap the
-// items' memory latency.
+// one launch of a phase.  The dynamic schedule's counters (slots 1-3, one
+// per stage) start at 0 and the finalize phase puts them back to 0 at the end
+// of every step, so no memset sits between the step's kernels.  Seeding
+// (phase 0) and the CFL reduction (phase 4) do little work per item, so they
+// always run one CTA per item and let the hardware overlap the items' memory
+// latency.
 dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out, int final_mode, int slot)
 {
     BatchArgs a = args(b, in, un, out, final_mode);
     const bool light = (ph == 0 || ph == 4 || ph == 5 || ph == 6 || ph == 7);
-    if (b->schedule == 2 && !light) {
-        a.queue = b->d_queue + slot;
-        B_CU(b, cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), b->stream), "queue reset");
-    }
+    if (b->schedule == 2 && !light) a.queue = b->d_queue + slot;
+    if (ph == 7) a.queue = b->d_queue;
     // seeding: one row of blocks per instance; CFL: one CTA per item
     const bool seeding = (ph == 0 || ph == 5 || ph == 6 || ph == 7);   // one block (row) per instance
     const int grid = seeding ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
@@ -317,6 +317,10 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     b->d_ctl_bak = (Ctl *)(b->ws + P.off_ctlbak);
     b->d_part = (double *)(b->ws + P.off_part);
     b->d_queue = (unsigned int *)(b->ws + P.off_queue);
+    if (cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int) * 8, b->stream) != cudaSuccess) {
+        delete b;
+        return DFV_ERR_CUDA;
+    }
     b->d_vbody = (double *)(b->ws + P.off_vbody);
     b->U = b->ws + P.off_U;
     b->U1 = b->ws + P.off_U1;

@@ -186,6 +186,36 @@ __device__ __forceinline__ void ctl_sync_v(Ctl *c)
 
 enum { ERR_STATE = 1u, ERR_SOUND = 2u };
 
+// Programmatic dependent launch: the kernels of a step are launched with
+// launch_pdl, so a kernel's CTAs may be scheduled while the previous kernel
+// on the stream is still finishing.  Each such kernel first waits for its
+// predecessor to complete with its memory visible (griddepcontrol.wait; a
+// no-op without a programmatic predecessor), then lets its own successor be
+// scheduled (griddepcontrol.launch_dependents): the successor's CTAs take SM
+// slots only after every CTA of this grid has started, and they wait in turn.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+__host__ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                       cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------------------ layout
 
 template <int DIM, int NMAT, bool SOLID>

@@ -37,8 +37,7 @@ struct Impl {
     template <int S>
     static cudaError_t stage_s(const GridP &g, const StageArgs &a, cudaStream_t st)
     {
-        k_stage<R, DIM, NMAT, SOLID, S><<<stage_grid(g), TL::THREADS, smem, st>>>(a, g);
-        return cudaGetLastError();
+        return launch_pdl(k_stage<R, DIM, NMAT, SOLID, S>, stage_grid(g), dim3(TL::THREADS), smem, st, a, g);
     }
 
     static cudaError_t stage(int s, const GridP &g, const void *in, const void *un, void *out, Ctl *ctl,
@@ -60,14 +59,14 @@ struct Impl {
     static cudaError_t seed_opt_k(const GridP &g, void *U, void *scratch, const Ctl *ctl, cudaStream_t st)
     {
         if (g.probe_mode == 1) {
-            k_seed<R, DIM, NMAT, SOLID, OPT, 1><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g);
-            cudaError_t e = cudaGetLastError();
+            cudaError_t e = launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 1>, dim3(gs_blocks(g.ncell)), dim3(256), 0,
+                                       st, U, scratch, ctl, g);
             if (e != cudaSuccess) return e;
-            k_seed<R, DIM, NMAT, SOLID, 0, 2><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g);
-        } else {
-            k_seed<R, DIM, NMAT, SOLID, OPT, 0><<<gs_blocks(g.ncell), 256, 0, st>>>(U, scratch, ctl, g);
+            return launch_pdl(k_seed<R, DIM, NMAT, SOLID, 0, 2>, dim3(gs_blocks(g.ncell)), dim3(256), 0, st, U,
+                              scratch, ctl, g);
         }
-        return cudaGetLastError();
+        return launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 0>, dim3(gs_blocks(g.ncell)), dim3(256), 0, st, U, scratch,
+                          ctl, g);
     }
 
     // seeding; scratch: planes of the grid's layout free until stage 1

@@ -169,6 +169,13 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
                                                int mode, int dim, double dx0, double dx1, double dx2,
                                                double *sred)
 {
+    // the control block is read once, word by word in parallel, so that the
+    // serial update below works on a shared copy instead of a chain of
+    // dependent global loads
+    __shared__ Ctl sc;
+    constexpr int NWORD = (int)(sizeof(Ctl) / sizeof(unsigned long long));
+    for (int k = threadIdx.x; k < NWORD; k += THREADS)
+        reinterpret_cast<unsigned long long *>(&sc)[k] = reinterpret_cast<const unsigned long long *>(ctl)[k];
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     // tiles of a stage-3 launch fold their maximum into ctl->smax_acc instead
     // of a partial (nb_cfl = 0 then): read it and leave it at 0
@@ -185,29 +192,34 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
     } else {
         red[0] = block_max<THREADS, double>(red[0], sred);
     }
+    __syncthreads();     // the shared copy is complete
     if (threadIdx.x != 0) return;
     const double dxs[3] = {dx0, dx1, dx2};
     if (mode & 2)
-        for (int d = 0; d < 3; d++) ctl->force[d] = red[1 + d];
+        for (int d = 0; d < 3; d++) sc.force[d] = ctl->force[d] = red[1 + d];
     if (mode & 4) {
-        if (ctl->dynamic && ctl->mass > 0.0) {
+        if (sc.dynamic && sc.mass > 0.0) {
             for (int d = 0; d < 3; d++) {
-                ctl->v[d] += ctl->dt * ctl->force[d] / ctl->mass;
-                ctl->x[d] += ctl->dt * ctl->v[d];
+                sc.v[d] += sc.dt * sc.force[d] / sc.mass;
+                sc.x[d] += sc.dt * sc.v[d];
+                ctl->v[d] = sc.v[d];
+                ctl->x[d] = sc.x[d];
+                ctl->vf[d] = (float)sc.v[d];
             }
-            ctl_sync_v(ctl);
         }
-        ctl->t += ctl->dt;
-        ctl->steps += 1;
+        ctl->t = sc.t + sc.dt;
+        ctl->steps = sc.steps + 1;
+        sc.t += sc.dt;
     }
     if (mode & 1) {
         double sb = 0.0;
-        for (int d = 0; d < dim; d++) sb += fabs(ctl->v[d]) / dxs[d];
-        ctl->smax = fmax(red[0], sb);
+        for (int d = 0; d < dim; d++) sb += fabs(sc.v[d]) / dxs[d];
+        sc.smax = fmax(red[0], sb);
+        ctl->smax = sc.smax;
     }
     if (mode & 8) {
-        double dt = ctl->cfl / ctl->smax;
-        if (ctl->t_end > 0.0) dt = fmin(dt, fmax(ctl->t_end - ctl->t, 0.0));
+        double dt = sc.cfl / sc.smax;
+        if (sc.t_end > 0.0) dt = fmin(dt, fmax(sc.t_end - sc.t, 0.0));
         if (!(dt == dt)) dt = 0.0;
         ctl_set_dt(ctl, dt);
     }
@@ -217,6 +229,7 @@ static __global__ void __launch_bounds__(1024) k_finalize(Ctl *ctl, const double
                                                    long long nb_force, int mode, int dim, double dx0, double dx1,
                                                    double dx2)
 {
+    pdl_enter();
     __shared__ double sred[4 * 32];
     finalize_block<1024>(ctl, partials, nb_cfl, nb_force, mode, dim, dx0, dx1, dx2, sred);
 }
@@ -605,6 +618,7 @@ __device__ __forceinline__ void seed_apply(R *U, const R *S, const GridP &g, lon
 template <class R, int DIM, int NMAT, bool SOLID, int OPT, int MODE>
 __global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl, GridP g)
 {
+    pdl_enter();
     R *U = reinterpret_cast<R *>(Uv);
     R *S = reinterpret_cast<R *>(Sv);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
@@ -882,6 +896,7 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
 template <class R, int DIM, int NMAT, bool SOLID, int STAGE>
 __global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(StageArgs a, GridP g)
 {
+    pdl_enter();
     const long long tile = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     const long long nt = (long long)gridDim.x * gridDim.y * gridDim.z;
     stage_tile<R, DIM, NMAT, SOLID, STAGE>(g, a, blockIdx.x, blockIdx.y, blockIdx.z, tile, nt);
