@@ -40,6 +40,7 @@ struct dfv_grid {
     long long launches = 0;
     cudaGraphExec_t graph = nullptr;
     bool graph_ready = false;
+    long long graph_launches = 0;   // kernels in one replay of the step graph
     bool dt_valid = false;               // ctl->dt holds the device-computed next dt
     double run_cfl = -1.0, run_tend = -1.0;
     bool prof = false;                   // per-kernel event timing (dfv_profile)
@@ -507,7 +508,7 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
         if (s != DFV_OK) return s;
         g->dt_valid = true;
     }
-    const bool use_graph = g->stream != nullptr && steps > 1 && !g->prof;
+    const bool use_graph = g->stream != nullptr && steps > 0 && !g->prof;
     if (use_graph && !g->graph_ready) {
         if (g->graph) {
             cudaGraphExecDestroy(g->graph);
@@ -518,6 +519,7 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
         const long long before = g->launches;
         dfv_status cs = launch_step(g, 8, true);
         cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+        g->graph_launches = g->launches - before;   // kernels of one replay
         g->launches = before;   // capture launches nothing
         if (cs != DFV_OK) return cs;
         if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
@@ -529,7 +531,7 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
     for (int k = 0; k < steps; k++) {
         if (use_graph) {
             DFV_CU(g, cudaGraphLaunch(g->graph, g->stream), "graph launch");
-            g->launches += 4;
+            g->launches += g->graph_launches;
         } else {
             s = launch_step(g, 8);
             if (s != DFV_OK) return s;

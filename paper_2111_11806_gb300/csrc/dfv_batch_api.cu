@@ -117,6 +117,7 @@ struct dfv_batch {
     double run_cfl = -1.0, run_tend = -1.0;
     cudaGraphExec_t graph = nullptr;
     bool graph_ready = false;
+    long long graph_launches = 0;   // kernels in one replay of the step graph
     bool prof = false;
     std::vector<std::array<cudaEvent_t, 5>> ev_steps;
     std::vector<cudaEvent_t> ev_free;
@@ -478,7 +479,7 @@ dfv_status dfv_batch_run(dfv_batch *b, int steps, double cfl, double t_end)
     dfv_status s = upload(b);
     if (s != DFV_OK) return s;
     if ((s = ensure_dt(b, cfl, t_end)) != DFV_OK) return s;
-    const bool use_graph = b->stream != nullptr && steps > 1 && !b->prof;
+    const bool use_graph = b->stream != nullptr && steps > 0 && !b->prof;
     if (use_graph && !b->graph_ready) {
         if (b->graph) {
             cudaGraphExecDestroy(b->graph);
@@ -489,6 +490,7 @@ dfv_status dfv_batch_run(dfv_batch *b, int steps, double cfl, double t_end)
         const long long before = b->launches;
         dfv_status cs = batch_step(b, true);
         cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        b->graph_launches = b->launches - before;   // kernels of one replay
         b->launches = before;
         if (cs != DFV_OK) return cs;
         if (e != cudaSuccess) return bfail(b, DFV_ERR_CUDA, "dfv_batch_run: end capture failed");
@@ -500,7 +502,7 @@ dfv_status dfv_batch_run(dfv_batch *b, int steps, double cfl, double t_end)
     for (int k = 0; k < steps; k++) {
         if (use_graph) {
             B_CU(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
-            b->launches += 4;
+            b->launches += b->graph_launches;
         } else if ((s = batch_step(b, false)) != DFV_OK) {
             return s;
         }
