@@ -188,9 +188,8 @@ dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out
     const bool light = (ph == 0 || ph == 4 || ph == 5 || ph == 6 || ph == 7);
     if (b->schedule == 2 && !light) a.queue = b->d_queue + slot;
     if (ph == 7) a.queue = b->d_queue;
-    // seeding: one row of blocks per instance; CFL: one CTA per item
-    const bool seeding = (ph == 0 || ph == 5 || ph == 6 || ph == 7);   // one block (row) per instance
-    const int grid = seeding ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
+    // seeding and CFL: one CTA per work item; finalize: one per instance
+    const int grid = ph == 7 ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
     B_CU(b, b->kern.launch(ph, grid, a, b->seed_opt, b->stream), "batch kernel");
     b->launches++;
     return DFV_OK;

@@ -58,15 +58,14 @@ struct Impl {
     template <int OPT>
     static cudaError_t seed_opt_k(const GridP &g, void *U, void *scratch, const Ctl *ctl, cudaStream_t st)
     {
+        dim3 block, grid;
+        seed_grid(g, block, grid);
         if (g.probe_mode == 1) {
-            cudaError_t e = launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 1>, dim3(gs_blocks(g.ncell)), dim3(256), 0,
-                                       st, U, scratch, ctl, g);
+            cudaError_t e = launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 1>, grid, block, 0, st, U, scratch, ctl, g);
             if (e != cudaSuccess) return e;
-            return launch_pdl(k_seed<R, DIM, NMAT, SOLID, 0, 2>, dim3(gs_blocks(g.ncell)), dim3(256), 0, st, U,
-                              scratch, ctl, g);
+            return launch_pdl(k_seed<R, DIM, NMAT, SOLID, 0, 2>, grid, block, 0, st, U, scratch, ctl, g);
         }
-        return launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 0>, dim3(gs_blocks(g.ncell)), dim3(256), 0, st, U, scratch,
-                          ctl, g);
+        return launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 0>, grid, block, 0, st, U, scratch, ctl, g);
     }
 
     // seeding; scratch: planes of the grid's layout free until stage 1

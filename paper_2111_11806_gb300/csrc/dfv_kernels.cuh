@@ -405,19 +405,17 @@ __device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R
 // OPT: bit 0 ELVIRA normals (2-D), bit 1 Riemann-problem variant; each option
 // set is its own kernel so that the plain seeding keeps its small footprint.
 template <class R, int DIM, int NMAT, bool SOLID, int OPT>
-__device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const GridP &g, long long c, R *q)
+__device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const GridP &g, const int ijk[3], long long c,
+                                             R *q)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     const GridC<R> &gc = gridc<R>(g);
     const long long P = g.pitch;
     {
-        const R rc = U[L::IR * P + c];
-        if (!(rc > R(0.5))) return false;
-        int ijk[3];
-        ijk[0] = (int)(c % g.n[0]);
-        ijk[1] = (int)((c / g.n[0]) % g.n[1]);
-        ijk[2] = (int)(c / ((long long)g.n[0] * g.n[1]));
-        R gr[3] = {R(0), R(0), R(0)};
+        // r of the cell and of its 2 DIM neighbours in one round of loads
+        // (most cells leave at the first test, but a band cell then needs no
+        // second round trip for its gradient)
+        R rn[3][2];
 #pragma unroll
         for (int d = 0; d < DIM; d++) {
             int lo[3] = {ijk[0], ijk[1], ijk[2]}, hi[3] = {ijk[0], ijk[1], ijk[2]};
@@ -425,8 +423,14 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
             hi[d] = map_idx(ijk[d] + 1, g.n[d], g.periodic[d]);
             const long long cl = lo[0] + (long long)g.n[0] * (lo[1] + (long long)g.n[1] * lo[2]);
             const long long ch = hi[0] + (long long)g.n[0] * (hi[1] + (long long)g.n[1] * hi[2]);
-            gr[d] = (U[L::IR * P + ch] - U[L::IR * P + cl]) / (R(2) * gc.dx[d]);
+            rn[d][0] = U[L::IR * P + cl];
+            rn[d][1] = U[L::IR * P + ch];
         }
+        const R rc = U[L::IR * P + c];
+        if (!(rc > R(0.5))) return false;
+        R gr[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int d = 0; d < DIM; d++) gr[d] = (rn[d][1] - rn[d][0]) / (R(2) * gc.dx[d]);
         const R gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
         if (!(gn * gc.dxmin > R(1e-10))) return false;
         R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
@@ -575,11 +579,11 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
 }
 
 template <class R, int DIM, int NMAT, bool SOLID, int OPT>
-__device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, long long c)
+__device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, const int ijk[3], long long c)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     R q[L::NVAR];
-    if (!seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, c, q)) return;
+    if (!seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c, q)) return;
 #pragma unroll
     for (int v = 0; v < L::NVAR; v++)
         if (v != L::IR) U[v * g.pitch + c] = q[v];
@@ -589,12 +593,13 @@ __device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, 
 // (fixed probe): the seeded state of cell c goes to the scratch planes S,
 // whose r plane flags it (1 seeded, 0 not); seed_apply then copies it into U.
 template <class R, int DIM, int NMAT, bool SOLID, int OPT>
-__device__ __forceinline__ void seed_cell_to(const R *U, R *S, const Ctl *ctl, const GridP &g, long long c)
+__device__ __forceinline__ void seed_cell_to(const R *U, R *S, const Ctl *ctl, const GridP &g, const int ijk[3],
+                                             long long c)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     if (!(U[L::IR * g.pitch + c] > R(0.5))) return;
     R q[L::NVAR];
-    const bool ok = seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, c, q);
+    const bool ok = seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c, q);
     if (ok) {
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++)
@@ -615,17 +620,33 @@ __device__ __forceinline__ void seed_apply(R *U, const R *S, const GridP &g, lon
 
 // MODE 0: in place (stepped probe: reads only r < 0.5 cells, writes only
 // r > 0.5 cells); 1: seeded states into the scratch S; 2: S into U.
+// One thread per cell, the cell index from the launch shape: 1-D blocks of
+// 256 cells along x in 1-D, 32 x 8 blocks over (x, y) and one z plane per
+// grid layer in 2-D and 3-D (seed_grid).
 template <class R, int DIM, int NMAT, bool SOLID, int OPT, int MODE>
 __global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl, GridP g)
 {
     pdl_enter();
     R *U = reinterpret_cast<R *>(Uv);
     R *S = reinterpret_cast<R *>(Sv);
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
-         c += (long long)gridDim.x * blockDim.x) {
-        if constexpr (MODE == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, c);
-        else if constexpr (MODE == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, c);
-        else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
+    const int ijk[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y),
+                        (int)blockIdx.z};
+    if (ijk[0] >= g.n[0] || ijk[1] >= g.n[1] || ijk[2] >= g.n[2]) return;
+    const long long c = ijk[0] + (long long)g.n[0] * (ijk[1] + (long long)g.n[1] * ijk[2]);
+    if constexpr (MODE == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c);
+    else if constexpr (MODE == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, ijk, c);
+    else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
+}
+
+// Launch shape of k_seed (block, grid) for a grid of g.n cells.
+__host__ inline void seed_grid(const GridP &g, dim3 &block, dim3 &grid)
+{
+    if (g.dim == 1) {
+        block = dim3(256, 1, 1);
+        grid = dim3((unsigned)((g.n[0] + 255) / 256), 1, 1);
+    } else {
+        block = dim3(32, 8, 1);
+        grid = dim3((unsigned)((g.n[0] + 31) / 32), (unsigned)((g.n[1] + 7) / 8), (unsigned)g.n[2]);
     }
 }
 
