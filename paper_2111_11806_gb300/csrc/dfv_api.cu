@@ -131,6 +131,7 @@ dfv_status cuda_fail(dfv_grid *g, cudaError_t e, const char *where)
 __global__ void k_init_ctl(Ctl *c)
 {
     memset(c, 0, sizeof(Ctl));
+    ctl_box_reset(c);
 }
 
 __global__ void k_set_body(Ctl *c, double v0, double v1, double v2, double x0, double x1, double x2, double mass,
@@ -394,6 +395,8 @@ dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device)
            "dfv_set_fields copy");
     DFV_CU(g, g->ops->prim_to_cons(g->g, g->staging, g->g.ncell, g->U, g->stream), "k_prim_to_cons");
     g->launches++;
+    // new r: the rigid box is unknown until the next stage 3
+    DFV_CU(g, cudaMemsetAsync(&g->ctl->rbox_valid, 0, sizeof(int), g->stream), "dfv_set_fields box");
     if (!on_device) DFV_CU(g, cudaStreamSynchronize(g->stream), "dfv_set_fields sync");
     g->fields_set = true;
     g->smax_valid = false;

@@ -80,27 +80,23 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_s
     }
 }
 
-// Rigid seeding of every instance: one CTA per (instance, tile) item of the
-// work list, one thread per cell of the tile (cell indices from the tile, no
-// division); the instance record is read through the cache.
+// Rigid seeding of every instance: SEED_CTAS CTAs of 256 threads per
+// instance stride over the cells of its rigid box (the whole grid until its
+// first stage 3); the instance record is read through the cache.
 // MODE 0: in place; 1: seeded states into the scratch planes b.out; 2: the
 // scratch into U (the fixed probe reads the step-start state only).
+constexpr int SEED_CTAS = 8;
+
 template <class R, int NMAT, int MODE, int OPT>
-__global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::TX * Tile<2, (int)sizeof(R)>::TY) k_batch_seed(BatchArgs b)
+__global__ void __launch_bounds__(256) k_batch_seed(BatchArgs b)
 {
     pdl_enter();
-    using TL = Tile<2, (int)sizeof(R)>;
-    const int2 w = b.items[blockIdx.x];
-    const BatchInst &I = b.inst[w.x];
+    const BatchInst &I = b.inst[blockIdx.x / SEED_CTAS];
     R *U = reinterpret_cast<R *>(const_cast<void *>(b.in)) + I.off;
     R *S = reinterpret_cast<R *>(b.out) + I.off;
-    const int ijk[3] = {(w.y % I.tiles_x) * TL::TX + (int)(threadIdx.x % TL::TX),
-                        (w.y / I.tiles_x) * TL::TY + (int)(threadIdx.x / TL::TX), 0};
-    if (ijk[0] >= I.g.n[0] || ijk[1] >= I.g.n[1]) return;
-    const long long c = ijk[0] + (long long)I.g.n[0] * ijk[1];
-    if (MODE == 0) seed_cell<R, 2, NMAT, false, OPT>(U, I.ctl, I.g, ijk, c);
-    else if (MODE == 1) seed_cell_to<R, 2, NMAT, false, OPT>(U, S, I.ctl, I.g, ijk, c);
-    else seed_apply<R, 2, NMAT, false>(U, S, I.g, c);
+    seed_box_cells<R, 2, NMAT, false, OPT, MODE>(U, S, I.ctl, I.g,
+                                                 (blockIdx.x % SEED_CTAS) * (long long)blockDim.x + threadIdx.x,
+                                                 (long long)SEED_CTAS * blockDim.x);
 }
 
 // CFL wave speed of every instance's stored state; the last tile of each
@@ -185,6 +181,7 @@ static __global__ void k_batch_init_ctl(Ctl *ctl, int count, const double *v_bod
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         Ctl *c = ctl + i;
         memset(c, 0, sizeof(Ctl));
+        ctl_box_reset(c);
         for (int d = 0; d < 3; d++) c->v[d] = v_body[3 * i + d];
         ctl_sync_v(c);
     }
@@ -202,7 +199,6 @@ static __global__ void k_batch_set_run(Ctl *ctl, int count, double cfl, double t
 template <class R, int NMAT>
 struct BK {
     static constexpr int threads = Tile<2, (int)sizeof(R)>::THREADS;
-    static constexpr int seed_threads = Tile<2, (int)sizeof(R)>::TX * Tile<2, (int)sizeof(R)>::TY;
     static constexpr size_t smem = StageSmem<R, 2, NMAT, false>::bytes;
     static cudaError_t prepare()
     {
@@ -227,10 +223,10 @@ struct BK {
     static void seed(int opt, int grid, const BatchArgs &a, cudaStream_t st)
     {
         switch (opt) {
-        case 0: launch_pdl(k_batch_seed<R, NMAT, MODE, 0>, dim3(grid), dim3(seed_threads), 0, st, a); break;
-        case 1: launch_pdl(k_batch_seed<R, NMAT, MODE, 1>, dim3(grid), dim3(seed_threads), 0, st, a); break;
-        case 2: launch_pdl(k_batch_seed<R, NMAT, MODE, 2>, dim3(grid), dim3(seed_threads), 0, st, a); break;
-        default: launch_pdl(k_batch_seed<R, NMAT, MODE, 3>, dim3(grid), dim3(seed_threads), 0, st, a); break;
+        case 0: launch_pdl(k_batch_seed<R, NMAT, MODE, 0>, dim3(grid * SEED_CTAS), dim3(256), 0, st, a); break;
+        case 1: launch_pdl(k_batch_seed<R, NMAT, MODE, 1>, dim3(grid * SEED_CTAS), dim3(256), 0, st, a); break;
+        case 2: launch_pdl(k_batch_seed<R, NMAT, MODE, 2>, dim3(grid * SEED_CTAS), dim3(256), 0, st, a); break;
+        default: launch_pdl(k_batch_seed<R, NMAT, MODE, 3>, dim3(grid * SEED_CTAS), dim3(256), 0, st, a); break;
         }
     }
     // phase: 0 seed in place, 1..3 stages, 4 CFL, 5 / 6 seed to scratch / apply,
@@ -241,7 +237,7 @@ struct BK {
         switch (phase) {
         case 0: seed<0>(opt, grid, a, st); break;
         case 5: seed<1>(opt, grid, a, st); break;
-        case 6: launch_pdl(k_batch_seed<R, NMAT, 2, 0>, dim3(grid), dim3(seed_threads), 0, st, a); break;
+        case 6: launch_pdl(k_batch_seed<R, NMAT, 2, 0>, dim3(grid * SEED_CTAS), dim3(256), 0, st, a); break;
         case 7: launch_pdl(k_batch_finalize<32>, dim3(grid), dim3(32), 0, st, a); break;
         case 1: launch_pdl(k_batch_stage<R, NMAT, 1>, dim3(grid), dim3(threads), smem, st, a); break;
         case 2: launch_pdl(k_batch_stage<R, NMAT, 2>, dim3(grid), dim3(threads), smem, st, a); break;

@@ -188,8 +188,10 @@ dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out
     const bool light = (ph == 0 || ph == 4 || ph == 5 || ph == 6 || ph == 7);
     if (b->schedule == 2 && !light) a.queue = b->d_queue + slot;
     if (ph == 7) a.queue = b->d_queue;
-    // seeding and CFL: one CTA per work item; finalize: one per instance
-    const int grid = ph == 7 ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
+    // seeding: SEED_CTAS per instance (the launcher multiplies); finalize: one
+    // per instance; CFL: one CTA per work item
+    const bool per_inst = (ph == 0 || ph == 5 || ph == 6 || ph == 7);
+    const int grid = per_inst ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
     B_CU(b, b->kern.launch(ph, grid, a, b->seed_opt, b->stream), "batch kernel");
     b->launches++;
     return DFV_OK;
@@ -441,6 +443,8 @@ dfv_status dfv_batch_set_fields(dfv_batch *b, int i, const double *prim, int on_
     B_CU(b, b->ops->prim_to_cons(g, b->staging, g.ncell, (char *)b->U + (size_t)w * b->hinst[i].off, b->stream),
          "prim_to_cons");
     b->launches++;
+    // new r: the instance's rigid box is unknown until its next stage 3
+    B_CU(b, cudaMemsetAsync(&b->d_ctl[i].rbox_valid, 0, sizeof(int), b->stream), "set_fields box");
     if (!on_device) B_CU(b, cudaStreamSynchronize(b->stream), "set_fields sync");
     b->fields_set[i] = 1;
     b->dt_valid = false;

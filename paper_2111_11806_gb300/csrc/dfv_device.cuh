@@ -158,7 +158,19 @@ struct Ctl {
     int steps;
     unsigned int ticket;      // blocks of the last stage that have written their partials
     float dtf, vf[3];         // dt and v in single precision, kept equal to (float)dt, (float)v
+    int rbox_valid;           // 1: rbox bounds every cell with r > 0.5 of the stored state
+    int rbox[6];              // inclusive cell-index box lo x, y, z, hi x, y, z (empty: lo > hi)
+    int rnext[6];             // the same for the state stage 3 produces (atomic min / max)
 };
+
+// Empty box for rnext, and a fresh control block's fields that are not 0.
+__host__ __device__ inline void ctl_box_reset(Ctl *c)
+{
+    for (int d = 0; d < 3; d++) {
+        c->rnext[d] = 0x7fffffff;
+        c->rnext[3 + d] = -1;
+    }
+}
 
 // dt and body velocity in the compute precision
 template <class T>

@@ -210,6 +210,10 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
         ctl->t = sc.t + sc.dt;
         ctl->steps = sc.steps + 1;
         sc.t += sc.dt;
+        // the rigid box of the state just produced becomes the seeding box
+        for (int k = 0; k < 6; k++) ctl->rbox[k] = sc.rnext[k];
+        ctl->rbox_valid = 1;
+        ctl_box_reset(ctl);
     }
     if (mode & 1) {
         double sb = 0.0;
@@ -620,34 +624,59 @@ __device__ __forceinline__ void seed_apply(R *U, const R *S, const GridP &g, lon
 
 // MODE 0: in place (stepped probe: reads only r < 0.5 cells, writes only
 // r > 0.5 cells); 1: seeded states into the scratch S; 2: S into U.
-// One thread per cell, the cell index from the launch shape: 1-D blocks of
-// 256 cells along x in 1-D, 32 x 8 blocks over (x, y) and one z plane per
-// grid layer in 2-D and 3-D (seed_grid).
+// The cells to seed lie in the box of the stored state's rigid cells
+// (r > 0.5), which stage 3 of the previous step folded into the control block;
+// without one (fields just set) the whole grid.  seed_box returns false when
+// the box is empty.
+__device__ __forceinline__ bool seed_box(const Ctl *ctl, const GridP &g, int lo[3], int hi[3])
+{
+    const bool valid = ctl->rbox_valid != 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        lo[d] = 0;
+        hi[d] = g.n[d] - 1;
+        if (valid) {
+            lo[d] = max(lo[d], ctl->rbox[d]);
+            hi[d] = min(hi[d], ctl->rbox[3 + d]);
+        }
+    }
+    return lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2];
+}
+
+// Threads stride over the cells of the rigid box, x fastest.
+template <class R, int DIM, int NMAT, bool SOLID, int OPT, int MODE>
+__device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const GridP &g, long long first,
+                                               long long stride)
+{
+    int lo[3], hi[3];
+    if (!seed_box(ctl, g, lo, hi)) return;
+    const long long w = hi[0] - lo[0] + 1, h = hi[1] - lo[1] + 1;
+    const long long total = w * h * (hi[2] - lo[2] + 1);
+    for (long long t = first; t < total; t += stride) {
+        const long long row = t / w;
+        const int ijk[3] = {lo[0] + (int)(t - row * w), lo[1] + (int)(row % h), lo[2] + (int)(row / h)};
+        const long long c = ijk[0] + (long long)g.n[0] * (ijk[1] + (long long)g.n[1] * ijk[2]);
+        if constexpr (MODE == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c);
+        else if constexpr (MODE == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, ijk, c);
+        else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
+    }
+}
+
 template <class R, int DIM, int NMAT, bool SOLID, int OPT, int MODE>
 __global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl, GridP g)
 {
     pdl_enter();
-    R *U = reinterpret_cast<R *>(Uv);
-    R *S = reinterpret_cast<R *>(Sv);
-    const int ijk[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y),
-                        (int)blockIdx.z};
-    if (ijk[0] >= g.n[0] || ijk[1] >= g.n[1] || ijk[2] >= g.n[2]) return;
-    const long long c = ijk[0] + (long long)g.n[0] * (ijk[1] + (long long)g.n[1] * ijk[2]);
-    if constexpr (MODE == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c);
-    else if constexpr (MODE == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, ijk, c);
-    else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
+    seed_box_cells<R, DIM, NMAT, SOLID, OPT, MODE>(reinterpret_cast<R *>(Uv), reinterpret_cast<R *>(Sv), ctl, g,
+                                                   blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                                                   (long long)gridDim.x * blockDim.x);
 }
 
-// Launch shape of k_seed (block, grid) for a grid of g.n cells.
+// Launch shape of k_seed: up to 4 CTAs of 256 threads per SM.
 __host__ inline void seed_grid(const GridP &g, dim3 &block, dim3 &grid)
 {
-    if (g.dim == 1) {
-        block = dim3(256, 1, 1);
-        grid = dim3((unsigned)((g.n[0] + 255) / 256), 1, 1);
-    } else {
-        block = dim3(32, 8, 1);
-        grid = dim3((unsigned)((g.n[0] + 31) / 32), (unsigned)((g.n[1] + 7) / 8), (unsigned)g.n[2]);
-    }
+    const long long b = (g.ncell + 255) / 256;
+    block = dim3(256, 1, 1);
+    grid = dim3((unsigned)(b < 1 ? 1 : (b > 152LL * 4 ? 152LL * 4 : b)), 1, 1);
 }
 
 // The option set of a grid as the OPT template argument of the seeding.
@@ -833,6 +862,7 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
 
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     R smax_cell = R(0);
+    bool rigid_new = false;
     if (inside) {
         const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
         const int bcell = ((lz + B::HZ) * B::BY + (ly + B::HY)) * B::BX + (lx + B::HX);
@@ -876,6 +906,7 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
                 red[1 + d] = (double)(p * gr * gc.dV);
             }
         }
+        if (STAGE == 3) rigid_new = o[L::IR] > R(0.5);
         if (STAGE == 3) {
             // CFL wave speed of the new state, in the compute precision
             R w[L::NVAR];
@@ -891,6 +922,26 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
         }
     }
     if (STAGE == 3) {
+        // box of the new state's rigid cells for the next seeding: warp
+        // minima / maxima, one atomic set per warp that holds a rigid cell
+        if (__any_sync(0xffffffffu, rigid_new)) {
+            const int big = 0x7fffffff;
+            const int b[6] = {rigid_new ? gx : big, rigid_new ? gy : big, rigid_new ? gz : big,
+                              rigid_new ? gx : -1, rigid_new ? gy : -1, rigid_new ? gz : -1};
+            int m[6];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                m[k] = __reduce_min_sync(0xffffffffu, b[k]);
+                m[3 + k] = __reduce_max_sync(0xffffffffu, b[3 + k]);
+            }
+            if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    atomicMin(&a.ctl->rnext[k], m[k]);
+                    atomicMax(&a.ctl->rnext[3 + k], m[3 + k]);
+                }
+            }
+        }
         // block maximum in the compute precision (the per-cell values are R),
         // folded into the launch's running maximum: the bits of non-negative
         // doubles order like the doubles, so an integer atomic max is exact

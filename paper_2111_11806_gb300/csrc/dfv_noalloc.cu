@@ -53,6 +53,7 @@ cudaError_t scratch_for_current_device(double **out)
 __global__ void k_noalloc_init_ctl(dfv::Ctl *c, double v0, double v1, double v2)
 {
     memset(c, 0, sizeof(dfv::Ctl));
+    dfv::ctl_box_reset(c);
     c->v[0] = v0;
     c->v[1] = v1;
     c->v[2] = v2;
