@@ -103,8 +103,9 @@ class Oracle:
         lo3 = _arr(lo, 3)
         hi3 = _arr(hi, 3)
         per = np.array(list(periodic or [0] * dim) + [0] * (3 - dim), dtype=np.int32)
+        # solid: False / True, or 2 for a solid with plastic-strain history planes
         self._h = L.o_create(dim, n3.ctypes.data_as(_ip), _p(lo3), _p(hi3), per.ctypes.data_as(_ip),
-                             len(materials), int(bool(solid)))
+                             len(materials), 2 if solid == 2 else int(bool(solid)))
         self.nmat = len(materials)
         self.solid = bool(solid)
         for l, m in enumerate(materials):
@@ -115,7 +116,8 @@ class Oracle:
     @classmethod
     def from_workload(cls, wl, use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0, normal_method=0,
                       probe_mode=0):
-        o = cls(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, wl.solid, wl.periodic)
+        solid = 2 if (wl.solid and getattr(wl, "history", False)) else wl.solid
+        o = cls(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, solid, wl.periodic)
         o.set_options(use_thinc, thinc_beta)
         o.set_variants(hllc_lm, seed_variant, normal_method, probe_mode)
         o.set_walls(getattr(wl, "walls", (0,) * 6))

@@ -52,7 +52,8 @@ typedef struct {
     double lo[3], dx[3];
     int periodic[3];
     int nmat, solid, nv, nvar;
-    int iphi, iar, imom, iE, iV, ir;            /* plane offsets */
+    int hist;                                   /* 1: equivalent plastic strain of every material */
+    int iphi, iar, imom, iE, iV, ir, ih;        /* plane offsets (ih: history planes after r) */
     int vmap[9][2];                             /* stored V components -> (a,b) */
     omat mat[2];
     long ncell;
@@ -297,6 +298,7 @@ typedef struct {
     double phi[2], rhol[2], ar[2];
     double rho, u[3], p, rhoE, c2, G, sigY;
     double devH[3][3], A[3][3], J2;
+    double eps[2];      /* equivalent plastic strain of each material (history planes) */
 } othermo;
 
 /* Mixture closure from primitives (Sec. 2.2): rho = sum phi_l rho_l,
@@ -324,6 +326,7 @@ static void thermo_from_prim(const ostate *s, const double *w, othermo *t)
     }
     for (int a = 0; a < 3; a++) t->u[a] = (a < s->dim) ? w[s->imom + a] : 0.0;
     t->p = w[s->iE];
+    for (int l = 0; l < N; l++) t->eps[l] = s->hist ? w[s->ih + l] : 0.0;
     mat_zero(t->devH);
     mat_zero(t->A);
     t->J2 = 0.0;
@@ -426,6 +429,10 @@ static void cons_to_prim(const ostate *s, const double *q, double *w)
     w[s->iE] = num / den;
     for (int c = 0; c < s->nv; c++) w[s->iV + c] = q[s->iV + c];
     w[s->ir] = q[s->ir];
+    /* history: the specific value eps_l = (phi rho eps)_l / (phi rho)_l, 0 where
+     * the material has no mass */
+    if (s->hist)
+        for (int l = 0; l < N; l++) w[s->ih + l] = ar[l] != 0.0 ? q[s->ih + l] / ar[l] : 0.0;
 }
 
 static void prim_to_cons(const ostate *s, const double *w, double *q)
@@ -439,6 +446,8 @@ static void prim_to_cons(const ostate *s, const double *w, double *q)
     q[s->iE] = t.rhoE;
     for (int c = 0; c < s->nv; c++) q[s->iV + c] = w[s->iV + c];
     q[s->ir] = w[s->ir];
+    if (s->hist)
+        for (int l = 0; l < N; l++) q[s->ih + l] = t.ar[l] * t.eps[l];
 }
 
 /* ------------------------------------------------------ reconstruction */
@@ -519,6 +528,11 @@ static void face_state(const ostate *s, int d, const double *w, oface *f)
     }
     f->U[s->iE] = t->rhoE;
     f->F[s->iE] = t->rhoE * t->u[d] - work;
+    if (s->hist)
+        for (int l = 0; l < N; l++) {
+            f->U[s->ih + l] = t->ar[l] * t->eps[l];
+            f->F[s->ih + l] = t->ar[l] * t->eps[l] * t->u[d];
+        }
 }
 
 /* HLLC flux at a face in direction d (Sec. 3.1: Toro's HLLC for the
@@ -561,7 +575,12 @@ void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *
     else region = 3;
     K = (region <= 1) ? &L : &R;
     SK = (region <= 1) ? SL : SR;
-    int nthermo_lo = s->iar, nthermo_hi = s->iE; /* ar .. rhoE inclusive */
+    /* the conserved planes the HLLC waves carry: partial densities, momenta,
+     * energy, and the history planes */
+    int adv[OMAXV], nadv = 0;
+    for (int v = s->iar; v <= s->iE; v++) adv[nadv++] = v;
+    if (s->hist)
+        for (int l = 0; l < N; l++) adv[nadv++] = s->ih + l;
     /* tangential traction and velocity at the face: the linear shear-wave
      * Riemann problem, sigma -/+ Z u constant along the right/left shear
      * characteristics, Z = sqrt(rho G) [reading: the paper's HLLD resolves
@@ -600,7 +619,7 @@ void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *
             oface *Kk = side[k];
             double SKk = Sside[k], uKk = Kk->t.u[d];
             double chi = (SKk - uKk) / (SKk - Ss);
-            for (int v = nthermo_lo; v <= nthermo_hi; v++) Fa[k][v] = Kk->F[v];
+            for (int i = 0; i < nadv; i++) Fa[k][adv[i]] = Kk->F[adv[i]];
             double work_t = 0.0;
             for (int a = 0; a < 3; a++) {
                 if (a == d) continue;
@@ -613,23 +632,27 @@ void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *
             for (int a = 0; a < s->dim; a++) Us[k][s->imom + a] = Kk->t.rho * chi * (a == d ? Ss : Kk->t.u[a]);
             double EK = Kk->t.rhoE / Kk->t.rho;
             Us[k][s->iE] = Kk->t.rho * chi * (EK + (Ss - uKk) * (Ss + Kk->T / (Kk->t.rho * (SKk - uKk))));
+            if (s->hist)
+                for (int l = 0; l < N; l++) Us[k][s->ih + l] = Kk->t.ar[l] * Kk->t.eps[l] * chi;
         }
-        for (int v = nthermo_lo; v <= nthermo_hi; v++)
+        for (int i = 0; i < nadv; i++) {
+            const int v = adv[i];
             F[v] = 0.5 * (Fa[0][v] + Fa[1][v]) +
                    0.5 * (phi * SL * (Us[0][v] - L.U[v]) + fabs(Ss) * (Us[0][v] - Us[1][v]) +
                           phi * SR * (Us[1][v] - R.U[v]));
+        }
         for (int a = 0; a < s->dim; a++)
             if (a != d) F[s->imom + a] -= sig_t[a];
         F[s->iE] -= work_ts;
     } else if (region == 0 || region == 3) {
-        for (int v = nthermo_lo; v <= nthermo_hi; v++) F[v] = K->F[v];
+        for (int i = 0; i < nadv; i++) F[adv[i]] = K->F[adv[i]];
     } else {
         /* HLLC on the advective part with the normal traction; the
          * tangential traction enters through its star value */
         double uK = K->t.u[d];
         double chi = (SK - uK) / (SK - Ss);
         double Us[OMAXV], Fa[OMAXV];
-        for (int v = nthermo_lo; v <= nthermo_hi; v++) Fa[v] = K->F[v];
+        for (int i = 0; i < nadv; i++) Fa[adv[i]] = K->F[adv[i]];
         double work_t = 0.0, work_ts = 0.0;
         for (int a = 0; a < 3; a++) {
             if (a == d) continue;
@@ -643,7 +666,9 @@ void o_hllc(const ostate *s, int d, const double *wL, const double *wR, double *
         for (int a = 0; a < s->dim; a++) Us[s->imom + a] = K->t.rho * chi * (a == d ? Ss : K->t.u[a]);
         double EK = K->t.rhoE / K->t.rho;
         Us[s->iE] = K->t.rho * chi * (EK + (Ss - uK) * (Ss + K->T / (K->t.rho * (SK - uK))));
-        for (int v = nthermo_lo; v <= nthermo_hi; v++) F[v] = Fa[v] + SK * (Us[v] - K->U[v]);
+        if (s->hist)
+            for (int l = 0; l < N; l++) Us[s->ih + l] = K->t.ar[l] * K->t.eps[l] * chi;
+        for (int i = 0; i < nadv; i++) F[adv[i]] = Fa[adv[i]] + SK * (Us[adv[i]] - K->U[adv[i]]);
         for (int a = 0; a < s->dim; a++)
             if (a != d) F[s->imom + a] -= sig_t[a];
         F[s->iE] -= work_ts;
@@ -868,6 +893,8 @@ static void riemann_seed(const ostate *s, const double nrm[3], const double *wne
     q[s->iE] = rs * (ER + (Ss - unR) * (Ss + TnR / (tr.rho * (SR - unR))));
     for (int c = 0; c < s->nv; c++) q[s->iV + c] = wint[s->iV + c];
     q[s->ir] = wint[s->ir];
+    if (s->hist)
+        for (int l = 0; l < N; l++) q[s->ih + l] = tr.ar[l] * chi * tr.eps[l];
 }
 
 /* ------------------------------------------------ ELVIRA normal (2-D) */
@@ -1170,6 +1197,15 @@ static void plastic_cell(const ostate *s, double *q)
     nd = sqrt(nd);
     double svm = sqrt(1.5) * 2.0 * t.G * nd;
     double sc = (svm > t.sigY) ? t.sigY / svm : 1.0;
+    /* equivalent plastic strain [reading: Sec. 2.1.1 names the history
+     * variable without its evolution law]: the deviatoric log-strain removed
+     * by the return, (1 - s) |d|, as the von Mises equivalent
+     * sqrt(2/3) (1 - s) |d|, added to every material with a yield stress */
+    if (s->hist && sc < 1.0) {
+        double deps = sqrt(2.0 / 3.0) * (1.0 - sc) * nd;
+        for (int l = 0; l < s->nmat; l++)
+            if (s->mat[l].sigY > 0.0) q[s->ih + l] += t.ar[l] * deps;
+    }
     double Vn[3][3];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
@@ -1268,6 +1304,9 @@ void o_step(ostate *s, double dt)
 
 /* ---------------------------------------------------------------- API */
 
+/* solid: 0 fluids, 1 elastoplastic (stretch tensor planes), 2 elastoplastic
+ * with one equivalent-plastic-strain plane (phi rho eps)_l per material after
+ * r (Sec. 2.1.1 history variables). */
 void *o_create(int dim, const int n[3], const double lo[3], const double hi[3], const int periodic[3], int nmat, int solid)
 {
     ostate *s = (ostate *)calloc(1, sizeof(ostate));
@@ -1281,7 +1320,8 @@ void *o_create(int dim, const int n[3], const double lo[3], const double hi[3], 
         s->ncell *= s->n[d];
     }
     s->nmat = nmat;
-    s->solid = solid;
+    s->solid = solid != 0;
+    s->hist = solid == 2;
     s->nv = solid ? (dim == 1 ? 3 : dim == 2 ? 5 : 9) : 0;
     s->iphi = 0;
     s->iar = nmat - 1;
@@ -1289,7 +1329,8 @@ void *o_create(int dim, const int n[3], const double lo[3], const double hi[3], 
     s->iE = s->imom + dim;
     s->iV = s->iE + 1;
     s->ir = s->iV + s->nv;
-    s->nvar = s->ir + 1;
+    s->ih = s->ir + 1;
+    s->nvar = s->ih + (s->hist ? nmat : 0);
     if (dim == 1) {
         int m[3][2] = {{0, 0}, {1, 1}, {2, 2}};
         memcpy(s->vmap, m, sizeof(m));

@@ -58,6 +58,7 @@ class Workload:
     steps: int = 1
     t_end: Optional[float] = None
     walls: tuple = (0, 0, 0, 0, 0, 0)   # reflective wall on the low / high side of each direction
+    history: bool = False               # solids: one plastic-strain plane per material after r
 
     @property
     def nmat(self) -> int:
@@ -72,8 +73,9 @@ class Workload:
         return int(np.prod(self.n))
 
 
-def layout(dim: int, nmat: int, solid: bool) -> dict:
-    """Plane offsets of the primitive / conserved vectors."""
+def layout(dim: int, nmat: int, solid: bool, history: bool = False) -> dict:
+    """Plane offsets of the primitive / conserved vectors (history planes, one
+    per material, after r for solids with plastic-strain history)."""
     nv = (3 if dim == 1 else 5 if dim == 2 else 9) if solid else 0
     iphi = 0
     irho = nmat - 1
@@ -81,7 +83,8 @@ def layout(dim: int, nmat: int, solid: bool) -> dict:
     ip = iu + dim
     iv = ip + 1
     ir = iv + nv
-    return dict(nv=nv, iphi=iphi, irho=irho, iu=iu, ip=ip, iv=iv, ir=ir, nvar=ir + 1)
+    nh = nmat if (solid and history) else 0
+    return dict(nv=nv, iphi=iphi, irho=irho, iu=iu, ip=ip, iv=iv, ir=ir, ih=ir + 1, nh=nh, nvar=ir + 1 + nh)
 
 
 def cell_centres(n, lo, hi):
@@ -356,6 +359,18 @@ def random_state(dim, n, nmat, solid, seed, periodic=None, body=True, amp=0.1):
         w[L["ir"]] = rigid_profile(sd, dx)
     per = tuple(periodic) if periodic is not None else tuple(0 for _ in range(dim))
     return Workload("random_%dd" % dim, dim, n, lo, hi, per, mats, solid, w)
+
+
+def with_history(wl: Workload, seed: Optional[int] = None, amp: float = 0.0) -> Workload:
+    """The same workload carrying one equivalent-plastic-strain plane per
+    material after r: zero, or uniform random in [0, amp) with `seed`."""
+    assert wl.solid
+    extra = np.zeros((wl.nmat, wl.ncell))
+    if seed is not None and amp > 0.0:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        extra = amp * rng.random((wl.nmat, wl.ncell))
+    prim = np.concatenate([wl.prim, extra], axis=0)
+    return dataclasses.replace(wl, prim=prim, history=True, name=wl.name + "_history")
 
 
 def material_params(m: dict) -> tuple:
