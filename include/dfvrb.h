@@ -26,9 +26,11 @@
  *    one after another, each plane ncell = n0*n1*n2 doubles with x fastest
  *    (cell (i,j,k) at i + n0*(j + n1*k)).
  *    Primitive planes (N materials, d dimensions, nv stretch components):
- *        phi_1..phi_{N-1}, rho_1..rho_N, u_1..u_d, p, V_1..V_nv, r
+ *        phi_1..phi_{N-1}, rho_1..rho_N, u_1..u_d, p, V_1..V_nv, r [, eps_1..eps_N]
  *    Conserved planes, same count and order of groups:
  *        phi_1..phi_{N-1}, (phi rho)_1..(phi rho)_N, (rho u)_1..(rho u)_d, rho E, V_1..V_nv, r
+ *        [, (phi rho eps)_1..(phi rho eps)_N]
+ *    (the bracketed plastic-strain planes only with dfv_options.solid = 2)
  *    nv = 0 for fluids; for solids nv = 3 (1-D: xx,yy,zz) or 5 (2-D:
  *    xx,xy,yx,yy,zz).  With N = 1 there is no phi plane and the single
  *    density plane is rho.
@@ -90,7 +92,10 @@ typedef struct {
 
 typedef struct {
     int nmat;            /* number of materials, 1 or 2 */
-    int solid;           /* 1: carry the stretch tensor V (elastoplastic) */
+    int solid;           /* 1: carry the stretch tensor V (elastoplastic); 2: also one
+                            equivalent-plastic-strain plane (phi rho eps)_l per
+                            material after r (Sec. 2.1.1 history variables; the
+                            primitive plane is eps_l); 0: fluids */
     int use_thinc;       /* 1: MUSCL-BVD-THINC on phi and r (Sec. 3.1); 0: MUSCL only */
     double thinc_beta;   /* THINC steepness (1.6) */
     int hllc_lm;         /* 1: HLLC-LM flux (the low-Mach HLLC variant the paper

@@ -1204,7 +1204,7 @@ static void plastic_cell(const ostate *s, double *q)
     if (s->hist && sc < 1.0) {
         double deps = sqrt(2.0 / 3.0) * (1.0 - sc) * nd;
         for (int l = 0; l < s->nmat; l++)
-            if (s->mat[l].sigY > 0.0) q[s->ih + l] += t.ar[l] * deps;
+            if (s->mat[l].sigY > 0.0) q[s->ih + l] += q[s->iar + l] * deps;
     }
     double Vn[3][3];
     for (int i = 0; i < 3; i++)

@@ -142,7 +142,7 @@ def material_struct(m: dict) -> dfv_material_params:
 def workspace_bytes(dim, n, nmat, solid, precision) -> int:
     n3 = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
     out = ctypes.c_size_t()
-    _check(load().dfv_workspace_bytes(dim, n3, nmat, int(bool(solid)), precision, ctypes.byref(out)),
+    _check(load().dfv_workspace_bytes(dim, n3, nmat, 2 if solid == 2 else int(bool(solid)), precision, ctypes.byref(out)),
            what="dfv_workspace_bytes")
     return out.value
 
@@ -204,9 +204,11 @@ class Grid:
         self.n = tuple(int(x) for x in n)
         self.nmat = len(materials)
         self.solid = bool(solid)
+        self.history = solid == 2          # solid with plastic-strain planes
         self.precision = precision
         self.ncell = int(np.prod(self.n))
-        nbytes = workspace_bytes(dim, self.n, self.nmat, solid, precision)
+        skind = 2 if self.history else int(self.solid)
+        nbytes = workspace_bytes(dim, self.n, self.nmat, skind, precision)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
@@ -216,7 +218,7 @@ class Grid:
         n3 = (ctypes.c_int * 3)(*(list(self.n) + [1] * (3 - dim)))
         lo3 = _d3(lo)
         hi3 = _d3(hi)
-        opt = dfv_options(self.nmat, int(self.solid), int(bool(use_thinc)), float(thinc_beta), int(bool(hllc_lm)),
+        opt = dfv_options(self.nmat, skind, int(bool(use_thinc)), float(thinc_beta), int(bool(hllc_lm)),
                           int(seed_variant), int(normal_method), int(probe_mode))
         h = _vp()
         with torch.cuda.device(self.device):
@@ -230,11 +232,12 @@ class Grid:
             _check(L.dfv_add_material(self._h, MAT_KIND[m["kind"]], ctypes.byref(p), None), self._h,
                    "dfv_add_material")
         self.nvar = (self.nmat - 1) + self.nmat + dim + 1 + ((3 if dim == 1 else 5 if dim == 2 else 9)
-                                                            if solid else 0) + 1
+                                                            if solid else 0) + 1 + (self.nmat if self.history else 0)
 
     @classmethod
     def from_workload(cls, wl, precision=DFV_FP64, **kw):
-        g = cls(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, solid=wl.solid, precision=precision,
+        solid = 2 if (wl.solid and getattr(wl, "history", False)) else wl.solid
+        g = cls(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, solid=solid, precision=precision,
                 periodic=wl.periodic, walls=getattr(wl, "walls", None), **kw)
         g.set_fields(wl.prim)
         g.set_body(wl.body_v, wl.body_x, wl.body_mass, wl.body_dynamic)

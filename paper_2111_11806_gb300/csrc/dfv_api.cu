@@ -61,11 +61,14 @@ long long cells_of(int dim, const int n[3])
     return c;
 }
 
+// solid: 0 fluids, 1 stretch tensor, 2 stretch tensor and plastic-strain planes
 int nvar_of(int dim, int nmat, int solid)
 {
     const int nv = solid ? (dim == 1 ? 3 : (dim == 2 ? 5 : 9)) : 0;
-    return (nmat - 1) + nmat + dim + 1 + nv + 1;
+    return (nmat - 1) + nmat + dim + 1 + nv + 1 + (solid == 2 ? nmat : 0);
 }
+
+int solid_kind(int solid) { return solid == 2 ? 2 : (solid ? 1 : 0); }
 
 struct Layout {
     size_t off_ctl, off_part, off_U, off_U1, off_U3, off_stage, total;
@@ -262,7 +265,7 @@ dfv_status dfv_workspace_bytes(int dim, const int n[3], int nmat, int solid, int
     for (int d = 0; d < dim; d++)
         if (n[d] < 1) return DFV_ERR_ARG;
     int n3[3] = {n[0], dim >= 2 ? n[1] : 1, dim >= 3 ? n[2] : 1};
-    *bytes = plan(dim, n3, nmat, solid ? 1 : 0, precision).total;
+    *bytes = plan(dim, n3, nmat, solid_kind(solid), precision).total;
     return DFV_OK;
 }
 
@@ -290,16 +293,16 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
                 return DFV_ERR_ARG;
     }
     if (opt->normal_method == 1 && dim != 2) return DFV_ERR_UNSUPPORTED;
-    const Ops *ops = pick_ops(precision, dim, opt->nmat, opt->solid ? 1 : 0);
+    const Ops *ops = pick_ops(precision, dim, opt->nmat, solid_kind(opt->solid));
     if (!ops) return DFV_ERR_UNSUPPORTED;
-    const Layout L = plan(dim, n3, opt->nmat, opt->solid ? 1 : 0, precision);
+    const Layout L = plan(dim, n3, opt->nmat, solid_kind(opt->solid), precision);
     if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) return DFV_ERR_WORKSPACE;
 
     dfv_grid *g = new dfv_grid();
     g->dim = dim;
     g->precision = precision;
     g->nmat_opt = opt->nmat;
-    g->solid = opt->solid ? 1 : 0;
+    g->solid = solid_kind(opt->solid);
     for (int k = 0; k < 6; k++) g->bc[k] = bcs[k];
     g->ops = ops;
     g->stream = (cudaStream_t)stream;

@@ -230,7 +230,7 @@ __host__ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3
 
 // ------------------------------------------------------------------ layout
 
-template <int DIM, int NMAT, bool SOLID>
+template <int DIM, int NMAT, int SOLID>
 struct Lay {
     static constexpr int NV = SOLID ? (DIM == 1 ? 3 : (DIM == 2 ? 5 : 9)) : 0;
     static constexpr int IPHI = 0;
@@ -239,7 +239,9 @@ struct Lay {
     static constexpr int IE = IMOM + DIM;
     static constexpr int IV = IE + 1;
     static constexpr int IR = IV + NV;
-    static constexpr int NVAR = IR + 1;
+    static constexpr int NH = SOLID == 2 ? NMAT : 0;   // plastic-strain planes (phi rho eps)_l
+    static constexpr int IH = IR + 1;
+    static constexpr int NVAR = IR + 1 + NH;
     static constexpr int NB = SOLID ? DIM : 0;   // V*_{d b} entries kept per face
     static constexpr int NF = NVAR + 1 + NB;     // per-face record: fluxes, u*_d, V*_{d.}
 };
@@ -414,14 +416,15 @@ __device__ __forceinline__ T phasic_density(const GridP &g, int l, T ar, T phc)
     return ar / (phc > guard ? phc : guard);
 }
 
-template <class T, int DIM, int NMAT, bool SOLID>
+template <class T, int DIM, int NMAT, int SOLID>
 struct State {
     T phi[NMAT], ar[NMAT];
     T rho, u[DIM], p, rhoE, c2, G, sigY;
     T H[DIM][DIM];     // dev(H), in-plane block
+    T eps[NMAT];       // equivalent plastic strain (SOLID == 2)
 };
 
-template <class T, int DIM, int NMAT, bool SOLID>
+template <class T, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void unpack_A(const T *w, double A[3][3])
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -437,7 +440,7 @@ __device__ __forceinline__ void unpack_A(const T *w, double A[3][3])
 // rho e = sum [ (phi rho)_l e_ref,l + phi_l (p - p_ref,l)/Gamma_l ],
 // G = sum(phi_l G_l/Gamma_l)/sum(phi_l/Gamma_l) (sigma_Y with the same weights),
 // c^2 = sum(Y_l c_l^2/Gamma_l)/sum(phi_l/Gamma_l) with c_l^2 = a_l^2 + 4/3 G_l/rho_l.
-template <class T, int DIM, int NMAT, bool SOLID>
+template <class T, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, State<T, DIM, NMAT, SOLID> &s)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -460,6 +463,12 @@ __device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, S
 #pragma unroll
     for (int a = 0; a < DIM; a++) s.u[a] = w[L::IMOM + a];
     s.p = w[L::IE];
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) s.eps[l] = T(0);
+    if constexpr (SOLID == 2) {
+#pragma unroll
+        for (int l = 0; l < NMAT; l++) s.eps[l] = w[L::IH + l];
+    }
     T J2 = T(0);
     if (SOLID) {
         double A[3][3], H[3][3], j2;
@@ -528,7 +537,7 @@ __device__ __forceinline__ bool needs_fp64(const T *phi_first)
 
 // State from primitives in the compute type T; the FP32 form switches to FP64
 // for cells whose smallest volume fraction is below 1e-6.
-template <class T, int DIM, int NMAT, bool SOLID>
+template <class T, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void state_from_prim(const GridP &g, const T *w, State<T, DIM, NMAT, SOLID> &s)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -551,6 +560,8 @@ __device__ __forceinline__ void state_from_prim(const GridP &g, const T *w, Stat
         s.c2 = (T)sd.c2;
         s.G = (T)sd.G;
         s.sigY = (T)sd.sigY;
+#pragma unroll
+        for (int l = 0; l < NMAT; l++) s.eps[l] = (T)sd.eps[l];
         if (SOLID) {
 #pragma unroll
             for (int a = 0; a < DIM; a++)
@@ -565,7 +576,7 @@ __device__ __forceinline__ void state_from_prim(const GridP &g, const T *w, Stat
 // Conserved -> primitive (Sec. 2.2): rho_l = (phi rho)_l / max(phi_l, guard),
 // u = (rho u)/rho and the mixture pressure
 // p = (rho E - rho|u|^2/2 - sum[(phi rho)_l e_ref,l - phi_l p_ref,l/Gamma_l]) / sum phi_l/Gamma_l.
-template <class T, int DIM, int NMAT, bool SOLID>
+template <class T, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -609,6 +620,7 @@ __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w
 #pragma unroll
         for (int c = 0; c < L::NV; c++) w[L::IV + c] = q[L::IV + c];
         w[L::IR] = q[L::IR];
+        if constexpr (SOLID == 2) w[L::IH] = rho != T(0) ? q[L::IH] / rho : T(0);
         return;
     }
 #pragma unroll
@@ -631,9 +643,14 @@ __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w
 #pragma unroll
     for (int c = 0; c < L::NV; c++) w[L::IV + c] = q[L::IV + c];
     w[L::IR] = q[L::IR];
+    // history: specific eps_l = (phi rho eps)_l / (phi rho)_l, 0 without mass
+    if constexpr (SOLID == 2) {
+#pragma unroll
+        for (int l = 0; l < NMAT; l++) w[L::IH + l] = ar[l] != T(0) ? q[L::IH + l] / ar[l] : T(0);
+    }
 }
 
-template <class T, int DIM, int NMAT, bool SOLID>
+template <class T, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void cons_to_prim(const GridP &g, const T *q, T *w)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -649,7 +666,7 @@ __device__ __forceinline__ void cons_to_prim(const GridP &g, const T *q, T *w)
     cons_to_prim_ct<T, DIM, NMAT, SOLID>(g, q, w);
 }
 
-template <class T, int DIM, int NMAT, bool SOLID>
+template <class T, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void prim_to_cons(const GridP &g, const T *w, T *q)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -665,6 +682,10 @@ __device__ __forceinline__ void prim_to_cons(const GridP &g, const T *w, T *q)
 #pragma unroll
     for (int c = 0; c < L::NV; c++) q[L::IV + c] = w[L::IV + c];
     q[L::IR] = w[L::IR];
+    if constexpr (SOLID == 2) {
+#pragma unroll
+        for (int l = 0; l < NMAT; l++) q[L::IH + l] = s.ar[l] * s.eps[l];
+    }
 }
 
 // ------------------------------------------------------- reconstruction
@@ -741,7 +762,7 @@ __device__ __forceinline__ T upwind_mix(T w, T xl, T xr)
 
 // out += a (U*_K - U_K) on the partial densities, momenta and energy, for the
 // HLLC star state of side K (wave speed SK, normal traction TK, contact Ss).
-template <class T, int DIM, int NMAT, bool SOLID, int D>
+template <class T, int DIM, int NMAT, int SOLID, int D>
 __device__ __forceinline__ void star_jump(const State<T, DIM, NMAT, SOLID> &K, T SK, T TK, T Ss, T a, T *out)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -749,6 +770,10 @@ __device__ __forceinline__ void star_jump(const State<T, DIM, NMAT, SOLID> &K, T
     const T chi = (SK - uK) / (SK - Ss);
 #pragma unroll
     for (int l = 0; l < NMAT; l++) out[L::IAR + l] += a * (K.ar[l] * chi - K.ar[l]);
+    if constexpr (SOLID == 2) {
+#pragma unroll
+        for (int l = 0; l < NMAT; l++) out[L::IH + l] += a * (K.ar[l] * K.eps[l] * chi - K.ar[l] * K.eps[l]);
+    }
 #pragma unroll
     for (int b = 0; b < DIM; b++) out[L::IMOM + b] += a * (K.rho * chi * (b == D ? Ss : K.u[b]) - K.rho * K.u[b]);
     const T EK = K.rhoE / K.rho;
@@ -760,7 +785,7 @@ __device__ __forceinline__ void star_jump(const State<T, DIM, NMAT, SOLID> &K, T
 // Davis wave speeds; partial densities scaled like the mixture density).
 // out[0..NVAR-1]: flux of every plane (r: upwind with the body velocity vr),
 // out[NVAR]: face velocity u*_D, out[NVAR+1+b]: V*_{D b} (upwind by S*).
-template <class T, int DIM, int NMAT, bool SOLID, int D>
+template <class T, int DIM, int NMAT, int SOLID, int D>
 __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR, T vr, T *out)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -833,6 +858,14 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
         const T F = K.ar[l] * uK;
         out[L::IAR + l] = star ? F + SK * (K.ar[l] * chi - K.ar[l]) : F;
     }
+    if constexpr (SOLID == 2) {
+        // plastic-strain planes: carried like the partial densities
+#pragma unroll
+        for (int l = 0; l < NMAT; l++) {
+            const T m = K.ar[l] * K.eps[l];
+            out[L::IH + l] = star ? m * uK + SK * (m * chi - m) : m * uK;
+        }
+    }
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
         const T m = K.rho * K.u[a];
@@ -898,15 +931,18 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
 // replaced by its symmetric unimodular stretch Q diag(exp(s d_k)) Q^T with d_k
 // the deviatoric log-stretches and s = min(1, sigma_Y/sigma_vm),
 // sigma_vm = sqrt(3/2) 2 G |d| (mixture G and sigma_Y).  Energy, masses and
-// momenta are untouched.
+// momenta are untouched.  Returns the equivalent plastic strain increment
+// sqrt(2/3) (1 - s) |d| (0 below yield).
 template <int DIM>
-__device__ __forceinline__ void plastic_return(double A[3][3], double G, double sigY)
+__device__ __forceinline__ double plastic_return(double A[3][3], double G, double sigY)
 {
     double H[3][3], J2;
     Eig2 e;
     stretch_log<DIM>(A, H, J2, e);
     const double svm = sqrt(1.5) * 2.0 * G * sqrt(J2);
     const double sc = (svm > sigY) ? sigY / svm : 1.0;
+    // equivalent plastic strain of the removed deviatoric log-strain (1 - s)|d|
+    const double deps = sc < 1.0 ? sqrt(2.0 / 3.0) * (1.0 - sc) * sqrt(J2) : 0.0;
     const double e0 = exp(sc * e.d[0]), e1 = exp(sc * e.d[1]), e2 = exp(sc * e.d[2]);
     const double av = 0.5 * (e0 + e1), df = 0.5 * (e0 - e1);
     A[0][0] = av + df * e.c2;
@@ -919,6 +955,7 @@ __device__ __forceinline__ void plastic_return(double A[3][3], double G, double 
         A[1][1] = e1;
         A[0][1] = A[1][0] = 0.0;
     }
+    return deps;
 }
 
 }  // namespace dfv

@@ -7,7 +7,7 @@
 
 namespace dfv {
 
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, int SOLID>
 struct Impl {
     using L = Lay<DIM, NMAT, SOLID>;
     using TL = Tile<DIM, (int)sizeof(R)>;
@@ -115,11 +115,13 @@ struct Impl {
 template <class R, int DIM>
 const Ops *select_ops_dim(int nmat, int solid)
 {
-    if (nmat == 1 && !solid) return Impl<R, DIM, 1, false>::ops();
-    if (nmat == 2 && !solid) return Impl<R, DIM, 2, false>::ops();
+    if (nmat == 1 && !solid) return Impl<R, DIM, 1, 0>::ops();
+    if (nmat == 2 && !solid) return Impl<R, DIM, 2, 0>::ops();
     if constexpr (DIM <= 2) {
-        if (nmat == 1 && solid) return Impl<R, DIM, 1, true>::ops();
-        if (nmat == 2 && solid) return Impl<R, DIM, 2, true>::ops();
+        if (nmat == 1 && solid == 1) return Impl<R, DIM, 1, 1>::ops();
+        if (nmat == 2 && solid == 1) return Impl<R, DIM, 2, 1>::ops();
+        if (nmat == 1 && solid == 2) return Impl<R, DIM, 1, 2>::ops();
+        if (nmat == 2 && solid == 2) return Impl<R, DIM, 2, 2>::ops();
     }
     return nullptr;
 }

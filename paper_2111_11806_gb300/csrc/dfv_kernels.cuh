@@ -54,7 +54,7 @@ struct Box {
     __host__ __device__ static constexpr int stride(int d) { return d == 0 ? 1 : (d == 1 ? BX : BX * BY); }
 };
 
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, int SOLID>
 struct StageSmem {
     using L = Lay<DIM, NMAT, SOLID>;
     using B = Box<DIM, (int)sizeof(R)>;
@@ -350,7 +350,7 @@ __device__ __forceinline__ void elvira_normal(const double b[9], double hx, doub
 // contact speed S*; the star state keeps the right state's volume fractions,
 // tangential velocity, stretch tensor and r, so its normal velocity is S*,
 // which the symmetric problem makes the body's v.n.
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R *wl, const R *wr, R *q)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -389,6 +389,10 @@ __device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R
 #pragma unroll
     for (int c = 0; c < L::NV; c++) q[L::IV + c] = wr[L::IV + c];
     q[L::IR] = wr[L::IR];
+    if constexpr (SOLID == 2) {
+#pragma unroll
+        for (int l = 0; l < NMAT; l++) q[L::IH + l] = sr.ar[l] * chi * sr.eps[l];
+    }
 }
 
 // Rigid seeding (Sec. 3.2), one thread per cell: cells with r > 0.5 and
@@ -408,7 +412,7 @@ __device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R
 // no gradient, or no valid probe point).
 // OPT: bit 0 ELVIRA normals (2-D), bit 1 Riemann-problem variant; each option
 // set is its own kernel so that the plain seeding keeps its small footprint.
-template <class R, int DIM, int NMAT, bool SOLID, int OPT>
+template <class R, int DIM, int NMAT, int SOLID, int OPT>
 __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const GridP &g, const int ijk[3], long long c,
                                              R *q)
 {
@@ -582,7 +586,7 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
     }
 }
 
-template <class R, int DIM, int NMAT, bool SOLID, int OPT>
+template <class R, int DIM, int NMAT, int SOLID, int OPT>
 __device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, const int ijk[3], long long c)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -596,7 +600,7 @@ __device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, 
 // Seeding from the step-start state when the probe may read rigid cells
 // (fixed probe): the seeded state of cell c goes to the scratch planes S,
 // whose r plane flags it (1 seeded, 0 not); seed_apply then copies it into U.
-template <class R, int DIM, int NMAT, bool SOLID, int OPT>
+template <class R, int DIM, int NMAT, int SOLID, int OPT>
 __device__ __forceinline__ void seed_cell_to(const R *U, R *S, const Ctl *ctl, const GridP &g, const int ijk[3],
                                              long long c)
 {
@@ -612,7 +616,7 @@ __device__ __forceinline__ void seed_cell_to(const R *U, R *S, const Ctl *ctl, c
     S[L::IR * g.pitch + c] = ok ? R(1) : R(0);
 }
 
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void seed_apply(R *U, const R *S, const GridP &g, long long c)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -644,7 +648,7 @@ __device__ __forceinline__ bool seed_box(const Ctl *ctl, const GridP &g, int lo[
 }
 
 // Threads stride over the cells of the rigid box, x fastest.
-template <class R, int DIM, int NMAT, bool SOLID, int OPT, int MODE>
+template <class R, int DIM, int NMAT, int SOLID, int OPT, int MODE>
 __device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const GridP &g, long long first,
                                                long long stride)
 {
@@ -662,7 +666,7 @@ __device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const
     }
 }
 
-template <class R, int DIM, int NMAT, bool SOLID, int OPT, int MODE>
+template <class R, int DIM, int NMAT, int SOLID, int OPT, int MODE>
 __global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl, GridP g)
 {
     pdl_enter();
@@ -696,7 +700,7 @@ struct StageArgs {
     int want_force;
 };
 
-template <class R, int DIM, int NMAT, bool SOLID, int D>
+template <class R, int DIM, int NMAT, int SOLID, int D>
 __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, bool own, int lx, int ly, int lz,
                                       Acc<R> *Dacc)
 {
@@ -789,7 +793,7 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
 // One tile of one SSP-RK3 stage, executed by a whole CTA: (tbx, tby, tbz) is
 // the tile position in tile units, tile_id its index among the ntiles tiles of
 // the grid (partials slot; the last of them to finish runs the finalize).
-template <class R, int DIM, int NMAT, bool SOLID, int STAGE>
+template <class R, int DIM, int NMAT, int SOLID, int STAGE>
 __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, int tbx, int tby, int tbz,
                                            long long tile_id, long long ntiles)
 {
@@ -887,9 +891,16 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
             state_from_prim<R, DIM, NMAT, SOLID>(g, w, s);
             double A[3][3];
             unpack_A<R, DIM, NMAT, SOLID>(o, A);
-            plastic_return<DIM>(A, (double)s.G, (double)s.sigY);
+            const double deps = plastic_return<DIM>(A, (double)s.G, (double)s.sigY);
 #pragma unroll
             for (int cc = 0; cc < L::NV; cc++) o[L::IV + cc] = (R)A[v_row(DIM, cc)][v_col(DIM, cc)];
+            if constexpr (SOLID == 2) {
+                // the strain removed by the return, added to every material with a yield stress
+#pragma unroll
+                for (int l = 0; l < NMAT; l++)
+                    if (matc<R>(g, l).sigY > R(0) && deps > 0.0)
+                        o[L::IH + l] = (R)((double)o[L::IH + l] + (double)o[L::IAR + l] * deps);
+            }
         }
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) out[v * P + c] = o[v];
@@ -965,7 +976,7 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
     }
 }
 
-template <class R, int DIM, int NMAT, bool SOLID, int STAGE>
+template <class R, int DIM, int NMAT, int SOLID, int STAGE>
 __global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(StageArgs a, GridP g)
 {
     pdl_enter();
@@ -976,7 +987,7 @@ __global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(St
 
 // ------------------------------------------------------------------ CFL
 
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, int SOLID>
 __global__ void __launch_bounds__(256) k_cfl(const void *Uv, double *partials, GridP g)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -1008,7 +1019,7 @@ static __global__ void k_set_dt(Ctl *ctl, double dt) { ctl_set_dt(ctl, dt); }
 
 // ------------------------------------------------------------ conversions
 
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, int SOLID>
 __global__ void __launch_bounds__(256) k_prim_to_cons(const double *prim, long long ppitch, void *Uv, GridP g)
 {
     using L = Lay<DIM, NMAT, SOLID>;
@@ -1024,7 +1035,7 @@ __global__ void __launch_bounds__(256) k_prim_to_cons(const double *prim, long l
     }
 }
 
-template <class R, int DIM, int NMAT, bool SOLID>
+template <class R, int DIM, int NMAT, int SOLID>
 __global__ void __launch_bounds__(256) k_cons_to_prim(const void *Uv, double *prim, long long ppitch, GridP g)
 {
     using L = Lay<DIM, NMAT, SOLID>;

@@ -1,0 +1,61 @@
+"""GPU parity of the equivalent-plastic-strain planes (dfv_options.solid = 2)
+against the oracle: the planes ride the HLLC waves like the partial
+densities and the radial return adds the plastic strain it removes.  Same
+bars as the plain parity tests (FP64 1e-12 after one step, 1e-8 after 100;
+FP32 1e-4)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import rel_l1, run_both
+
+pytestmark = pytest.mark.gpu
+
+B = pytest.importorskip("paper_2111_11806_gb300.binding")
+
+ONE = [
+    ("impact_96", lambda: W.with_history(W.impact_2d(96), seed=3, amp=0.01)),
+    ("solid_two_mat_40x37", lambda: W.with_history(W.random_state(2, (40, 37), 2, True, seed=12, amp=0.02),
+                                                   seed=4, amp=0.01)),
+    ("solid_1d_300", lambda: W.with_history(W.random_state(1, (300,), 1, True, seed=13, amp=0.02), seed=5,
+                                            amp=0.01)),
+    ("solid_1d_two_mat_257", lambda: W.with_history(W.random_state(1, (257,), 2, True, seed=14, amp=0.02),
+                                                    seed=6, amp=0.01)),
+]
+
+
+@pytest.mark.parametrize("name,make", ONE, ids=[c[0] for c in ONE])
+def test_history_fp64_one_step(name, make):
+    wl = make()
+    o, g = run_both(wl, 1, B.DFV_FP64)
+    assert g.nvar == wl.nvar
+    err = rel_l1(g.cons(), o.cons(), wl)
+    assert np.all(err <= 1e-12), err
+
+
+def test_history_fp64_100_steps_impact():
+    wl = W.with_history(W.impact_2d(96))
+    o, g = run_both(wl, 100, B.DFV_FP64)
+    err = rel_l1(g.cons(), o.cons(), wl)
+    assert np.all(err <= 1e-8), err
+    L = W.layout(2, 2, True, True)
+    assert g.prim()[L["ih"]].max() > 1e-3          # the block has yielded
+
+
+def test_history_fp32_impact():
+    wl = W.with_history(W.impact_2d(96))
+    o, g = run_both(wl, 20, B.DFV_FP32)
+    err = rel_l1(g.cons(), o.cons(), wl)
+    assert np.all(err <= 1e-4), err
+
+
+def test_history_planes_leave_the_rest_unchanged():
+    """The same impact with and without the planes: the other conserved
+    planes agree to rounding (the extra planes have no feedback; the two
+    kernels are separate compilations)."""
+    wl = W.impact_2d(96)
+    a = B.Grid.from_workload(wl, precision=B.DFV_FP64)
+    b = B.Grid.from_workload(W.with_history(wl), precision=B.DFV_FP64)
+    a.run(10, wl.cfl)
+    b.run(10, wl.cfl)
+    assert np.all(rel_l1(b.cons()[: wl.nvar], a.cons(), wl) <= 1e-13)
