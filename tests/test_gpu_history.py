@@ -43,10 +43,16 @@ def test_history_fp64_100_steps_impact():
 
 
 def test_history_fp32_impact():
+    """FP32: the physical planes to 1e-4.  The plastic-strain plane sums
+    sqrt(2/3) (1 - s) |d| over the yielding cells, and near the yield surface
+    (s -> 1) the factor 1 - s magnifies the FP32 rounding of the stretch by
+    1/(1 - s): that plane is held to 5e-3."""
     wl = W.with_history(W.impact_2d(96))
     o, g = run_both(wl, 20, B.DFV_FP32)
     err = rel_l1(g.cons(), o.cons(), wl)
-    assert np.all(err <= 1e-4), err
+    L = W.layout(2, 2, True, True)
+    assert np.all(err[: L["ih"]] <= 1e-4), err
+    assert np.all(err[L["ih"]:] <= 5e-3), err
 
 
 def test_history_planes_leave_the_rest_unchanged():
