@@ -36,6 +36,7 @@
 #include <string.h>
 
 #define OMAXV 24
+#define OMAXM 3      /* materials per grid */
 
 enum { MAT_IDEAL = 0, MAT_STIFFENED = 1, MAT_ROMENSKII = 2 };
 
@@ -55,7 +56,7 @@ typedef struct {
     int hist;                                   /* 1: equivalent plastic strain of every material */
     int iphi, iar, imom, iE, iV, ir, ih;        /* plane offsets (ih: history planes after r) */
     int vmap[9][2];                             /* stored V components -> (a,b) */
-    omat mat[2];
+    omat mat[OMAXM];
     long ncell;
     double *U, *Un, *U1, *U3, *D, *W, *tmp;
     unsigned char *mask;
@@ -295,10 +296,10 @@ void o_mat_ref(const omat *m, double rho, double J2, double out[6])
 
 /* Full thermodynamic state of one cell or face, derived from primitives. */
 typedef struct {
-    double phi[2], rhol[2], ar[2];
+    double phi[OMAXM], rhol[OMAXM], ar[OMAXM];
     double rho, u[3], p, rhoE, c2, G, sigY;
     double devH[3][3], A[3][3], J2;
-    double eps[2];      /* equivalent plastic strain of each material (history planes) */
+    double eps[OMAXM];  /* equivalent plastic strain of each material (history planes) */
 } othermo;
 
 /* Mixture closure from primitives (Sec. 2.2): rho = sum phi_l rho_l,
@@ -389,7 +390,7 @@ static double phasic_density(const ostate *s, int l, double ar, double phc)
 static void cons_to_prim(const ostate *s, const double *q, double *w)
 {
     int N = s->nmat;
-    double phi[2], ar[2], rho = 0.0, fsum = 0.0;
+    double phi[OMAXM], ar[OMAXM], rho = 0.0, fsum = 0.0;
     for (int l = 0; l < N - 1; l++) {
         phi[l] = q[s->iphi + l];
         fsum += phi[l];
@@ -413,7 +414,7 @@ static void cons_to_prim(const ostate *s, const double *q, double *w)
     for (int a = 0; a < 3; a++) ke += 0.5 * rho * u[a] * u[a];
     double rhoe = q[s->iE] - ke;
     double num = rhoe, den = 0.0;
-    double rhol[2];
+    double rhol[OMAXM];
     for (int l = 0; l < N; l++) {
         double phc = phi_clip(phi[l]);
         rhol[l] = (N == 1) ? rho : phasic_density(s, l, ar[l], phc);
@@ -1309,6 +1310,7 @@ void o_step(ostate *s, double dt)
  * r (Sec. 2.1.1 history variables). */
 void *o_create(int dim, const int n[3], const double lo[3], const double hi[3], const int periodic[3], int nmat, int solid)
 {
+    if (nmat < 1 || nmat > OMAXM) return NULL;
     ostate *s = (ostate *)calloc(1, sizeof(ostate));
     s->dim = dim;
     s->ncell = 1;

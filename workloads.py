@@ -33,6 +33,7 @@ AIR = dict(kind="ideal", gamma=1.4, rho0=1.225)
 WATER = dict(kind="stiffened", gamma=4.4, pinf=6.0e8, rho0=1000.0)
 # Aluminium-like Romenskii solid: rho0, K0, G0 and the yield stress are the
 # impact workload's; alpha, beta, Gamma0 are the paper's Table 1 aluminium row.
+HELIUM = dict(kind="ideal", gamma=1.67, rho0=0.166)
 ALUMINIUM = dict(kind="romenskii", rho0=2700.0, K0=76.0e9, G0=26.0e9, alpha=0.627,
                  beta=2.288, Gamma0=1.484, sigY=0.3e9)
 
@@ -336,11 +337,22 @@ def random_state(dim, n, nmat, solid, seed, periodic=None, body=True, amp=0.1):
     mats = [AIR] if nmat == 1 else ([ALUMINIUM, AIR] if solid else [AIR, WATER])
     if nmat == 1 and solid:
         mats = [ALUMINIUM]
+    if nmat == 3:
+        mats = [ALUMINIUM, WATER, AIR] if solid else [WATER, HELIUM, AIR]
     if nmat == 2:
         blob = np.hypot(X - 0.4, Y - 0.5) < 0.25
         w[L["iphi"]] = np.where(blob, 1.0 - PHI_PURE, PHI_PURE)
         w[L["iphi"]] = np.clip(w[L["iphi"]] + 0.02 * rng.standard_normal(nc) * (
             (w[L["iphi"]] > 0.5) - 0.5), PHI_PURE, 1.0 - PHI_PURE)
+    if nmat == 3:
+        # two blobs (materials 1 and 2) in the third
+        b1 = np.hypot(X - 0.35, Y - 0.45) < 0.2
+        b2 = (np.hypot(X - 0.7, Y - 0.6) < 0.18) & ~b1 if dim > 1 else (np.abs(X - 0.75) < 0.1)
+        f1 = np.where(b1, 1.0 - 2 * PHI_PURE, PHI_PURE)
+        f2 = np.where(b2, 1.0 - 2 * PHI_PURE, PHI_PURE)
+        f1 = np.clip(f1 + 0.01 * rng.standard_normal(nc) * (f1 > 0.5), PHI_PURE, 1.0 - 2 * PHI_PURE)
+        w[L["iphi"]] = f1
+        w[L["iphi"] + 1] = np.where(b1, PHI_PURE, f2)
     for l, m in enumerate(mats):
         base = {"ideal": 1.2, "stiffened": 1000.0, "romenskii": m.get("rho0", 1.0)}[m["kind"]]
         w[L["irho"] + l] = base * (1.0 + amp * 0.5 * rng.standard_normal(nc) * 0.2 + amp * np.sin(2 * np.pi * X))
