@@ -29,8 +29,26 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libdfvrb.so")
 
 
+# dfv_inst_tu.cu holds one launcher table; it is compiled once per
+# (precision, dimension, number of materials).
+TU = os.path.join(CSRC, "dfv_inst_tu.cu")
+TU_COMBOS = [(prec, dim, nmat) for prec in ("f32", "f64") for dim in (1, 2, 3) for nmat in (1, 2, 3)]
+
+
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    """(source, object name, extra defines, FP32 flags?) of every translation unit."""
+    out = []
+    for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
+        if src == TU:
+            continue
+        base = os.path.basename(src).replace(".cu", "")
+        out.append((src, base, [], "_f32_" in base))
+    for prec, dim, nmat in TU_COMBOS:
+        name = "ops_%s_d%d_n%d" % (prec, dim, nmat)
+        defs = ["-DDFV_TU_REAL=%s" % ("float" if prec == "f32" else "double"), "-DDFV_TU_DIM=%d" % dim,
+                "-DDFV_TU_NMAT=%d" % nmat, "-DDFV_TU_NAME=" + name]
+        out.append((TU, "dfv_inst_" + name, defs, prec == "f32"))
+    return out
 
 
 def headers():
@@ -51,11 +69,12 @@ def _stale(target, deps):
 FP32_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 
 
-def _compile(src, extra):
-    obj = os.path.join(OBJDIR, os.path.basename(src).replace(".cu", ".o"))
+def _compile(unit, extra):
+    src, name, defs, fp32 = unit
+    obj = os.path.join(OBJDIR, name + ".o")
     if _stale(obj, [src] + headers() + [os.path.abspath(__file__)]):
-        flags = FP32_FLAGS if "_f32_" in os.path.basename(src) else []
-        cmd = [nvcc()] + ARCH + FLAGS + flags + list(extra) + ["-c", src, "-o", obj + ".tmp"]
+        flags = FP32_FLAGS if fp32 else []
+        cmd = [nvcc()] + ARCH + FLAGS + flags + defs + list(extra) + ["-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -72,6 +91,8 @@ def build(force: bool = False, extra=(), jobs: int = 0) -> str:
         for o in glob.glob(os.path.join(OBJDIR, "*.o")):
             os.remove(o)
     jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
+    # the kernel tables first: they are the longest compilations
+    srcs = sorted(srcs, key=lambda u: 0 if u[0] == TU else 1)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     if force or _stale(LIB, objs):

@@ -260,7 +260,7 @@ extern "C" {
 
 dfv_status dfv_workspace_bytes(int dim, const int n[3], int nmat, int solid, int precision, size_t *bytes)
 {
-    if (!n || !bytes || dim < 1 || dim > 3 || nmat < 1 || nmat > 2) return DFV_ERR_ARG;
+    if (!n || !bytes || dim < 1 || dim > 3 || nmat < 1 || nmat > 3) return DFV_ERR_ARG;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
     for (int d = 0; d < dim; d++)
         if (n[d] < 1) return DFV_ERR_ARG;
@@ -275,7 +275,7 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
 {
     if (!out || !n || !lo || !hi || !opt) return DFV_ERR_ARG;
     *out = nullptr;
-    if (dim < 1 || dim > 3 || opt->nmat < 1 || opt->nmat > 2) return DFV_ERR_ARG;
+    if (dim < 1 || dim > 3 || opt->nmat < 1 || opt->nmat > 3) return DFV_ERR_ARG;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
     int n3[3] = {1, 1, 1};
     for (int d = 0; d < dim; d++) {

@@ -54,7 +54,7 @@ struct GridP {
     double lo[3], dx[3], inv_dx[3];
     long long ncell, pitch;   // cells, elements between planes
     double dV, dxmin;
-    MatP mat[2];
+    MatP mat[3];
     int use_thinc;
     int hllc_lm;        // 1: low-Mach HLLC-LM dissipation in the star regions
     int seed_variant;   // 0: reflected state (Sec. 3.2), 1: Riemann-problem star state
@@ -63,8 +63,8 @@ struct GridP {
     int wall[3][2];     // reflective wall on the low / high side of direction d
     double beta, cosh_b, sinh_b, tanh_b;   // THINC constants
     double phi_guard;
-    MatC<double> mc_d[2];
-    MatC<float> mc_f[2];
+    MatC<double> mc_d[3];
+    MatC<float> mc_f[3];
     GridC<double> gc_d;
     GridC<float> gc_f;
 };
@@ -72,7 +72,7 @@ struct GridP {
 template <class T>
 __host__ inline void fill_consts(const GridP &g, MatC<T> *mc, GridC<T> &gc)
 {
-    for (int l = 0; l < 2; l++) {
+    for (int l = 0; l < 3; l++) {
         const MatP &m = g.mat[l];
         mc[l].kind = m.kind;
         mc[l].Gam = (T)(m.kind == 2 ? m.Gamma0 : m.gamma - 1.0);

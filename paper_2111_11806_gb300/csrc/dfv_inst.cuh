@@ -111,17 +111,15 @@ struct Impl {
     }
 };
 
-// Tables of one dimension (3-D solids are not built).
-template <class R, int DIM>
-const Ops *select_ops_dim(int nmat, int solid)
+// Tables of one (precision, dimension, materials): fluids, solids and solids
+// with plastic-strain planes (3-D solids are not built).
+template <class R, int DIM, int NMAT>
+const Ops *select_ops_nmat(int solid)
 {
-    if (nmat == 1 && !solid) return Impl<R, DIM, 1, 0>::ops();
-    if (nmat == 2 && !solid) return Impl<R, DIM, 2, 0>::ops();
+    if (!solid) return Impl<R, DIM, NMAT, 0>::ops();
     if constexpr (DIM <= 2) {
-        if (nmat == 1 && solid == 1) return Impl<R, DIM, 1, 1>::ops();
-        if (nmat == 2 && solid == 1) return Impl<R, DIM, 2, 1>::ops();
-        if (nmat == 1 && solid == 2) return Impl<R, DIM, 1, 2>::ops();
-        if (nmat == 2 && solid == 2) return Impl<R, DIM, 2, 2>::ops();
+        if (solid == 1) return Impl<R, DIM, NMAT, 1>::ops();
+        if (solid == 2) return Impl<R, DIM, NMAT, 2>::ops();
     }
     return nullptr;
 }

@@ -675,12 +675,12 @@ __global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl
                                                    (long long)gridDim.x * blockDim.x);
 }
 
-// Launch shape of k_seed: up to 4 CTAs of 256 threads per SM.
+// Launch shape of k_seed: up to 16 CTAs of 256 threads per SM.
 __host__ inline void seed_grid(const GridP &g, dim3 &block, dim3 &grid)
 {
     const long long b = (g.ncell + 255) / 256;
     block = dim3(256, 1, 1);
-    grid = dim3((unsigned)(b < 1 ? 1 : (b > 152LL * 4 ? 152LL * 4 : b)), 1, 1);
+    grid = dim3((unsigned)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b)), 1, 1);
 }
 
 // The option set of a grid as the OPT template argument of the seeding.

@@ -69,7 +69,7 @@ extern "C" dfv_status dfv_compute_dt_noalloc(int dim, const int n[3], const doub
                                              void *stream, double *dt_out)
 {
     if (!n || !lo || !hi || !opt || !kinds || !params || !cons || !dt_out || !(cfl > 0.0)) return DFV_ERR_ARG;
-    if (dim < 1 || dim > 3 || opt->nmat < 1 || opt->nmat > 2) return DFV_ERR_ARG;
+    if (dim < 1 || dim > 3 || opt->nmat < 1 || opt->nmat > 3) return DFV_ERR_ARG;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
     const dfv::Ops *ops = dfv::ops_for(precision == DFV_FP32 ? 1 : 0, dim, opt->nmat,
                                        opt->solid == 2 ? 2 : (opt->solid ? 1 : 0));

@@ -27,26 +27,38 @@ struct Ops {
 };
 
 // nullptr when the combination is not built.  One translation unit per
-// (precision, dimension) so that the build compiles them in parallel.
-const Ops *ops_f64_d1(int nmat, int solid);
-const Ops *ops_f64_d2(int nmat, int solid);
-const Ops *ops_f64_d3(int nmat, int solid);
-const Ops *ops_f32_d1(int nmat, int solid);
-const Ops *ops_f32_d2(int nmat, int solid);
-const Ops *ops_f32_d3(int nmat, int solid);
+// (precision, dimension, materials) so that the build compiles them in
+// parallel (dfv_inst_tu.cu, compiled once per combination).
+const Ops *ops_f32_d1_n1(int solid);
+const Ops *ops_f32_d1_n2(int solid);
+const Ops *ops_f32_d1_n3(int solid);
+const Ops *ops_f32_d2_n1(int solid);
+const Ops *ops_f32_d2_n2(int solid);
+const Ops *ops_f32_d2_n3(int solid);
+const Ops *ops_f32_d3_n1(int solid);
+const Ops *ops_f32_d3_n2(int solid);
+const Ops *ops_f32_d3_n3(int solid);
+const Ops *ops_f64_d1_n1(int solid);
+const Ops *ops_f64_d1_n2(int solid);
+const Ops *ops_f64_d1_n3(int solid);
+const Ops *ops_f64_d2_n1(int solid);
+const Ops *ops_f64_d2_n2(int solid);
+const Ops *ops_f64_d2_n3(int solid);
+const Ops *ops_f64_d3_n1(int solid);
+const Ops *ops_f64_d3_n2(int solid);
+const Ops *ops_f64_d3_n3(int solid);
 
 inline const Ops *ops_for(int precision_fp32, int dim, int nmat, int solid)
 {
-    if (precision_fp32) {
-        if (dim == 1) return ops_f32_d1(nmat, solid);
-        if (dim == 2) return ops_f32_d2(nmat, solid);
-        if (dim == 3) return ops_f32_d3(nmat, solid);
-    } else {
-        if (dim == 1) return ops_f64_d1(nmat, solid);
-        if (dim == 2) return ops_f64_d2(nmat, solid);
-        if (dim == 3) return ops_f64_d3(nmat, solid);
-    }
-    return nullptr;
+    typedef const Ops *(*Fn)(int);
+    static const Fn f32[3][3] = {{ops_f32_d1_n1, ops_f32_d1_n2, ops_f32_d1_n3},
+                                 {ops_f32_d2_n1, ops_f32_d2_n2, ops_f32_d2_n3},
+                                 {ops_f32_d3_n1, ops_f32_d3_n2, ops_f32_d3_n3}};
+    static const Fn f64[3][3] = {{ops_f64_d1_n1, ops_f64_d1_n2, ops_f64_d1_n3},
+                                 {ops_f64_d2_n1, ops_f64_d2_n2, ops_f64_d2_n3},
+                                 {ops_f64_d3_n1, ops_f64_d3_n2, ops_f64_d3_n3}};
+    if (dim < 1 || dim > 3 || nmat < 1 || nmat > 3) return nullptr;
+    return (precision_fp32 ? f32 : f64)[dim - 1][nmat - 1](solid);
 }
 
 // Grid-stride launches use at most this many blocks of 256 threads.
