@@ -55,7 +55,8 @@ typedef int dfv_status;
 #define DFV_ERR_NONPHYSICAL (-3)  /* a kernel saw rho <= 0, c^2 <= 0 or NaN */
 #define DFV_ERR_TIMEOUT (-4)      /* a host wait exceeded its time limit */
 #define DFV_ERR_WORKSPACE (-5)    /* workspace too small or misaligned */
-#define DFV_ERR_UNSUPPORTED (-6)  /* combination not built (e.g. 3-D solid) */
+#define DFV_ERR_UNSUPPORTED (-6)  /* combination not built (3-D solids; 3-D FP64 with
+                                     three materials, whose tile exceeds shared memory) */
 #define DFV_ERR_TOO_LARGE (-7)    /* grid larger than a fixed-size scratch allows */
 
 #define DFV_FP64 0       /* plain FP64 everywhere */

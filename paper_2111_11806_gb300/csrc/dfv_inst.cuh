@@ -116,7 +116,11 @@ struct Impl {
 template <class R, int DIM, int NMAT>
 const Ops *select_ops_nmat(int solid)
 {
-    if (!solid) return Impl<R, DIM, NMAT, 0>::ops();
+    // a stage tile must fit the 227 KB of shared memory a CTA may have (the
+    // 3-D FP64 three-material fluid does not: not built)
+    if constexpr (StageSmem<R, DIM, NMAT, 0>::bytes <= 227u * 1024u) {
+        if (!solid) return Impl<R, DIM, NMAT, 0>::ops();
+    }
     if constexpr (DIM <= 2) {
         if (solid == 1) return Impl<R, DIM, NMAT, 1>::ops();
         if (solid == 2) return Impl<R, DIM, NMAT, 2>::ops();
