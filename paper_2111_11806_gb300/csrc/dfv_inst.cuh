@@ -118,12 +118,15 @@ const Ops *select_ops_nmat(int solid)
 {
     // a stage tile must fit the 227 KB of shared memory a CTA may have (the
     // 3-D FP64 three-material fluid does not: not built)
-    if constexpr (StageSmem<R, DIM, NMAT, 0>::bytes <= 227u * 1024u) {
+    constexpr size_t lim = 227u * 1024u;
+    if constexpr (StageSmem<R, DIM, NMAT, 0>::bytes <= lim) {
         if (!solid) return Impl<R, DIM, NMAT, 0>::ops();
     }
     if constexpr (DIM <= 2) {
-        if (solid == 1) return Impl<R, DIM, NMAT, 1>::ops();
-        if (solid == 2) return Impl<R, DIM, NMAT, 2>::ops();
+        if constexpr (StageSmem<R, DIM, NMAT, 1>::bytes <= lim)
+            if (solid == 1) return Impl<R, DIM, NMAT, 1>::ops();
+        if constexpr (StageSmem<R, DIM, NMAT, 2>::bytes <= lim)
+            if (solid == 2) return Impl<R, DIM, NMAT, 2>::ops();
     }
     return nullptr;
 }

@@ -58,8 +58,12 @@ template <class R, int DIM, int NMAT, int SOLID>
 struct StageSmem {
     using L = Lay<DIM, NMAT, SOLID>;
     using B = Box<DIM, (int)sizeof(R)>;
-    static constexpr size_t bytes =
-        ((sizeof(R) * ((size_t)L::NVAR * B::N + (size_t)L::NF * B::MAXF) + 7) & ~(size_t)7) + 4 * 32 * sizeof(double);
+    // 2-D fluid tiles compute the faces of both directions before one
+    // barrier, so they keep one face array per direction (solids keep one:
+    // their larger face records would cost occupancy)
+    static constexpr int NSF = (DIM == 2 && SOLID == 0) ? 2 : 1;
+    static constexpr size_t floats = (size_t)L::NVAR * B::N + (size_t)NSF * L::NF * B::MAXF;
+    static constexpr size_t bytes = ((sizeof(R) * floats + 7) & ~(size_t)7) + 4 * 32 * sizeof(double);
 };
 
 // ---------------------------------------------------- compensated sums
@@ -700,9 +704,9 @@ struct StageArgs {
     int want_force;
 };
 
+// Fluxes of every face of direction D of the tile into sF (no barrier).
 template <class R, int DIM, int NMAT, int SOLID, int D>
-__device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, bool own, int lx, int ly, int lz,
-                                      Acc<R> *Dacc)
+__device__ __forceinline__ void face_pass(const GridP &g, const R *sW, R *sF, R vr)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     using B = Box<DIM, (int)sizeof(R)>;
@@ -763,7 +767,18 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
 #pragma unroll
         for (int k = 0; k < L::NF; k++) sF[k * B::MAXF + item] = F[k];
     }
-    __syncthreads();
+}
+
+// Divergence and non-conservative terms of direction D for the thread's own
+// cell, from the face fluxes in sF (no barrier).
+template <class R, int DIM, int NMAT, int SOLID, int D>
+__device__ __forceinline__ void accum_pass(const GridP &g, const R *sW, const R *sF, bool own, int lx, int ly, int lz,
+                                           Acc<R> *Dacc)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    using B = Box<DIM, (int)sizeof(R)>;
+    using TL = Tile<DIM, (int)sizeof(R)>;
+    constexpr int EX = TL::TX + (D == 0), EY = TL::TY + (D == 1);
     if (own) {
         const int fl = (lz * EY + ly) * EX + lx;
         const int fr = fl + (D == 0 ? 1 : (D == 1 ? EX : EX * EY));
@@ -787,7 +802,6 @@ __device__ __forceinline__ void sweep(const GridP &g, const R *sW, R *sF, R vr, 
             else Dacc[v].add(div - snc);
         }
     }
-    __syncthreads();
 }
 
 // One tile of one SSP-RK3 stage, executed by a whole CTA: (tbx, tby, tbz) is
@@ -801,10 +815,10 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
     using B = Box<DIM, (int)sizeof(R)>;
     using TL = Tile<DIM, (int)sizeof(R)>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    using SM = StageSmem<R, DIM, NMAT, SOLID>;
     R *sW = reinterpret_cast<R *>(smem_raw);
     R *sF = sW + (size_t)L::NVAR * B::N;
-    double *sred = reinterpret_cast<double *>(
-        smem_raw + ((sizeof(R) * ((size_t)L::NVAR * B::N + (size_t)L::NF * B::MAXF) + 7) & ~(size_t)7));
+    double *sred = reinterpret_cast<double *>(smem_raw + ((sizeof(R) * SM::floats + 7) & ~(size_t)7));
 
     const R *in = reinterpret_cast<const R *>(a.in);
     const R *un = reinterpret_cast<const R *>(a.un);
@@ -860,9 +874,28 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
 #pragma unroll
     for (int v = 0; v < L::NVAR; v++) Dacc[v].zero();
 
-    sweep<R, DIM, NMAT, SOLID, 0>(g, sW, sF, vr[0], own, lx, ly, lz, Dacc);
-    if constexpr (DIM >= 2) sweep<R, DIM, NMAT, SOLID, 1>(g, sW, sF, vr[1], own, lx, ly, lz, Dacc);
-    if constexpr (DIM >= 3) sweep<R, DIM, NMAT, SOLID, 2>(g, sW, sF, vr[2], own, lx, ly, lz, Dacc);
+    if constexpr (SM::NSF == 2) {
+        // 2-D fluids: the faces of both directions, one barrier, both divergences
+        R *sF1 = sF + (size_t)L::NF * B::MAXF;
+        face_pass<R, DIM, NMAT, SOLID, 0>(g, sW, sF, vr[0]);
+        face_pass<R, DIM, NMAT, SOLID, 1>(g, sW, sF1, vr[1]);
+        __syncthreads();
+        accum_pass<R, DIM, NMAT, SOLID, 0>(g, sW, sF, own, lx, ly, lz, Dacc);
+        accum_pass<R, DIM, NMAT, SOLID, 1>(g, sW, sF1, own, lx, ly, lz, Dacc);
+        __syncthreads();
+    } else {
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            if (d == 0) face_pass<R, DIM, NMAT, SOLID, 0>(g, sW, sF, vr[0]);
+            if constexpr (DIM >= 2) if (d == 1) face_pass<R, DIM, NMAT, SOLID, 1>(g, sW, sF, vr[1]);
+            if constexpr (DIM >= 3) if (d == 2) face_pass<R, DIM, NMAT, SOLID, 2>(g, sW, sF, vr[2]);
+            __syncthreads();
+            if (d == 0) accum_pass<R, DIM, NMAT, SOLID, 0>(g, sW, sF, own, lx, ly, lz, Dacc);
+            if constexpr (DIM >= 2) if (d == 1) accum_pass<R, DIM, NMAT, SOLID, 1>(g, sW, sF, own, lx, ly, lz, Dacc);
+            if constexpr (DIM >= 3) if (d == 2) accum_pass<R, DIM, NMAT, SOLID, 2>(g, sW, sF, own, lx, ly, lz, Dacc);
+            __syncthreads();
+        }
+    }
 
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     R smax_cell = R(0);
