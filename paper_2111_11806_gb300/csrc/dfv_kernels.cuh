@@ -719,9 +719,9 @@ __device__ __forceinline__ void face_pass(const GridP &g, const R *sW, R *sF, R 
     // the rows' closing faces (x = 32); otherwise a flat index.
     constexpr bool ROWS = TL::TX == 32 && DIM >= 2;
     constexpr int NROW = TL::TY * TL::TZ;                   // rows of the tile
-    constexpr int ITEMS = ROWS ? TL::THREADS : NFACE;
-    static_assert(!ROWS || (D == 0 ? (NROW + (NROW + 31) / 32) * 32 <= TL::THREADS
-                                   : EY * EZ * 32 <= TL::THREADS), "a face without a thread");
+    // warps of work: one per face row, plus (x sweep) the closing faces
+    constexpr int WROWS = D == 0 ? NROW + (NROW + 31) / 32 : EY * EZ;
+    constexpr int ITEMS = ROWS ? WROWS * 32 : NFACE;
     for (int t = threadIdx.x; t < ITEMS; t += TL::THREADS) {
         int fx, fy, fz;
         if constexpr (ROWS) {
