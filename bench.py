@@ -292,7 +292,8 @@ def run_sphere(torch, B, W, stream):
             "phase_ms_per_step": {"seed": pms[0] / pn, "stage1": pms[1] / pn, "stage2": pms[2] / pn,
                                   "stage3": pms[3] / pn},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "kernel": "k_stage 3-D, FP32"}}
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "kernel": "k_stage_z (3-D FP32, marching along z)"}}
 
 
 def run_ours(args):

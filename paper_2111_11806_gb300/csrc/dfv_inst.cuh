@@ -3,6 +3,7 @@
 #pragma once
 
 #include "dfv_kernels.cuh"
+#include "dfv_kernels_z.cuh"
 #include "dfv_ops.h"
 
 namespace dfv {
@@ -19,6 +20,21 @@ struct Impl {
 
     static constexpr size_t smem = StageSmem<R, DIM, NMAT, SOLID>::bytes;
 
+    // 3-D FP32 single-material fluids march along z (k_stage_z); stage 1
+    // with the pressure force keeps the tiled kernel, whose tiles own the
+    // force partials
+    static constexpr bool ZM = DIM == 3 && SOLID == 0 && NMAT == 1 && sizeof(R) == 4;
+    static constexpr size_t zsmem = ZSmem<R, NMAT>::bytes;
+    // planes per CTA: 32 on the 256^3 sphere beats 16, 24, 64 and 256 (the
+    // six-plane prologue of a chunk against the CTA count for the 152 SMs)
+    static constexpr int ZCHUNK = 32;
+
+    static dim3 zgrid(const GridP &g)
+    {
+        return dim3((g.n[0] + ZGeo::TX - 1) / ZGeo::TX, (g.n[1] + ZGeo::TY - 1) / ZGeo::TY,
+                    (g.n[2] + ZCHUNK - 1) / ZCHUNK);
+    }
+
     // Opt the stage kernels in to their dynamic shared memory on the current
     // device (called at grid creation, outside any stream capture).
     static cudaError_t prepare()
@@ -31,12 +47,27 @@ struct Impl {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_stage<R, DIM, NMAT, SOLID, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
+        if constexpr (ZM) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_stage_z<R, NMAT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)zsmem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_stage_z<R, NMAT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)zsmem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_stage_z<R, NMAT, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)zsmem);
+        }
         return e;
     }
 
     template <int S>
     static cudaError_t stage_s(const GridP &g, const StageArgs &a, cudaStream_t st)
     {
+        if constexpr (ZM) {
+            if (!(S == 1 && a.want_force))
+                return launch_pdl(k_stage_z<R, NMAT, S>, zgrid(g), dim3(ZGeo::THREADS), zsmem, st, a, g, ZCHUNK);
+        }
         return launch_pdl(k_stage<R, DIM, NMAT, SOLID, S>, stage_grid(g), dim3(TL::THREADS), smem, st, a, g);
     }
 
