@@ -32,32 +32,62 @@ struct ZSmem {
 
 __device__ __forceinline__ int z_slot(int z) { return ((z % ZGeo::RING) + ZGeo::RING) % ZGeo::RING; }
 
-// Primitives of plane z (with its x, y halo) into one ring slot; boundary
-// planes and cells mapped as in the tiled kernel (mirror images behind walls).
+// The conserved values of one plane (with its x, y halo) in the registers
+// of the CTA's threads: fetched from global memory one plane ahead, so that
+// the loads are in flight while the faces of the current plane are computed,
+// then converted to primitives into a ring slot.  Boundary planes and cells
+// are mapped as in the tiled kernel (mirror images behind walls).
 template <class R, int NMAT>
-__device__ __forceinline__ void z_load_plane(const GridP &g, const R *in, R *dst, int ox, int oy, int z, bool interior)
+struct ZPlane {
+    static constexpr int K = (ZGeo::SN + ZGeo::THREADS - 1) / ZGeo::THREADS;   // cells per thread
+    R q[K][Lay<3, NMAT, 0>::NVAR];
+    unsigned flip;   // 3 bits per cell: mirrored in x, y, z
+};
+
+template <class R, int NMAT>
+__device__ __forceinline__ void z_fetch_plane(const GridP &g, const R *in, ZPlane<R, NMAT> &f, int ox, int oy, int z,
+                                              bool interior)
 {
     using L = Lay<3, NMAT, 0>;
     using Z = ZGeo;
     bool flz = false;
     const int gz = halo_idx(g, 2, z, &flz);
-    for (int i = threadIdx.x; i < Z::SN; i += Z::THREADS) {
+    f.flip = 0u;
+#pragma unroll
+    for (int k = 0; k < ZPlane<R, NMAT>::K; k++) {
+        const int i = threadIdx.x + k * Z::THREADS;
+        if (i >= Z::SN) continue;
         const int lx = i % Z::BX - Z::HX, ly = i / Z::BX - Z::HY;
         if ((lx < 0 || lx >= Z::TX) && (ly < 0 || ly >= Z::TY)) continue;
-        bool fl[3] = {false, false, flz};
+        bool fx = false, fy = false;
         int gx = ox + lx, gy = oy + ly;
         if (!interior) {
-            gx = halo_idx(g, 0, ox + lx, &fl[0]);
-            gy = halo_idx(g, 1, oy + ly, &fl[1]);
+            gx = halo_idx(g, 0, ox + lx, &fx);
+            gy = halo_idx(g, 1, oy + ly, &fy);
         }
+        f.flip |= ((fx ? 1u : 0u) | (fy ? 2u : 0u) | (flz ? 4u : 0u)) << (3 * k);
         const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
-        R q[L::NVAR], w[L::NVAR];
 #pragma unroll
-        for (int v = 0; v < L::NVAR; v++) q[v] = in[v * g.pitch + c];
-        cons_to_prim<R, 3, NMAT, 0>(g, q, w);
+        for (int v = 0; v < L::NVAR; v++) f.q[k][v] = in[v * g.pitch + c];
+    }
+}
+
+template <class R, int NMAT>
+__device__ __forceinline__ void z_commit_plane(const GridP &g, const ZPlane<R, NMAT> &f, R *dst)
+{
+    using L = Lay<3, NMAT, 0>;
+    using Z = ZGeo;
+#pragma unroll
+    for (int k = 0; k < ZPlane<R, NMAT>::K; k++) {
+        const int i = threadIdx.x + k * Z::THREADS;
+        if (i >= Z::SN) continue;
+        const int lx = i % Z::BX - Z::HX, ly = i / Z::BX - Z::HY;
+        if ((lx < 0 || lx >= Z::TX) && (ly < 0 || ly >= Z::TY)) continue;
+        R w[L::NVAR];
+        cons_to_prim<R, 3, NMAT, 0>(g, f.q[k], w);
 #pragma unroll
         for (int d = 0; d < 3; d++)
-            if (fl[d]) w[L::IMOM + d] = -w[L::IMOM + d];
+            if ((f.flip >> (3 * k + d)) & 1u) w[L::IMOM + d] = -w[L::IMOM + d];
 #pragma unroll
         for (int v = 0; v < L::NVAR; v++) dst[v * Z::SN + i] = w[v];
     }
@@ -129,8 +159,11 @@ __device__ __forceinline__ void z_face(const GridP &g, const R *ring, int z, int
     riemann<R, 3, NMAT, 0, 2>(g, wL, wR, vr, F);
 }
 
+// Two CTAs per SM (the ring takes 92 KB): the register bound keeps both
+// resident (without it the pipelined loads push stages 1-2 to 111 registers
+// and 40 % longer launches).
 template <class R, int NMAT, int STAGE>
-__global__ void __launch_bounds__(ZGeo::THREADS) k_stage_z(StageArgs a, GridP g, int zc)
+__global__ void __launch_bounds__(ZGeo::THREADS, 2) k_stage_z(StageArgs a, GridP g, int zc)
 {
     pdl_enter();
     using L = Lay<3, NMAT, 0>;
@@ -158,9 +191,14 @@ __global__ void __launch_bounds__(ZGeo::THREADS) k_stage_z(StageArgs a, GridP g,
     const R ca = STAGE == 2 ? R(0.75) : (STAGE == 3 ? R(1.0 / 3.0) : R(0));
     const R cb = STAGE == 2 ? R(0.25) : (STAGE == 3 ? R(2.0 / 3.0) : R(1));
 
-    // planes z0-3 .. z0+2, then the z face below the first plane
-    for (int z = z0 - 3; z <= z0 + 2; z++)
-        z_load_plane<R, NMAT>(g, in, ring + (size_t)z_slot(z) * L::NVAR * Z::SN, ox, oy, z, interior);
+    // planes z0-3 .. z0+2, plane z0+3 into registers, then the z face below
+    // the first plane
+    ZPlane<R, NMAT> fp;
+    for (int z = z0 - 3; z <= z0 + 2; z++) {
+        z_fetch_plane<R, NMAT>(g, in, fp, ox, oy, z, interior);
+        z_commit_plane<R, NMAT>(g, fp, ring + (size_t)z_slot(z) * L::NVAR * Z::SN);
+    }
+    z_fetch_plane<R, NMAT>(g, in, fp, ox, oy, z0 + 3, interior);
     __syncthreads();
     R Flo[L::NF];
     if (col) z_face<R, NMAT>(g, ring, z0 - 1, lx, ly, vr[2], Flo);
@@ -171,8 +209,20 @@ __global__ void __launch_bounds__(ZGeo::THREADS) k_stage_z(StageArgs a, GridP g,
     for (int z = z0; z < z1; z++) {
         // plane z+3 into the slot of plane z-3, which nothing reads any more
         // (its last reader, the z face below plane z-1, is behind a barrier)
-        z_load_plane<R, NMAT>(g, in, ring + (size_t)z_slot(z + 3) * L::NVAR * Z::SN, ox, oy, z + 3, interior);
+        z_commit_plane<R, NMAT>(g, fp, ring + (size_t)z_slot(z + 3) * L::NVAR * Z::SN);
         __syncthreads();
+        // loads in flight during the faces: plane z+4 and the cell's own
+        // stage input and step-start values
+        if (z + 1 < z1) z_fetch_plane<R, NMAT>(g, in, fp, ox, oy, z + 4, interior);
+        const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * z);
+        R cin[L::NVAR], cun[L::NVAR];
+        if (col) {
+#pragma unroll
+            for (int v = 0; v < L::NVAR; v++) {
+                cin[v] = in[v * P + c];
+                cun[v] = un[v * P + c];
+            }
+        }
         const R *pl = ring + (size_t)z_slot(z) * L::NVAR * Z::SN;
         z_face_pass<R, NMAT, 0>(g, pl, sFx, vr[0]);
         z_face_pass<R, NMAT, 1>(g, pl, sFy, vr[1]);
@@ -218,14 +268,11 @@ __global__ void __launch_bounds__(ZGeo::THREADS) k_stage_z(StageArgs a, GridP g,
                     Dacc[v].add(div - snc);
                 }
             }
-            const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * z);
-            const bool masked = un[L::IR * P + c] > R(0.5);
+            const bool masked = cun[L::IR] > R(0.5);
             R o[L::NVAR];
 #pragma unroll
-            for (int v = 0; v < L::NVAR; v++) {
-                const R unv = un[v * P + c];
-                o[v] = (masked && v != L::IR) ? unv : rk_combine<R>(STAGE, unv, in[v * P + c], Dacc[v], dt, ca, cb);
-            }
+            for (int v = 0; v < L::NVAR; v++)
+                o[v] = (masked && v != L::IR) ? cun[v] : rk_combine<R>(STAGE, cun[v], cin[v], Dacc[v], dt, ca, cb);
 #pragma unroll
             for (int v = 0; v < L::NVAR; v++) out[v * P + c] = o[v];
             if (!(o[L::IAR] + (NMAT > 1 ? o[L::IAR + NMAT - 1] : R(0)) > R(0)) || !(o[L::IE] == o[L::IE]))
