@@ -34,8 +34,9 @@ struct Plan {
     std::vector<int> tiles_x, tiles_y;
 };
 
-int tile_x(int) { return 32; }
-int tile_y(int precision) { return precision == DFV_FP32 ? 16 : 8; }
+// the tile of the 2-D stage kernels that the batch items address
+int tile_x(int precision) { return precision == DFV_FP32 ? dfv::Tile<2, 4>::TX : dfv::Tile<2, 8>::TX; }
+int tile_y(int precision) { return precision == DFV_FP32 ? dfv::Tile<2, 4>::TY : dfv::Tile<2, 8>::TY; }
 
 int nvar_2d(int nmat) { return (nmat - 1) + nmat + 2 + 1 + 1; }
 
