@@ -42,6 +42,8 @@ struct dfv_grid {
     bool graph_ready = false;
     long long graph_launches = 0;   // kernels in one replay of the step graph
     bool dt_valid = false;               // ctl->dt holds the device-computed next dt
+    int fin_pending = 0;                 // mode of a finalize deferred to the next seeding launch (0: none)
+    bool graph_defer = false;            // the captured step defers its finalize
     double run_cfl = -1.0, run_tend = -1.0;
     bool prof = false;                   // per-kernel event timing (dfv_profile)
     std::vector<cudaEvent_t> ev_free;
@@ -186,10 +188,26 @@ dfv_status read_ctl(dfv_grid *g, Ctl *h)
 dfv_status finalize(dfv_grid *g, int mode, long long nb_max)
 {
     g->launches++;
+    if (nb_max == 0 && !(mode & 2)) {
+        DFV_CU(g, dfv::launch_pdl(dfv::k_finalize_lite, dim3(1), dim3(32), 0, g->stream, g->ctl, mode, g->dim,
+                                  g->g.dx[0], g->g.dx[1], g->g.dx[2]),
+               "k_finalize_lite");
+        return DFV_OK;
+    }
     DFV_CU(g, dfv::launch_pdl(dfv::k_finalize, dim3(1), dim3(1024), 0, g->stream, g->ctl, (const double *)g->partials,
                               nb_max, g->nb_stage, mode, g->dim, g->g.dx[0], g->g.dx[1], g->g.dx[2]),
            "k_finalize");
     return DFV_OK;
+}
+
+// A finalize that a device-driven run deferred to the next step's seeding
+// launch, run now: before anything else reads or writes the control block.
+dfv_status flush_fin(dfv_grid *g)
+{
+    if (!g->fin_pending) return DFV_OK;
+    const int mode = g->fin_pending;
+    g->fin_pending = 0;
+    return finalize(g, mode, 0);
 }
 
 // CFL reduction over the stored state into ctl->smax.
@@ -216,7 +234,14 @@ cudaEvent_t take_event(dfv_grid *g)
     return e;
 }
 
-dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false)
+// The finalize of a device-driven step of a static body (stepped probe) is
+// deferred: the next step's seeding launch runs it beside the seeding, which
+// needs only the rigid box that stage 3 folded.
+bool can_defer(const dfv_grid *g) { return !g->dynamic && g->g.probe_mode == 0; }
+
+// fin_in: mode of the previous step's deferred finalize to run in this step's
+// seeding launch (0: none); defer: leave this step's finalize pending.
+dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false, int fin_in = 0, bool defer = false)
 {
     const int want_force = g->dynamic ? 1 : 0;
     const bool rec = g->prof && !capturing;
@@ -228,7 +253,7 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false)
         }
         DFV_CU(g, cudaEventRecord(ev[0], g->stream), "event");
     }
-    DFV_CU(g, g->ops->seed(g->g, g->U, g->U1, g->ctl, g->stream), "k_seed");
+    DFV_CU(g, g->ops->seed(g->g, g->U, g->U1, g->ctl, fin_in, g->stream), "k_seed");
     if (rec) DFV_CU(g, cudaEventRecord(ev[1], g->stream), "event");
     DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, g->stream),
            "k_stage<1>");
@@ -239,8 +264,10 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false)
     if (rec) DFV_CU(g, cudaEventRecord(ev[4], g->stream), "event");
     // one block: CFL maximum (folded by the stage-3 tiles), force sum, body
     // update, next dt
-    dfv_status fs = finalize(g, 1 | (want_force ? 2 : 0) | 4 | mode_extra, 0);
-    if (fs != DFV_OK) return fs;
+    if (!defer) {
+        dfv_status fs = finalize(g, 1 | (want_force ? 2 : 0) | 4 | mode_extra, 0);
+        if (fs != DFV_OK) return fs;
+    }
     if (rec) {
         DFV_CU(g, cudaEventRecord(ev[5], g->stream), "event");
         g->ev_steps.push_back(ev);
@@ -391,6 +418,7 @@ dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device)
 {
     if (!g) return DFV_ERR_ARG;
     if (!prim) return fail(g, DFV_ERR_ARG, "dfv_set_fields: null field pointer");
+    if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
     if (g->nmat != g->nmat_opt) return fail(g, DFV_ERR_ARG, "dfv_set_fields: materials missing");
     const size_t bytes = sizeof(double) * g->ops->nvar * (size_t)g->g.ncell;
     DFV_CU(g, cudaMemcpyAsync(g->staging, prim, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -432,6 +460,7 @@ dfv_status dfv_set_body(dfv_grid *g, const double v[3], const double x[3], doubl
 {
     if (!g) return DFV_ERR_ARG;
     double vv[3] = {0, 0, 0}, xx[3] = {0, 0, 0};
+    if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
     for (int d = 0; d < 3; d++) {
         vv[d] = (v && d < g->dim) ? v[d] : 0.0;
         xx[d] = x ? x[d] : 0.0;
@@ -450,6 +479,7 @@ dfv_status dfv_set_body(dfv_grid *g, const double v[3], const double x[3], doubl
 dfv_status dfv_get_body(dfv_grid *g, double force[3], double v[3], double x[3])
 {
     if (!g) return DFV_ERR_ARG;
+    if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
     Ctl h;
     dfv_status s = read_ctl(g, &h);
     for (int d = 0; d < 3; d++) {
@@ -465,6 +495,7 @@ dfv_status dfv_compute_dt(dfv_grid *g, double cfl, double *dt_out)
     if (!g) return DFV_ERR_ARG;
     if (!dt_out || !(cfl > 0.0)) return fail(g, DFV_ERR_ARG, "dfv_compute_dt: bad arguments");
     if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_compute_dt: fields not set");
+    if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
     if (!g->smax_valid) {
         dfv_status s = reduce_cfl(g);
         if (s != DFV_OK) return s;
@@ -480,6 +511,7 @@ dfv_status dfv_step(dfv_grid *g, double dt)
     if (!g) return DFV_ERR_ARG;
     if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_step: fields not set");
     if (!(dt >= 0.0)) return fail(g, DFV_ERR_ARG, "dfv_step: dt must be >= 0");
+    if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
     dfv::k_set_dt<<<1, 1, 0, g->stream>>>(g->ctl, dt);
     g->launches++;
     DFV_CU(g, cudaGetLastError(), "k_set_dt");
@@ -495,6 +527,11 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
     if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_run: fields not set");
     if (steps < 0 || !(cfl > 0.0)) return fail(g, DFV_ERR_ARG, "dfv_run: bad arguments");
     const double tend = t_end > 0.0 ? t_end : 0.0;
+    const bool defer = can_defer(g);
+    if (g->fin_pending && (!defer || cfl != g->run_cfl || tend != g->run_tend || !g->smax_valid || !g->dt_valid)) {
+        dfv_status fs = flush_fin(g);
+        if (fs != DFV_OK) return fs;
+    }
     if (cfl != g->run_cfl || tend != g->run_tend) {
         k_set_run<<<1, 1, 0, g->stream>>>(g->ctl, cfl, tend);
         g->launches++;
@@ -515,7 +552,8 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
         g->dt_valid = true;
     }
     const bool use_graph = g->stream != nullptr && steps > 0 && !g->prof;
-    if (use_graph && !g->graph_ready) {
+    const int fin_run = 1 | 4 | 8;   // the finalize mode of a device-driven step (static body)
+    if (use_graph && (!g->graph_ready || g->graph_defer != defer)) {
         if (g->graph) {
             cudaGraphExecDestroy(g->graph);
             g->graph = nullptr;
@@ -523,7 +561,8 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
         cudaGraph_t graph = nullptr;
         DFV_CU(g, cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         const long long before = g->launches;
-        dfv_status cs = launch_step(g, 8, true);
+        // the replayed step runs the previous step's deferred finalize
+        dfv_status cs = defer ? launch_step(g, 8, true, fin_run, true) : launch_step(g, 8, true);
         cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
         g->graph_launches = g->launches - before;   // kernels of one replay
         g->launches = before;   // capture launches nothing
@@ -533,18 +572,25 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
         g->graph_ready = true;
+        g->graph_defer = defer;
     }
     for (int k = 0; k < steps; k++) {
-        if (use_graph) {
+        if (defer && !g->fin_pending) {
+            // nothing to finalize before this step: launched directly
+            s = launch_step(g, 8, false, 0, true);
+            if (s != DFV_OK) return s;
+        } else if (use_graph) {
             DFV_CU(g, cudaGraphLaunch(g->graph, g->stream), "graph launch");
             g->launches += g->graph_launches;
         } else {
-            s = launch_step(g, 8);
+            s = defer ? launch_step(g, 8, false, g->fin_pending, true) : launch_step(g, 8);
             if (s != DFV_OK) return s;
         }
+        if (defer) g->fin_pending = fin_run;
     }
     g->smax_valid = true;
     if (t_out) {
+        if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
         Ctl h;
         s = read_ctl(g, &h);
         *t_out = h.t;
@@ -556,6 +602,7 @@ dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_o
 dfv_status dfv_check(dfv_grid *g, int timeout_ms)
 {
     if (!g) return DFV_ERR_ARG;
+    if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
     dfv_status s = sync_stream(g, timeout_ms);
     if (s != DFV_OK) return s;
     Ctl h;

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_batch_seed(BatchArgs b)
     R *S = reinterpret_cast<R *>(b.out) + I.off;
     seed_box_cells<R, 2, NMAT, false, OPT, MODE>(U, S, I.ctl, I.g,
                                                  (blockIdx.x % SEED_CTAS) * (long long)blockDim.x + threadIdx.x,
-                                                 (long long)SEED_CTAS * blockDim.x);
+                                                 (long long)SEED_CTAS * blockDim.x, false);
 }
 
 // CFL wave speed of every instance's stored state; the last tile of each

@@ -87,26 +87,29 @@ struct Impl {
     }
 
     template <int OPT>
-    static cudaError_t seed_opt_k(const GridP &g, void *U, void *scratch, const Ctl *ctl, cudaStream_t st)
+    static cudaError_t seed_opt_k(const GridP &g, void *U, void *scratch, Ctl *ctl, int fin_mode, cudaStream_t st)
     {
         dim3 block, grid;
         seed_grid(g, block, grid);
         if (g.probe_mode == 1) {
-            cudaError_t e = launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 1>, grid, block, 0, st, U, scratch, ctl, g);
+            cudaError_t e = launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 1>, grid, block, 0, st, U, scratch, ctl, g, 0);
             if (e != cudaSuccess) return e;
-            return launch_pdl(k_seed<R, DIM, NMAT, SOLID, 0, 2>, grid, block, 0, st, U, scratch, ctl, g);
+            return launch_pdl(k_seed<R, DIM, NMAT, SOLID, 0, 2>, grid, block, 0, st, U, scratch, ctl, g, 0);
         }
-        return launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 0>, grid, block, 0, st, U, scratch, ctl, g);
+        if (fin_mode) grid.x += 1;   // the block that runs the deferred finalize
+        return launch_pdl(k_seed<R, DIM, NMAT, SOLID, OPT, 0>, grid, block, 0, st, U, scratch, ctl, g, fin_mode);
     }
 
-    // seeding; scratch: planes of the grid's layout free until stage 1
-    static cudaError_t seed(const GridP &g, void *U, void *scratch, const Ctl *ctl, cudaStream_t st)
+    // seeding; scratch: planes of the grid's layout free until stage 1;
+    // fin_mode: the deferred finalize of the previous step (stepped probe
+    // only), 0 for none
+    static cudaError_t seed(const GridP &g, void *U, void *scratch, Ctl *ctl, int fin_mode, cudaStream_t st)
     {
         switch (seed_opt(g)) {
-        case 0: return seed_opt_k<0>(g, U, scratch, ctl, st);
-        case 1: return seed_opt_k<1>(g, U, scratch, ctl, st);
-        case 2: return seed_opt_k<2>(g, U, scratch, ctl, st);
-        default: return seed_opt_k<3>(g, U, scratch, ctl, st);
+        case 0: return seed_opt_k<0>(g, U, scratch, ctl, fin_mode, st);
+        case 1: return seed_opt_k<1>(g, U, scratch, ctl, fin_mode, st);
+        case 2: return seed_opt_k<2>(g, U, scratch, ctl, fin_mode, st);
+        default: return seed_opt_k<3>(g, U, scratch, ctl, fin_mode, st);
         }
     }
 

@@ -160,6 +160,9 @@ __device__ __forceinline__ T block_max(T v, T *scratch /* 32 */)
 
 // ------------------------------------------------------------ finalize
 
+__device__ __forceinline__ void finalize_apply(Ctl *ctl, Ctl &sc, const double red[4], int mode, int dim,
+                                               const double dxs[3], bool reset_box);
+
 // mode bit 0: reduce the CFL partials (nb_cfl blocks) into ctl->smax
 // mode bit 1: reduce the force partials (nb_force blocks) into ctl->force
 // mode bit 2: end of a step: body update with ctl->dt, t += dt
@@ -196,6 +199,15 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
     __syncthreads();     // the shared copy is complete
     if (threadIdx.x != 0) return;
     const double dxs[3] = {dx0, dx1, dx2};
+    finalize_apply(ctl, sc, red, mode, dim, dxs, true);
+}
+
+// The serial part of the finalize (one thread): sc is a copy of *ctl, red
+// the reduced maxima / sums.  reset_box = false leaves ctl->rnext as it is
+// (other blocks of the launch still read it; stage 1 resets it).
+__device__ __forceinline__ void finalize_apply(Ctl *ctl, Ctl &sc, const double red[4], int mode, int dim,
+                                               const double dxs[3], bool reset_box)
+{
     if (mode & 2)
         for (int d = 0; d < 3; d++) sc.force[d] = ctl->force[d] = red[1 + d];
     if (mode & 4) {
@@ -214,7 +226,7 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
         // the rigid box of the state just produced becomes the seeding box
         for (int k = 0; k < 6; k++) ctl->rbox[k] = sc.rnext[k];
         ctl->rbox_valid = 1;
-        ctl_box_reset(ctl);
+        if (reset_box) ctl_box_reset(ctl);
     }
     if (mode & 1) {
         double sb = 0.0;
@@ -228,6 +240,31 @@ __device__ __forceinline__ void finalize_block(Ctl *ctl, const double *partials,
         if (!(dt == dt)) dt = 0.0;
         ctl_set_dt(ctl, dt);
     }
+}
+
+// The finalize without partial sums (CFL maximum folded into ctl->smax_acc by
+// the stage-3 tiles; mode bit 1 not allowed), executed by one warp: the lanes
+// copy the control block, lane 0 applies the update.
+__device__ __forceinline__ void finalize_warp(Ctl *ctl, int mode, int dim, const double dxs[3], bool reset_box)
+{
+    __shared__ Ctl sc;
+    constexpr int NWORD = (int)(sizeof(Ctl) / sizeof(unsigned long long));
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k < NWORD; k += 32)
+        reinterpret_cast<unsigned long long *>(&sc)[k] = reinterpret_cast<const unsigned long long *>(ctl)[k];
+    __syncwarp();
+    if (lane != 0) return;
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    if (mode & 1) red[0] = __longlong_as_double((long long)atomicExch(&ctl->smax_acc, 0ull));
+    finalize_apply(ctl, sc, red, mode, dim, dxs, reset_box);
+}
+
+static __global__ void __launch_bounds__(32) k_finalize_lite(Ctl *ctl, int mode, int dim, double dx0, double dx1,
+                                                             double dx2)
+{
+    pdl_enter();
+    const double dxs[3] = {dx0, dx1, dx2};
+    finalize_warp(ctl, mode, dim, dxs, true);
 }
 
 static __global__ void __launch_bounds__(1024) k_finalize(Ctl *ctl, const double *partials, long long nb_cfl,
@@ -466,6 +503,10 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
         unsigned int valid = 0u;
         const bool fixed = g.probe_mode == 1;
         if (!fixed) {
+        // a step is valid when its 2^DIM enclosing cells lie in the grid (or
+        // wrap, in a periodic direction) and all have r < 0.5
+        const bool anyper = g.periodic[0] || (DIM >= 2 && g.periodic[1]) || (DIM >= 3 && g.periodic[2]);
+        const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
 #pragma unroll
         for (int step = 0; step < 7; step++) {
             const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
@@ -478,18 +519,34 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
             }
             bool ok = true;
             R rmax = R(0);
+            if (!anyper) {
+                // corner offsets from the lowest corner; nothing is loaded for
+                // a step whose cells leave the grid
 #pragma unroll
-            for (int m = 0; m < NC; m++) {
-                int ci[3] = {0, 0, 0};
+                for (int d = 0; d < DIM; d++) ok = ok && base[d] >= 0 && base[d] <= g.n[d] - 2;
+                if (ok) {
+                    const long long c0 = base[0] + sy * base[1] + sz * base[2];
 #pragma unroll
-                for (int d = 0; d < DIM; d++) {
-                    int ii = base[d] + ((m >> d) & 1);
-                    if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
-                    else if (ii < 0 || ii > g.n[d] - 1) ok = false;
-                    ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
+                    for (int m = 0; m < NC; m++) {
+                        const long long cm = c0 + (m & 1) + ((m >> 1) & 1) * sy + ((m >> 2) & 1) * sz;
+                        const R rv = U[L::IR * P + cm];
+                        rmax = (rv < R(0.5)) ? rmax : R(1);
+                    }
                 }
-                const R rv = U[L::IR * P + ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2])];
-                rmax = (rv < R(0.5)) ? rmax : R(1);
+            } else {
+#pragma unroll
+                for (int m = 0; m < NC; m++) {
+                    int ci[3] = {0, 0, 0};
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) {
+                        int ii = base[d] + ((m >> d) & 1);
+                        if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
+                        else if (ii < 0 || ii > g.n[d] - 1) ok = false;
+                        ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
+                    }
+                    const R rv = U[L::IR * P + ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2])];
+                    rmax = (rv < R(0.5)) ? rmax : R(1);
+                }
             }
             if (ok && rmax == R(0)) valid |= 1u << step;
         }
@@ -633,16 +690,19 @@ __device__ __forceinline__ void seed_apply(R *U, const R *S, const GridP &g, lon
 // (r > 0.5), which stage 3 of the previous step folded into the control block;
 // without one (fields just set) the whole grid.  seed_box returns false when
 // the box is empty.
-__device__ __forceinline__ bool seed_box(const Ctl *ctl, const GridP &g, int lo[3], int hi[3])
+__device__ __forceinline__ bool seed_box(const Ctl *ctl, const GridP &g, int lo[3], int hi[3], bool next)
 {
-    const bool valid = ctl->rbox_valid != 0;
+    // next: the box that the last stage 3 folded, not yet published (its
+    // finalize runs in this launch)
+    const bool valid = next || ctl->rbox_valid != 0;
+    const int *box = next ? ctl->rnext : ctl->rbox;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         lo[d] = 0;
         hi[d] = g.n[d] - 1;
         if (valid) {
-            lo[d] = max(lo[d], ctl->rbox[d]);
-            hi[d] = min(hi[d], ctl->rbox[3 + d]);
+            lo[d] = max(lo[d], box[d]);
+            hi[d] = min(hi[d], box[3 + d]);
         }
     }
     return lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2];
@@ -651,12 +711,26 @@ __device__ __forceinline__ bool seed_box(const Ctl *ctl, const GridP &g, int lo[
 // Threads stride over the cells of the rigid box, x fastest.
 template <class R, int DIM, int NMAT, int SOLID, int OPT, int MODE>
 __device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const GridP &g, long long first,
-                                               long long stride)
+                                               long long stride, bool next)
 {
     int lo[3], hi[3];
-    if (!seed_box(ctl, g, lo, hi)) return;
+    if (!seed_box(ctl, g, lo, hi, next)) return;
     const long long w = hi[0] - lo[0] + 1, h = hi[1] - lo[1] + 1;
     const long long total = w * h * (hi[2] - lo[2] + 1);
+    if (total < (1LL << 31)) {
+        // 32-bit index arithmetic (the 64-bit divisions below are software
+        // routines, a large part of a cell's instructions)
+        const unsigned uw = (unsigned)w, uh = (unsigned)h, ut = (unsigned)total;
+        for (unsigned t = (unsigned)first; t < ut; t += (unsigned)stride) {
+            const unsigned row = t / uw;
+            const int ijk[3] = {lo[0] + (int)(t - row * uw), lo[1] + (int)(row % uh), lo[2] + (int)(row / uh)};
+            const long long c = ijk[0] + (long long)g.n[0] * (ijk[1] + (long long)g.n[1] * ijk[2]);
+            if constexpr (MODE == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c);
+            else if constexpr (MODE == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, ijk, c);
+            else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
+        }
+        return;
+    }
     for (long long t = first; t < total; t += stride) {
         const long long row = t / w;
         const int ijk[3] = {lo[0] + (int)(t - row * w), lo[1] + (int)(row % h), lo[2] + (int)(row / h)};
@@ -668,12 +742,20 @@ __device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const
 }
 
 template <class R, int DIM, int NMAT, int SOLID, int OPT, int MODE>
-__global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, const Ctl *ctl, GridP g)
+// fin_mode != 0: the finalize of the previous step was deferred to this
+// launch (a static body: the seeding needs no result of it but the box,
+// read from rnext); its last block runs it while the others seed.
+__global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, Ctl *ctl, GridP g, int fin_mode)
 {
     pdl_enter();
+    const int nseed = gridDim.x - (fin_mode ? 1 : 0);
+    if (fin_mode && (int)blockIdx.x == nseed) {
+        if (threadIdx.x < 32) finalize_warp(ctl, fin_mode, g.dim, g.dx, false);
+        return;
+    }
     seed_box_cells<R, DIM, NMAT, SOLID, OPT, MODE>(reinterpret_cast<R *>(Uv), reinterpret_cast<R *>(Sv), ctl, g,
                                                    blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                                                   (long long)gridDim.x * blockDim.x);
+                                                   (long long)nseed * blockDim.x, fin_mode != 0);
 }
 
 // Launch shape of k_seed: up to 16 CTAs of 256 threads per SM.
@@ -866,6 +948,9 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
     const bool inside = own && gx < g.n[0] && gy < g.n[1] && gz < g.n[2];
     const R dt = ctl_dt<R>(a.ctl);
     R vr[3] = {ctl_v<R>(a.ctl, 0), ctl_v<R>(a.ctl, 1), ctl_v<R>(a.ctl, 2)};
+    // the rigid box that stage 3 folds starts empty (the seeding before this
+    // stage was its last reader)
+    if (STAGE == 1 && tile_id == 0 && threadIdx.x == 0) ctl_box_reset(a.ctl);
 
     Acc<R> Dacc[L::NVAR];
 #pragma unroll

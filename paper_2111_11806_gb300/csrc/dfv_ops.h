@@ -17,7 +17,9 @@ struct Ops {
     int elem_bytes;
     cudaError_t (*prepare)();
     dim3 (*stage_grid)(const GridP &);
-    cudaError_t (*seed)(const GridP &, void *U, void *scratch, const Ctl *ctl, cudaStream_t);
+    // fin_mode != 0 (stepped probe only): the same launch runs the deferred
+    // finalize of the previous step with that mode
+    cudaError_t (*seed)(const GridP &, void *U, void *scratch, Ctl *ctl, int fin_mode, cudaStream_t);
     cudaError_t (*stage)(int stage, const GridP &, const void *in, const void *un, void *out, Ctl *ctl,
                          double *partials, int want_force, cudaStream_t);
     cudaError_t (*cfl)(const GridP &, const void *U, double *partials, int nblocks, cudaStream_t);
