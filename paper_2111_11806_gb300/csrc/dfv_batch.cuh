@@ -1,7 +1,7 @@
 // dfv_batch.cuh -- many independent 2-D instances (own grid size, body and
 // time step) advanced together: every kernel is a persistent launch over a
 // work list of (instance, tile) items, so one launch per phase serves the whole
-// batch.  The per-tile work is the single-grid stage_tile / seed_cell code.
+// batch.  The per-tile work is the single-grid stage_tile / seeding code.
 #pragma once
 
 #include <algorithm>
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_batch_seed(BatchArgs b)
     R *U = reinterpret_cast<R *>(const_cast<void *>(b.in)) + I.off;
     R *S = reinterpret_cast<R *>(b.out) + I.off;
     seed_box_cells<R, 2, NMAT, false, OPT, MODE>(U, S, I.ctl, I.g,
-                                                 (blockIdx.x % SEED_CTAS) * (long long)blockDim.x + threadIdx.x,
+                                                 (blockIdx.x % SEED_CTAS) * (long long)blockDim.x,
                                                  (long long)SEED_CTAS * blockDim.x, false);
 }
 

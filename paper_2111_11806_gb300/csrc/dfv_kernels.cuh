@@ -450,6 +450,43 @@ __device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R
 // no gradient, or no valid probe point).
 // OPT: bit 0 ELVIRA normals (2-D), bit 1 Riemann-problem variant; each option
 // set is its own kernel so that the plain seeding keeps its small footprint.
+// Executed by a group of SEED_G aligned lanes of one warp for the same cell:
+// every lane forms the normal, lane k tests step k of the probe ladder, the
+// group takes the first valid step, lane m fetches enclosing cell m of the
+// probe point, and lane 0 interpolates (in the order of the cells), reflects
+// and returns the state (the other lanes return false).
+constexpr int SEED_G = 8;
+
+// A band cell: rigid (r > 0.5) with a non-zero central-difference gradient of
+// r (Youngs); r of the cell and of its 2 DIM neighbours in one round of loads.
+template <class R, int DIM, int NMAT, int SOLID>
+__device__ __forceinline__ bool seed_band_test(const R *U, const GridP &g, const int ijk[3], long long c, R &rc,
+                                               R gr[3], R &gn)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    const GridC<R> &gc = gridc<R>(g);
+    const long long P = g.pitch;
+    R rn[3][2];
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        int lo[3] = {ijk[0], ijk[1], ijk[2]}, hi[3] = {ijk[0], ijk[1], ijk[2]};
+        lo[d] = map_idx(ijk[d] - 1, g.n[d], g.periodic[d]);
+        hi[d] = map_idx(ijk[d] + 1, g.n[d], g.periodic[d]);
+        const long long cl = lo[0] + (long long)g.n[0] * (lo[1] + (long long)g.n[1] * lo[2]);
+        const long long ch = hi[0] + (long long)g.n[0] * (hi[1] + (long long)g.n[1] * hi[2]);
+        rn[d][0] = U[L::IR * P + cl];
+        rn[d][1] = U[L::IR * P + ch];
+    }
+    rc = U[L::IR * P + c];
+    gr[0] = gr[1] = gr[2] = R(0);
+    gn = R(0);
+    if (!(rc > R(0.5))) return false;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) gr[d] = (rn[d][1] - rn[d][0]) / (R(2) * gc.dx[d]);
+    gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+    return gn * gc.dxmin > R(1e-10);
+}
+
 template <class R, int DIM, int NMAT, int SOLID, int OPT>
 __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const GridP &g, const int ijk[3], long long c,
                                              R *q)
@@ -457,28 +494,11 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
     using L = Lay<DIM, NMAT, SOLID>;
     const GridC<R> &gc = gridc<R>(g);
     const long long P = g.pitch;
+    const int lane = threadIdx.x & 31, sub = lane & (SEED_G - 1), gbase = lane & ~(SEED_G - 1);
+    const unsigned gm = ((1u << SEED_G) - 1u) << gbase;
     {
-        // r of the cell and of its 2 DIM neighbours in one round of loads
-        // (most cells leave at the first test, but a band cell then needs no
-        // second round trip for its gradient)
-        R rn[3][2];
-#pragma unroll
-        for (int d = 0; d < DIM; d++) {
-            int lo[3] = {ijk[0], ijk[1], ijk[2]}, hi[3] = {ijk[0], ijk[1], ijk[2]};
-            lo[d] = map_idx(ijk[d] - 1, g.n[d], g.periodic[d]);
-            hi[d] = map_idx(ijk[d] + 1, g.n[d], g.periodic[d]);
-            const long long cl = lo[0] + (long long)g.n[0] * (lo[1] + (long long)g.n[1] * lo[2]);
-            const long long ch = hi[0] + (long long)g.n[0] * (hi[1] + (long long)g.n[1] * hi[2]);
-            rn[d][0] = U[L::IR * P + cl];
-            rn[d][1] = U[L::IR * P + ch];
-        }
-        const R rc = U[L::IR * P + c];
-        if (!(rc > R(0.5))) return false;
-        R gr[3] = {R(0), R(0), R(0)};
-#pragma unroll
-        for (int d = 0; d < DIM; d++) gr[d] = (rn[d][1] - rn[d][0]) / (R(2) * gc.dx[d]);
-        const R gn = m_sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-        if (!(gn * gc.dxmin > R(1e-10))) return false;
+        R rc, gr[3], gn;
+        if (!seed_band_test<R, DIM, NMAT, SOLID>(U, g, ijk, c, rc, gr, gn)) return false;
         R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
         if constexpr (DIM == 2 && (OPT & 1)) {
             double blk[9], n2[2];
@@ -495,61 +515,61 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
             nv[1] = (R)n2[1];
             nv[2] = R(0);
         }
-        // Probe steps s = 1.0, 1.5, ..., 4.0 dx_min: the r values of all steps'
-        // enclosing cells are fetched first (independent loads, one memory
-        // round trip), then the first valid step is taken.
+        // Probe steps s = 1.0, 1.5, ..., 4.0 dx_min: lane k of the group tests
+        // step k (its enclosing cells in one round of loads), then the group
+        // takes the first valid step.
         constexpr int NC = 1 << DIM;
         int first = -1;
         unsigned int valid = 0u;
         const bool fixed = g.probe_mode == 1;
         if (!fixed) {
-        // a step is valid when its 2^DIM enclosing cells lie in the grid (or
-        // wrap, in a periodic direction) and all have r < 0.5
-        const bool anyper = g.periodic[0] || (DIM >= 2 && g.periodic[1]) || (DIM >= 3 && g.periodic[2]);
-        const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
-#pragma unroll
-        for (int step = 0; step < 7; step++) {
-            const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
-            int base[3] = {0, 0, 0};
-#pragma unroll
-            for (int d = 0; d < DIM; d++) {
-                const R xp = gc.lo[d] + ((R)ijk[d] + R(0.5)) * gc.dx[d] + sd * nv[d];
-                const R fi = (xp - gc.lo[d]) / gc.dx[d] - R(0.5);
-                base[d] = (int)floor(fi);
-            }
-            bool ok = true;
+            // a step is valid when its 2^DIM enclosing cells lie in the grid
+            // (or wrap, in a periodic direction) and all have r < 0.5
+            bool ok = sub < 7;
             R rmax = R(0);
-            if (!anyper) {
-                // corner offsets from the lowest corner; nothing is loaded for
-                // a step whose cells leave the grid
+            if (ok) {
+                const int step = sub;
+                const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
+                int base[3] = {0, 0, 0};
 #pragma unroll
-                for (int d = 0; d < DIM; d++) ok = ok && base[d] >= 0 && base[d] <= g.n[d] - 2;
-                if (ok) {
-                    const long long c0 = base[0] + sy * base[1] + sz * base[2];
+                for (int d = 0; d < DIM; d++) {
+                    const R xp = gc.lo[d] + ((R)ijk[d] + R(0.5)) * gc.dx[d] + sd * nv[d];
+                    const R fi = (xp - gc.lo[d]) / gc.dx[d] - R(0.5);
+                    base[d] = (int)floor(fi);
+                }
+                const bool anyper = g.periodic[0] || (DIM >= 2 && g.periodic[1]) || (DIM >= 3 && g.periodic[2]);
+                if (!anyper) {
+                    // nothing is loaded for a step whose cells leave the grid
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) ok = ok && base[d] >= 0 && base[d] <= g.n[d] - 2;
+                    if (ok) {
+                        const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+                        const long long c0 = base[0] + sy * base[1] + sz * base[2];
+#pragma unroll
+                        for (int m = 0; m < NC; m++) {
+                            const long long cm = c0 + (m & 1) + ((m >> 1) & 1) * sy + ((m >> 2) & 1) * sz;
+                            const R rv = U[L::IR * P + cm];
+                            rmax = (rv < R(0.5)) ? rmax : R(1);
+                        }
+                    }
+                } else {
 #pragma unroll
                     for (int m = 0; m < NC; m++) {
-                        const long long cm = c0 + (m & 1) + ((m >> 1) & 1) * sy + ((m >> 2) & 1) * sz;
-                        const R rv = U[L::IR * P + cm];
+                        int ci[3] = {0, 0, 0};
+#pragma unroll
+                        for (int d = 0; d < DIM; d++) {
+                            int ii = base[d] + ((m >> d) & 1);
+                            if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
+                            else if (ii < 0 || ii > g.n[d] - 1) ok = false;
+                            ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
+                        }
+                        const R rv =
+                            U[L::IR * P + ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2])];
                         rmax = (rv < R(0.5)) ? rmax : R(1);
                     }
                 }
-            } else {
-#pragma unroll
-                for (int m = 0; m < NC; m++) {
-                    int ci[3] = {0, 0, 0};
-#pragma unroll
-                    for (int d = 0; d < DIM; d++) {
-                        int ii = base[d] + ((m >> d) & 1);
-                        if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
-                        else if (ii < 0 || ii > g.n[d] - 1) ok = false;
-                        ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
-                    }
-                    const R rv = U[L::IR * P + ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2])];
-                    rmax = (rv < R(0.5)) ? rmax : R(1);
-                }
             }
-            if (ok && rmax == R(0)) valid |= 1u << step;
-        }
+            valid = (__ballot_sync(gm, ok && rmax == R(0)) >> gbase) & 0x7fu;
         }
         if (!fixed && !valid) return false;
         first = fixed ? 1 : __ffs(valid) - 1;     // step 1 of the ladder is the fixed 1.5 dx_min
@@ -569,12 +589,13 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
                 base[d] = (int)fl;
                 fr[d] = fi - fl;
             }
+            // lane m: enclosing cell m and its weight
+            R wt = R(1), w[L::NVAR];
 #pragma unroll
-            for (int v = 0; v < L::NVAR; v++) wi[v] = R(0);
-#pragma unroll
-            for (int m = 0; m < NC; m++) {
+            for (int v = 0; v < L::NVAR; v++) w[v] = R(0);
+            if (sub < NC) {
+                const int m = sub;
                 int ci[3] = {0, 0, 0};
-                R wt = R(1);
 #pragma unroll
                 for (int d = 0; d < DIM; d++) {
                     const int bit = (m >> d) & 1;
@@ -582,14 +603,22 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
                     wt *= bit ? fr[d] : (R(1) - fr[d]);
                 }
                 const long long cc = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
-                R q[L::NVAR], w[L::NVAR];
+                R qc[L::NVAR];
 #pragma unroll
-                for (int v = 0; v < L::NVAR; v++) q[v] = U[v * P + cc];
-                cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
+                for (int v = 0; v < L::NVAR; v++) qc[v] = U[v * P + cc];
+                cons_to_prim<R, DIM, NMAT, SOLID>(g, qc, w);
+            }
+            // lane 0 sums them in the order of the cells
 #pragma unroll
-                for (int v = 0; v < L::NVAR; v++) wi[v] += wt * w[v];
+            for (int v = 0; v < L::NVAR; v++) wi[v] = R(0);
+#pragma unroll
+            for (int m = 0; m < NC; m++) {
+                const R wm = __shfl_sync(gm, wt, gbase + m);
+#pragma unroll
+                for (int v = 0; v < L::NVAR; v++) wi[v] += wm * __shfl_sync(gm, w[v], gbase + m);
             }
         }
+        if (sub != 0) return false;
         R wr[L::NVAR];      // the interpolated state, kept for the Riemann variant
         if constexpr ((OPT & 2) != 0) {
 #pragma unroll
@@ -644,36 +673,9 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
     }
 }
 
-template <class R, int DIM, int NMAT, int SOLID, int OPT>
-__device__ __forceinline__ void seed_cell(R *U, const Ctl *ctl, const GridP &g, const int ijk[3], long long c)
-{
-    using L = Lay<DIM, NMAT, SOLID>;
-    R q[L::NVAR];
-    if (!seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c, q)) return;
-#pragma unroll
-    for (int v = 0; v < L::NVAR; v++)
-        if (v != L::IR) U[v * g.pitch + c] = q[v];
-}
-
 // Seeding from the step-start state when the probe may read rigid cells
-// (fixed probe): the seeded state of cell c goes to the scratch planes S,
+// (fixed probe): the seeded state of a cell goes to the scratch planes S,
 // whose r plane flags it (1 seeded, 0 not); seed_apply then copies it into U.
-template <class R, int DIM, int NMAT, int SOLID, int OPT>
-__device__ __forceinline__ void seed_cell_to(const R *U, R *S, const Ctl *ctl, const GridP &g, const int ijk[3],
-                                             long long c)
-{
-    using L = Lay<DIM, NMAT, SOLID>;
-    if (!(U[L::IR * g.pitch + c] > R(0.5))) return;
-    R q[L::NVAR];
-    const bool ok = seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c, q);
-    if (ok) {
-#pragma unroll
-        for (int v = 0; v < L::NVAR; v++)
-            if (v != L::IR) S[v * g.pitch + c] = q[v];
-    }
-    S[L::IR * g.pitch + c] = ok ? R(1) : R(0);
-}
-
 template <class R, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void seed_apply(R *U, const R *S, const GridP &g, long long c)
 {
@@ -709,42 +711,97 @@ __device__ __forceinline__ bool seed_box(const Ctl *ctl, const GridP &g, int lo[
 }
 
 // Threads stride over the cells of the rigid box, x fastest.
+// Cell t of the box (x fastest) as grid indices and linear index.
+__device__ __forceinline__ long long seed_box_cell(const GridP &g, const int lo[3], long long w, long long h,
+                                                   bool small, long long t, int ijk[3])
+{
+    if (small) {
+        // 32-bit index arithmetic (64-bit divisions are software routines)
+        const unsigned ut = (unsigned)t, uw = (unsigned)w, uh = (unsigned)h, row = ut / uw;
+        ijk[0] = lo[0] + (int)(ut - row * uw);
+        ijk[1] = lo[1] + (int)(row % uh);
+        ijk[2] = lo[2] + (int)(row / uh);
+    } else {
+        const long long row = t / w;
+        ijk[0] = lo[0] + (int)(t - row * w);
+        ijk[1] = lo[1] + (int)(row % h);
+        ijk[2] = lo[2] + (int)(row / h);
+    }
+    return ijk[0] + (long long)g.n[0] * (ijk[1] + (long long)g.n[1] * ijk[2]);
+}
+
+// The box cells, by whole blocks of at most 256 threads: block_first is the
+// block's first cell, stride the cells all blocks cover in one round.  Each
+// thread tests one cell; the band cells go to a queue in shared memory and
+// are seeded by groups of SEED_G lanes (seed_compute), lane 0 storing the
+// state (MODE 0: into U, except r; MODE 1: into S with the flag).  MODE 2
+// copies S into U, one cell per thread.
 template <class R, int DIM, int NMAT, int SOLID, int OPT, int MODE>
-__device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const GridP &g, long long first,
+__device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const GridP &g, long long block_first,
                                                long long stride, bool next)
 {
+    using L = Lay<DIM, NMAT, SOLID>;
+    const long long P = g.pitch;
     int lo[3], hi[3];
     if (!seed_box(ctl, g, lo, hi, next)) return;
     const long long w = hi[0] - lo[0] + 1, h = hi[1] - lo[1] + 1;
     const long long total = w * h * (hi[2] - lo[2] + 1);
-    if (total < (1LL << 31)) {
-        // 32-bit index arithmetic (the 64-bit divisions below are software
-        // routines, a large part of a cell's instructions)
-        const unsigned uw = (unsigned)w, uh = (unsigned)h, ut = (unsigned)total;
-        for (unsigned t = (unsigned)first; t < ut; t += (unsigned)stride) {
-            const unsigned row = t / uw;
-            const int ijk[3] = {lo[0] + (int)(t - row * uw), lo[1] + (int)(row % uh), lo[2] + (int)(row / uh)};
-            const long long c = ijk[0] + (long long)g.n[0] * (ijk[1] + (long long)g.n[1] * ijk[2]);
-            if constexpr (MODE == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c);
-            else if constexpr (MODE == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, ijk, c);
-            else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
+    const bool small = total + stride < (1LL << 31);
+    if constexpr (MODE == 2) {
+        for (long long t = block_first + threadIdx.x; t < total; t += stride) {
+            int ijk[3];
+            seed_apply<R, DIM, NMAT, SOLID>(U, S, g, seed_box_cell(g, lo, w, h, small, t, ijk));
         }
         return;
     }
-    for (long long t = first; t < total; t += stride) {
-        const long long row = t / w;
-        const int ijk[3] = {lo[0] + (int)(t - row * w), lo[1] + (int)(row % h), lo[2] + (int)(row / h)};
-        const long long c = ijk[0] + (long long)g.n[0] * (ijk[1] + (long long)g.n[1] * ijk[2]);
-        if constexpr (MODE == 0) seed_cell<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c);
-        else if constexpr (MODE == 1) seed_cell_to<R, DIM, NMAT, SOLID, OPT>(U, S, ctl, g, ijk, c);
-        else seed_apply<R, DIM, NMAT, SOLID>(U, S, g, c);
+    __shared__ int s_n;
+    __shared__ unsigned short s_q[256];
+    const int sub = threadIdx.x & (SEED_G - 1);
+    for (long long b0 = block_first; b0 < total; b0 += stride) {     // the same rounds for the whole block
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        const long long t = b0 + threadIdx.x;
+        if (t < total) {
+            int ijk[3];
+            const long long c = seed_box_cell(g, lo, w, h, small, t, ijk);
+            R rc, gr[3], gn;
+            if (seed_band_test<R, DIM, NMAT, SOLID>(U, g, ijk, c, rc, gr, gn))
+                s_q[atomicAdd(&s_n, 1)] = (unsigned short)threadIdx.x;
+            else if (MODE == 1 && rc > R(0.5))
+                S[L::IR * P + c] = R(0);
+        }
+        __syncthreads();
+        const int n = s_n;
+        for (int k = threadIdx.x / SEED_G; k < n; k += blockDim.x / SEED_G) {
+            int ijk[3];
+            const long long c = seed_box_cell(g, lo, w, h, small, b0 + s_q[k], ijk);
+            R q[L::NVAR];
+            const bool ok = seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c, q);
+            if (sub == 0) {
+                if constexpr (MODE == 0) {
+                    if (ok) {
+#pragma unroll
+                        for (int v = 0; v < L::NVAR; v++)
+                            if (v != L::IR) U[v * P + c] = q[v];
+                    }
+                } else {
+                    if (ok) {
+#pragma unroll
+                        for (int v = 0; v < L::NVAR; v++)
+                            if (v != L::IR) S[v * P + c] = q[v];
+                    }
+                    S[L::IR * P + c] = ok ? R(1) : R(0);
+                }
+            }
+        }
+        __syncthreads();     // the queue is refilled in the next round
     }
 }
 
-template <class R, int DIM, int NMAT, int SOLID, int OPT, int MODE>
 // fin_mode != 0: the finalize of the previous step was deferred to this
 // launch (a static body: the seeding needs no result of it but the box,
 // read from rnext); its last block runs it while the others seed.
+template <class R, int DIM, int NMAT, int SOLID, int OPT, int MODE>
 __global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, Ctl *ctl, GridP g, int fin_mode)
 {
     pdl_enter();
@@ -754,8 +811,8 @@ __global__ void __launch_bounds__(256) k_seed(void *Uv, void *Sv, Ctl *ctl, Grid
         return;
     }
     seed_box_cells<R, DIM, NMAT, SOLID, OPT, MODE>(reinterpret_cast<R *>(Uv), reinterpret_cast<R *>(Sv), ctl, g,
-                                                   blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                                                   (long long)nseed * blockDim.x, fin_mode != 0);
+                                                   blockIdx.x * (long long)blockDim.x, (long long)nseed * blockDim.x,
+                                                   fin_mode != 0);
 }
 
 // Launch shape of k_seed: up to 16 CTAs of 256 threads per SM.
