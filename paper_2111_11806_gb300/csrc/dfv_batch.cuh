@@ -51,8 +51,11 @@ __device__ __forceinline__ void load_inst(const BatchInst *src, BatchInst *dst)
     for (int k = threadIdx.x; k < NW; k += blockDim.x) d[k] = s[k];
 }
 
+// Register bound: four CTAs per SM for the FP32 single-material form (56
+// registers, no spills), two otherwise.
 template <class R, int NMAT, int STAGE>
-__global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_stage(BatchArgs b)
+__global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, (sizeof(R) == 4 && NMAT == 1) ? 4 : 2)
+    k_batch_stage(BatchArgs b)
 {
     pdl_enter();
     __shared__ BatchInst s_inst;
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, 2) k_batch_s
 // first stage 3); the instance record is read through the cache.
 // MODE 0: in place; 1: seeded states into the scratch planes b.out; 2: the
 // scratch into U (the fixed probe reads the step-start state only).
-constexpr int SEED_CTAS = 8;
+constexpr int SEED_CTAS = 32;
 
 template <class R, int NMAT, int MODE, int OPT>
 __global__ void __launch_bounds__(256) k_batch_seed(BatchArgs b)

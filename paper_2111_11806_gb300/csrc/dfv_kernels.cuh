@@ -1148,8 +1148,17 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
     }
 }
 
+// Register bound: four CTAs per SM for the 2-D FP32 single-material fluid
+// (56 registers without spills; stage 3 would otherwise take 62 and three).
+template <class R, int DIM, int NMAT, int SOLID>
+constexpr int stage_min_ctas()
+{
+    return (DIM == 2 && sizeof(R) == 4 && NMAT == 1 && SOLID == 0) ? 4 : 1;
+}
+
 template <class R, int DIM, int NMAT, int SOLID, int STAGE>
-__global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS) k_stage(StageArgs a, GridP g)
+__global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS, stage_min_ctas<R, DIM, NMAT, SOLID>())
+    k_stage(StageArgs a, GridP g)
 {
     pdl_enter();
     const long long tile = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
