@@ -255,12 +255,13 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false, int 
     }
     DFV_CU(g, g->ops->seed(g->g, g->U, g->U1, g->ctl, fin_in, g->stream), "k_seed");
     if (rec) DFV_CU(g, cudaEventRecord(ev[1], g->stream), "event");
-    DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, g->stream),
+    DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, fin_in != 0 ? 1 : 0,
+                            g->stream),
            "k_stage<1>");
     if (rec) DFV_CU(g, cudaEventRecord(ev[2], g->stream), "event");
-    DFV_CU(g, g->ops->stage(2, g->g, g->U1, g->U, g->U3, g->ctl, g->partials, 0, g->stream), "k_stage<2>");
+    DFV_CU(g, g->ops->stage(2, g->g, g->U1, g->U, g->U3, g->ctl, g->partials, 0, 0, g->stream), "k_stage<2>");
     if (rec) DFV_CU(g, cudaEventRecord(ev[3], g->stream), "event");
-    DFV_CU(g, g->ops->stage(3, g->g, g->U3, g->U, g->U, g->ctl, g->partials, 0, g->stream), "k_stage<3>");
+    DFV_CU(g, g->ops->stage(3, g->g, g->U3, g->U, g->U, g->ctl, g->partials, 0, 0, g->stream), "k_stage<3>");
     if (rec) DFV_CU(g, cudaEventRecord(ev[4], g->stream), "event");
     // one block: CFL maximum (folded by the stage-3 tiles), force sum, body
     // update, next dt

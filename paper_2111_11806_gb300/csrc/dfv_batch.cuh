@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, (sizeof(R) =
         a.ctl = I.ctl;
         a.partials = b.partials + 4 * I.part0;
         a.want_force = 0;
+        a.early = 0;
+        a.next = 0;
         stage_tile<R, 2, NMAT, false, STAGE>(I.g, a, w.y % I.tiles_x, w.y / I.tiles_x, 0, w.y, I.ntiles);
     }
 }

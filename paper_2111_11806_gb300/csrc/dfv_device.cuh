@@ -185,6 +185,13 @@ template <>
 __device__ __forceinline__ double ctl_v<double>(const Ctl *c, int d) { return c->v[d]; }
 template <>
 __device__ __forceinline__ float ctl_v<float>(const Ctl *c, int d) { return c->vf[d]; }
+// the same read from L2 (bypassing a possibly stale L1 line)
+template <class T>
+__device__ __forceinline__ T ctl_v_cg(const Ctl *c, int d);
+template <>
+__device__ __forceinline__ double ctl_v_cg<double>(const Ctl *c, int d) { return __ldcg(&c->v[d]); }
+template <>
+__device__ __forceinline__ float ctl_v_cg<float>(const Ctl *c, int d) { return __ldcg(&c->vf[d]); }
 
 __device__ __forceinline__ void ctl_set_dt(Ctl *c, double dt)
 {
@@ -210,6 +217,11 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+
+// The two halves, for a kernel that does work not depending on its
+// predecessor before it waits.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 __host__ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,

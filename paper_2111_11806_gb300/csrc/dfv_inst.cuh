@@ -71,8 +71,28 @@ struct Impl {
         return launch_pdl(k_stage<R, DIM, NMAT, SOLID, S>, stage_grid(g), dim3(TL::THREADS), smem, st, a, g);
     }
 
+    // CTAs of the stage-1 kernel resident at once on the device (the first
+    // wave), looked up once
+    static int first_wave()
+    {
+        static int n = -1;
+        if (n < 0) {
+            int dev = 0, sms = 0, per = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stage<R, DIM, NMAT, SOLID, 1>, TL::THREADS,
+                                                              smem) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return 0;
+            }
+            n = sms * per;
+        }
+        return n;
+    }
+
+    // next: the seeding before stage 1 reads its box from ctl->rnext
     static cudaError_t stage(int s, const GridP &g, const void *in, const void *un, void *out, Ctl *ctl,
-                             double *partials, int want_force, cudaStream_t st)
+                             double *partials, int want_force, int next, cudaStream_t st)
     {
         StageArgs a;
         a.in = in;
@@ -81,6 +101,8 @@ struct Impl {
         a.ctl = ctl;
         a.partials = partials;
         a.want_force = want_force;
+        a.early = s == 1 ? first_wave() : 0;
+        a.next = next;
         if (s == 1) return stage_s<1>(g, a, st);
         if (s == 2) return stage_s<2>(g, a, st);
         return stage_s<3>(g, a, st);

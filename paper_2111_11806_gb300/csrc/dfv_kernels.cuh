@@ -838,7 +838,43 @@ struct StageArgs {
     Ctl *ctl;
     double *partials;   // 4 doubles per block
     int want_force;
+    int early;          // stage 1 after the seeding launch: of the first `early` tiles (the first wave
+                        // of CTAs), those that read no cell of the seeding box load and compute their
+                        // faces before waiting for it
+    int next;           // ... the seeding box is ctl->rnext (its finalize runs in the seeding launch)
 };
+
+// Whether a tile's loaded cells (the tile and its halo of 3, after boundary
+// mapping) may include a cell of the seeding box, i.e. a cell the seeding
+// of this step writes.  Conservative: a halo that wraps (periodic) or is
+// mirrored (wall) counts as touching; a clamped (outflow) halo is clamped.
+// Read before the seeding launch has finished: the box words come from L2
+// (written by an earlier launch, complete before this one started).
+template <int DIM, int W>
+__device__ __forceinline__ bool tile_touches_box(const GridP &g, const Ctl *ctl, int ox, int oy, int oz, bool next)
+{
+    using TL = Tile<DIM, W>;
+    using B = Box<DIM, W>;
+    const bool valid = next || __ldcg(&ctl->rbox_valid) != 0;
+    if (!valid) return true;
+    const int *box = next ? ctl->rnext : ctl->rbox;
+    const int o[3] = {ox, oy, oz}, t[3] = {TL::TX, TL::TY, TL::TZ}, h[3] = {B::HX, B::HY, B::HZ};
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        const int lo = __ldcg(&box[d]), hi = __ldcg(&box[3 + d]);
+        int a = o[d] - h[d], b = o[d] + t[d] + h[d] - 1;
+        if (a < 0) {
+            if (g.periodic[d] || g.wall[d][0]) return true;
+            a = 0;
+        }
+        if (b > g.n[d] - 1) {
+            if (g.periodic[d] || g.wall[d][1]) return true;
+            b = g.n[d] - 1;
+        }
+        if (b < lo || a > hi) return false;
+    }
+    return true;
+}
 
 // Fluxes of every face of direction D of the tile into sF (no barrier).
 template <class R, int DIM, int NMAT, int SOLID, int D>
@@ -961,6 +997,14 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
     R *out = reinterpret_cast<R *>(a.out);
     const long long P = g.pitch;
     const int ox = tbx * TL::TX, oy = tby * TL::TY, oz = tbz * TL::TZ;
+    // a stage-1 tile whose loaded cells miss the seeding box runs up to its
+    // update before waiting for the seeding launch (its reads before the
+    // wait bypass L1); the others wait first
+    // (only the first wave: later tiles start after the seeding anyway, and
+    // their loads keep the L1 hits of the halo shared with earlier tiles)
+    const bool early = STAGE == 1 && tile_id < a.early &&
+                       !tile_touches_box<DIM, (int)sizeof(R)>(g, a.ctl, ox, oy, oz, a.next);
+    if (STAGE == 1 && a.early > 0 && !early) pdl_wait();
 
     // 1. primitives of the tile and its halo (the corner regions are unused);
     // a tile whose halo lies inside the grid needs no boundary mapping
@@ -981,8 +1025,13 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
         }
         const long long c = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
         R q[L::NVAR], w[L::NVAR];
+        if (early) {
 #pragma unroll
-        for (int v = 0; v < L::NVAR; v++) q[v] = in[v * P + c];
+            for (int v = 0; v < L::NVAR; v++) q[v] = __ldcg(&in[v * P + c]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < L::NVAR; v++) q[v] = in[v * P + c];
+        }
         cons_to_prim<R, DIM, NMAT, SOLID>(g, q, w);
         // mirror image behind a reflective wall: u_d and the stretch
         // components with exactly one index d change sign
@@ -1003,11 +1052,14 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
     const int lx = threadIdx.x % TL::TX, ly = (threadIdx.x / TL::TX) % TL::TY, lz = threadIdx.x / (TL::TX * TL::TY);
     const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
     const bool inside = own && gx < g.n[0] && gy < g.n[1] && gz < g.n[2];
-    const R dt = ctl_dt<R>(a.ctl);
-    R vr[3] = {ctl_v<R>(a.ctl, 0), ctl_v<R>(a.ctl, 1), ctl_v<R>(a.ctl, 2)};
-    // the rigid box that stage 3 folds starts empty (the seeding before this
-    // stage was its last reader)
-    if (STAGE == 1 && tile_id == 0 && threadIdx.x == 0) ctl_box_reset(a.ctl);
+    // the body velocity: set before the seeding launch (a deferred
+    // finalize, the only kind that launch runs, leaves it unchanged)
+    R vr[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) vr[d] = early ? ctl_v_cg<R>(a.ctl, d) : ctl_v<R>(a.ctl, d);
+    // the rigid box that stage 3 folds starts empty (the seeding and stage 1,
+    // which read it, have finished)
+    if (STAGE == 2 && tile_id == 0 && threadIdx.x == 0) ctl_box_reset(a.ctl);
 
     Acc<R> Dacc[L::NVAR];
 #pragma unroll
@@ -1036,6 +1088,8 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
         }
     }
 
+    if (early) pdl_wait();   // Δt and the seeded cells of U^n are final from here on
+    const R dt = ctl_dt<R>(a.ctl);
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     R smax_cell = R(0);
     bool rigid_new = false;
@@ -1160,7 +1214,9 @@ template <class R, int DIM, int NMAT, int SOLID, int STAGE>
 __global__ void __launch_bounds__(Tile<DIM, (int)sizeof(R)>::THREADS, stage_min_ctas<R, DIM, NMAT, SOLID>())
     k_stage(StageArgs a, GridP g)
 {
-    pdl_enter();
+    // stage 1 after the seeding waits inside stage_tile (early tiles late)
+    if (STAGE == 1 && a.early > 0) pdl_release();
+    else pdl_enter();
     const long long tile = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     const long long nt = (long long)gridDim.x * gridDim.y * gridDim.z;
     stage_tile<R, DIM, NMAT, SOLID, STAGE>(g, a, blockIdx.x, blockIdx.y, blockIdx.z, tile, nt);

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(ZGeo::THREADS, 2) k_stage_z(StageArgs a, GridP
     const R ca = STAGE == 2 ? R(0.75) : (STAGE == 3 ? R(1.0 / 3.0) : R(0));
     const R cb = STAGE == 2 ? R(0.25) : (STAGE == 3 ? R(2.0 / 3.0) : R(1));
     // the rigid box that stage 3 folds starts empty
-    if (STAGE == 1 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+    if (STAGE == 2 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
         ctl_box_reset(a.ctl);
 
     // planes z0-3 .. z0+2, plane z0+3 into registers, then the z face below

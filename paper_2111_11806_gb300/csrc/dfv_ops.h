@@ -20,8 +20,9 @@ struct Ops {
     // fin_mode != 0 (stepped probe only): the same launch runs the deferred
     // finalize of the previous step with that mode
     cudaError_t (*seed)(const GridP &, void *U, void *scratch, Ctl *ctl, int fin_mode, cudaStream_t);
+    // next: the seeding before this stage 1 took its box from ctl->rnext
     cudaError_t (*stage)(int stage, const GridP &, const void *in, const void *un, void *out, Ctl *ctl,
-                         double *partials, int want_force, cudaStream_t);
+                         double *partials, int want_force, int next, cudaStream_t);
     cudaError_t (*cfl)(const GridP &, const void *U, double *partials, int nblocks, cudaStream_t);
     cudaError_t (*prim_to_cons)(const GridP &, const double *prim, long long ppitch, void *U, cudaStream_t);
     cudaError_t (*cons_to_prim)(const GridP &, const void *U, double *prim, long long ppitch, cudaStream_t);
