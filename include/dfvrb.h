@@ -170,7 +170,12 @@ dfv_status dfv_step(dfv_grid *g, double dt);
  * (clipped to land on t_end when t_end > 0), all launches on the stream with
  * no host synchronisation; the sequence of one step is captured once into a
  * CUDA graph and replayed.  *t_out (optional) receives the simulated time
- * (synchronises). */
+ * (synchronises).  For a static body with the stepped probe, the end-of-step
+ * update of the control block (time, next dt, rigid box) of each step runs in
+ * the seeding launch of the next step, and that of the last step when a later
+ * call needs it (dfv_run with a new cfl / t_end or with t_out, dfv_step,
+ * dfv_compute_dt, dfv_get_body, dfv_set_body, dfv_set_fields, dfv_check):
+ * results are identical, a step is four launches instead of five. */
 dfv_status dfv_run(dfv_grid *g, int steps, double cfl, double t_end, double *t_out);
 
 /* Synchronise the stream (waiting at most timeout_ms, <= 0: no limit) and
@@ -181,8 +186,8 @@ dfv_status dfv_check(dfv_grid *g, int timeout_ms);
  * stream around each launch.  enable = 1 clears the record and starts
  * recording; enable = 0 stops, synchronises the stream and returns in
  * ms_out[0..4] the summed device time of the seeding, stage-1, stage-2 and
- * stage-3 launches and of the finalize (0: it runs in the last block of stage
- * 3), and in *steps_out the number of recorded
+ * stage-3 launches and of the finalize (about 0 when it runs in the next
+ * step's seeding launch), and in *steps_out the number of recorded
  * steps (either output may be NULL).  While recording, dfv_run launches the
  * kernels of each step directly instead of replaying a graph. */
 dfv_status dfv_profile(dfv_grid *g, int enable, double ms_out[5], long long *steps_out);

@@ -1,5 +1,7 @@
 // dfv_kernels.cuh -- the kernels of one time step (arXiv:2111.11806, Sec. 3):
 //   k_seed      rigid interface seeding (Sec. 3.2), in place, band cells only
+//               (queued per block, seeded by groups of 8 lanes); optionally
+//               with the previous step's finalize in one extra block
 //   k_stage<S>  one SSP-RK3 stage (Sec. 3.1): halo-3 tile of primitives in
 //               shared memory, per-face MUSCL-BVD-THINC + HLLC, divergence,
 //               non-conservative terms, rigid mask, RK combination; stage 1
@@ -7,8 +9,9 @@
 //               return and reduces the CFL wave speed of the new state
 //   k_cfl       CFL wave-speed reduction of a stored state
 //   k_finalize  one block: deterministic sums of the per-block partials,
-//               body update, next dt
+//               body update, next dt (k_finalize_lite: one warp, no partials)
 //   k_prim_to_cons / k_cons_to_prim / k_cons_to_f64   field conversion
+// The 3-D FP32 single-material stages march along z instead (dfv_kernels_z.cuh).
 #pragma once
 
 #include "dfv_device.cuh"
