@@ -1206,11 +1206,13 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
 }
 
 // Register bound: four CTAs per SM for the 2-D FP32 single-material fluid
-// (56 registers without spills; stage 3 would otherwise take 62 and three).
+// (56 registers without spills; stage 3 would otherwise take 62 and three),
+// two for the other 2-D forms (which would otherwise take up to 138
+// registers and run one 9-warp CTA per SM).
 template <class R, int DIM, int NMAT, int SOLID>
 constexpr int stage_min_ctas()
 {
-    return (DIM == 2 && sizeof(R) == 4 && NMAT == 1 && SOLID == 0) ? 4 : 1;
+    return DIM != 2 ? 1 : ((sizeof(R) == 4 && NMAT == 1 && SOLID == 0) ? 4 : 2);
 }
 
 template <class R, int DIM, int NMAT, int SOLID, int STAGE>
