@@ -47,6 +47,8 @@ struct Impl {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_stage<R, DIM, NMAT, SOLID, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
+        // the first-wave size is looked up here, outside any stream capture
+        if (e == cudaSuccess) (void)first_wave();
         if constexpr (ZM) {
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_stage_z<R, NMAT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
