@@ -491,8 +491,10 @@ __device__ __forceinline__ bool seed_band_test(const R *U, const GridP &g, const
 }
 
 template <class R, int DIM, int NMAT, int SOLID, int OPT>
+// rc, gr, gn: r of the band cell, its central-difference gradient and the
+// gradient's norm (seed_band_test, true for this cell).
 __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const GridP &g, const int ijk[3], long long c,
-                                             R *q)
+                                             R rc, const R gr[3], R gn, R *q)
 {
     using L = Lay<DIM, NMAT, SOLID>;
     const GridC<R> &gc = gridc<R>(g);
@@ -500,8 +502,6 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
     const int lane = threadIdx.x & 31, sub = lane & (SEED_G - 1), gbase = lane & ~(SEED_G - 1);
     const unsigned gm = ((1u << SEED_G) - 1u) << gbase;
     {
-        R rc, gr[3], gn;
-        if (!seed_band_test<R, DIM, NMAT, SOLID>(U, g, ijk, c, rc, gr, gn)) return false;
         R nv[3] = {-gr[0] / gn, -gr[1] / gn, -gr[2] / gn};
         if constexpr (DIM == 2 && (OPT & 1)) {
             double blk[9], n2[2];
@@ -757,8 +757,11 @@ __device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const
         }
         return;
     }
+    // the queue: thread index of a band cell in this round, with its r,
+    // gradient and gradient norm from the test
     __shared__ int s_n;
     __shared__ unsigned short s_q[256];
+    __shared__ R s_b[5][256];
     const int sub = threadIdx.x & (SEED_G - 1);
     for (long long b0 = block_first; b0 < total; b0 += stride) {     // the same rounds for the whole block
         if (threadIdx.x == 0) s_n = 0;
@@ -768,9 +771,15 @@ __device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const
             int ijk[3];
             const long long c = seed_box_cell(g, lo, w, h, small, t, ijk);
             R rc, gr[3], gn;
-            if (seed_band_test<R, DIM, NMAT, SOLID>(U, g, ijk, c, rc, gr, gn))
-                s_q[atomicAdd(&s_n, 1)] = (unsigned short)threadIdx.x;
-            else if (MODE == 1 && rc > R(0.5))
+            if (seed_band_test<R, DIM, NMAT, SOLID>(U, g, ijk, c, rc, gr, gn)) {
+                const int k = atomicAdd(&s_n, 1);
+                s_q[k] = (unsigned short)threadIdx.x;
+                s_b[0][k] = rc;
+                s_b[1][k] = gr[0];
+                s_b[2][k] = gr[1];
+                s_b[3][k] = gr[2];
+                s_b[4][k] = gn;
+            } else if (MODE == 1 && rc > R(0.5))
                 S[L::IR * P + c] = R(0);
         }
         __syncthreads();
@@ -778,8 +787,9 @@ __device__ __forceinline__ void seed_box_cells(R *U, R *S, const Ctl *ctl, const
         for (int k = threadIdx.x / SEED_G; k < n; k += blockDim.x / SEED_G) {
             int ijk[3];
             const long long c = seed_box_cell(g, lo, w, h, small, b0 + s_q[k], ijk);
+            const R gr[3] = {s_b[1][k], s_b[2][k], s_b[3][k]};
             R q[L::NVAR];
-            const bool ok = seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c, q);
+            const bool ok = seed_compute<R, DIM, NMAT, SOLID, OPT>(U, ctl, g, ijk, c, s_b[0][k], gr, s_b[4][k], q);
             if (sub == 0) {
                 if constexpr (MODE == 0) {
                     if (ok) {
