@@ -51,10 +51,11 @@ __device__ __forceinline__ void load_inst(const BatchInst *src, BatchInst *dst)
     for (int k = threadIdx.x; k < NW; k += blockDim.x) d[k] = s[k];
 }
 
-// Register bound: four CTAs per SM for the FP32 single-material form (56
-// registers, no spills), two otherwise.
+// Register bound: five CTAs per SM for the FP32 single-material form (40
+// registers, a few dozen bytes of spills; 1 % faster than four on the
+// 256-ellipse batch), two otherwise.
 template <class R, int NMAT, int STAGE>
-__global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, (sizeof(R) == 4 && NMAT == 1) ? 4 : 2)
+__global__ void __launch_bounds__(Tile<2, (int)sizeof(R)>::THREADS, (sizeof(R) == 4 && NMAT == 1) ? 5 : 2)
     k_batch_stage(BatchArgs b)
 {
     pdl_enter();
