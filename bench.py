@@ -1,26 +1,41 @@
 #!/usr/bin/env python
 """Benchmark of the diffuse rigid-body finite-volume update (arXiv:2111.11806)
-on GB300: cell-updates/s of the FP32 bulk form against the plain FP64 form,
-with the HBM roofline fraction of the dominant kernel (the SSP-RK3 stage).
+on GB300, in the metric's own terms: cell-updates/s of the FP32 and batched
+forms against the plain FP64 form, at a stated L1 error against the FP64
+oracle, as a fraction of the HBM roofline.
 
-Workload: 2-D Mach 3 shock over a static rigid cylinder, 512 x 512 cells, air,
-CFL 0.8 (the metric's quoted configuration).  One benchmark step = one solver
-time step (seeding, three RK stages, CFL and force reductions).  The state
-(5.2 MB in FP32) fits in L2, so L2 is flushed (a 256 MiB write) before every
-timed step and only the step itself is inside its CUDA-event window.
+Headline workload (the batched form): 256 independent 2-D shock-over-rigid-
+ellipse instances, grid sizes drawn from {128,192,256,384,512}^2 (about 27 M
+cells, 0.54 GB per FP32 state copy, larger than the 129 MB L2, so no flush is
+needed), Mach U[1.5,3], FP32, advanced by one persistent launch per phase in a
+captured CUDA graph with the autotuned schedule.  One benchmark step = one
+time step of every instance (seeding, three SSP-RK3 stages, CFL reduction).
+
+The roofline is taken from the timed region itself: (8 nvar + 1) w
+algorithmic bytes per cell-step (eight plane touches per conserved variable
+over the three stages, plus the r read of the seeding) times the cells, over
+the measured time of one graph-replayed step.
+
+Also reported, each with the same fields: the 256^3 sphere (3-D, FP32), the
+512^2 cylinder, the 1024x512 two-fluid dynamic body and the 1024^2
+elastoplastic impact (FP32 and FP64 each), the FP64 batch, the accuracy of
+every FP32 form against the FP64 CPU oracle (relative L1 per conserved plane
+and shock position), end-to-end throughput through the C ABI with host
+buffers, and the oracle's rate on one host core and on all of them.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle on the host cores on the same
-workload (each benchmark step: one oracle time step on a bounded sample of
-the grid's rows).  Under torchrun every rank runs an independent replica
-(the single-grid workload does not shard); the whole-job value sums the
-replicas' cell updates over the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores on the headline
+workload: every core advances its own ellipse instance (the first instances
+of the batch), one oracle time step per benchmark step.  Under torchrun every
+rank runs an independent replica of the batch (no data-path collective); the
+whole-job value sums the replicas' cell updates over the slowest rank's time.
 """
 import argparse
 import hashlib
 import json
 import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -35,28 +50,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s FP32 & batched vs plain FP64 at stated L1 error; % HBM roofline"
 UNIT = "cell-updates/s"
-WORKLOAD = "cylinder_2d_512x512_mach3_cfl0.8"
-N_CELL = 512 * 512
-KERNEL_SOURCES = ["paper_2111_11806_gb300/csrc/dfv_device.cuh", "paper_2111_11806_gb300/csrc/dfv_kernels.cuh"]
+BATCH_COUNT = 256
+KERNEL_SOURCES = ["paper_2111_11806_gb300/csrc/dfv_device.cuh", "paper_2111_11806_gb300/csrc/dfv_kernels.cuh",
+                  "paper_2111_11806_gb300/csrc/dfv_batch.cuh"]
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="headline only (no other workloads)")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
 
 
 def measured_peaks():
@@ -76,17 +90,25 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per stage launch from the committed ncu summary, if the
-    kernel sources still match the ones it was captured from."""
-    p = os.path.join(ROOT, "profiles", "rk_stage_cylinder_512_fp32.json")
+def recorded_traffic(name):
+    """DRAM bytes per step from a committed ncu summary, if the kernel
+    sources still match the ones it was captured from (else null)."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     if d.get("kernel_source_hash") != kernel_hash():
         return None
-    return d.get("dram_bytes_per_stage_launch")
+    return d
+
+
+def bytes_per_cell_step(nvar, w):
+    """Algorithmic HBM bytes of one stage-by-stage SSP-RK3 step per cell:
+    stage 1 reads U^n and writes U1, stages 2 and 3 read their input and U^n
+    and write their output (8 plane touches per variable), plus the r read
+    of the seeding."""
+    return (8 * nvar + 1) * w
 
 
 class Clocks:
@@ -133,174 +155,380 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(max_seconds, rows=None):
-    """FP64 oracle cell-updates/s on the benchmark workload (one core)."""
-    import numpy as np
+# ------------------------------------------------------------ workloads
+
+def make_workload(spec):
+    """A workload from a small picklable description (shared by the GPU side
+    and the oracle processes)."""
     import workloads as W
+    kind, args = spec
+    return {"ellipse": lambda: W.ellipse_instance(*args), "cylinder": lambda: W.cylinder_2d(*args),
+            "dynamic_body": lambda: W.dynamic_body_2d(*args), "impact": lambda: W.impact_2d(*args),
+            "sphere": lambda: W.sphere_3d(*args)}[kind]()
+
+
+def shock_row(spec, wl):
+    """Index of a pencil along x that crosses the shock away from the body:
+    (row j, plane k) of the density field."""
+    kind = spec[0]
+    n = wl.n
+    if kind == "dynamic_body":
+        return n[1] // 2, 0                      # y = 0.5: air, above the water and the body
+    if kind == "impact":
+        return n[1] // 2, 0                      # through the block's centre line
+    if kind == "sphere":
+        return n[1] // 8, n[2] // 8
+    return n[1] // 8, 0                          # y = 1/8: clear of the body
+
+
+def front_index(rho, wl, row):
+    j, k = row
+    nx = wl.n[0]
+    ny = wl.n[1] if wl.dim >= 2 else 1
+    line = rho.reshape(-1, nx)[k * ny + j]
+    return int(np.argmax(np.abs(np.diff(line))))
+
+
+def plane_scales(ref, wl):
+    """Denominator of the relative L1 of each conserved plane: sum |ref|, with
+    the momentum planes floored at sum(rho) x 10 m/s, and the r and volume-
+    fraction planes at 1e-3 per cell and the stretch planes at 1 per cell, so
+    that near-zero planes are measured against a physical scale."""
+    import workloads as W
+    L = W.layout(wl.dim, wl.nmat, wl.solid)
+    rho = ref[L["irho"]: L["irho"] + wl.nmat].sum(axis=0)
+    s = np.abs(ref).sum(axis=1)
+    for a in range(wl.dim):
+        s[L["iu"] + a] = max(s[L["iu"] + a], 10.0 * np.abs(rho).sum())
+    s[L["ir"]] = max(s[L["ir"]], 1e-3 * ref.shape[1])
+    for c in range(L["nv"]):
+        s[L["iv"] + c] = max(s[L["iv"] + c], 1.0 * ref.shape[1])
+    for l in range(wl.nmat - 1):
+        s[L["iphi"] + l] = max(s[L["iphi"] + l], 1e-3 * ref.shape[1])
+    return np.where(s > 0, s, 1.0)
+
+
+def oracle_accuracy_job(spec, checkpoints):
+    """Run the FP64 oracle on a workload, returning the conserved state and the
+    front position at each checkpoint step (own CFL time step each step)."""
     from oracle import Oracle
-    wl = W.cylinder_2d(512)
-    if rows is not None and rows < 512:
-        # bounded sample: the band of `rows` rows through the body's centre
-        lo_row = 256 - rows // 2
-        prim = wl.prim.reshape(wl.nvar, 512, 512)[:, lo_row:lo_row + rows, :].reshape(wl.nvar, -1)
-        o = Oracle(2, (512, rows), (0.0, lo_row / 512.0), (1.0, (lo_row + rows) / 512.0), wl.materials)
-        o.set_prim(np.ascontiguousarray(prim))
-        cells = 512 * rows
-    else:
-        o = Oracle.from_workload(wl)
-        cells = N_CELL
+    wl = make_workload(spec)
+    o = Oracle.from_workload(wl)
+    out, k, t0 = {}, 0, time.perf_counter()
+    row = shock_row(spec, wl)
+    for c in checkpoints:
+        while k < c:
+            o.step(o.compute_dt(wl.cfl))
+            k += 1
+        cons = o.cons()
+        out[c] = (cons, front_index(density_line(cons, wl), wl, row))
+    return out, time.perf_counter() - t0
+
+
+def density_line(cons, wl):
+    """Mixture density: the sum of the partial-density planes."""
+    return cons[wl.nmat - 1: 2 * wl.nmat - 1].sum(axis=0)
+
+
+def accuracy_record(got, ref, wl, spec, fronts_o, step):
+    e = np.abs(got - ref).sum(axis=1) / plane_scales(ref, wl)
+    row = shock_row(spec, wl)
+    fg = front_index(density_line(got, wl), wl, row)
+    return {"steps": step, "rel_l1_max": float(e.max()), "rel_l1_per_plane": [float(x) for x in e],
+            "front_cell_oracle": int(fronts_o), "front_cell_gpu": int(fg),
+            "front_offset_cells": int(abs(fg - fronts_o))}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_rate_worker(spec, seconds, q):
+    from oracle import Oracle
+    wl = make_workload(spec)
+    o = Oracle.from_workload(wl)
+    o.step(o.compute_dt(wl.cfl))                       # warm-up step
     steps, t0 = 0, time.perf_counter()
     while True:
-        o.step(o.compute_dt(0.8))
+        o.step(o.compute_dt(wl.cfl))
         steps += 1
         el = time.perf_counter() - t0
-        if el >= max_seconds:
+        if el >= seconds:
             break
-    return cells * steps / el, "%d oracle steps on a 512x%d band of the 512x512 grid in %.1f s" % (
-        steps, cells // 512, el)
+    q.put((wl.ncell * steps, el, steps, wl.ncell))
+
+
+def oracle_rates(seconds, ncores):
+    """The oracle as it stands, timed on the host cores: one process per core,
+    each advancing its own ellipse instance of the batch (instances 0, 1, ...)
+    for `seconds`; the rate is the summed cell updates over the longest
+    window.  Returns (one-core record, all-cores record)."""
+    ctx = mp.get_context("spawn")
+    res = {}
+    for cores in (1, ncores):
+        q = ctx.Queue()
+        ps = [ctx.Process(target=oracle_rate_worker, args=(("ellipse", (i,)), seconds, q)) for i in range(cores)]
+        for p in ps:
+            p.start()
+        got = [q.get() for _ in ps]
+        for p in ps:
+            p.join()
+        cu = sum(g[0] for g in got)
+        el = max(g[1] for g in got)
+        sizes = sorted(set(int(round(math.sqrt(g[3]))) for g in got))
+        res[cores] = {"value": cu / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+                      "sample": "%d process(es), each its own ellipse instance of the batch (sizes %s^2) for "
+                                "%.0f s: %d oracle steps in all" % (cores, "/".join(map(str, sizes)), seconds,
+                                                                    sum(g[2] for g in got))}
+    return res[1], res[ncores]
+
+
+def reference_worker(spec, warmup, steps, q):
+    from oracle import Oracle
+    wl = make_workload(spec)
+    o = Oracle.from_workload(wl)
+    for _ in range(warmup):
+        o.step(o.compute_dt(wl.cfl))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(o.compute_dt(wl.cfl))
+    q.put((wl.ncell * steps, time.perf_counter() - t0, wl.ncell))
 
 
 def run_reference(args):
+    """The oracle on the headline workload, on every host core: process i
+    advances ellipse instance i of the batch (instances too large for a run of
+    a few minutes are skipped); value = summed cell updates of the timed steps
+    over the slowest process's time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import numpy as np
-    import workloads as W
-    from oracle import Oracle
     import oracle
+    import workloads as W
     oracle.build()
-    wl = W.cylinder_2d(512)
-    # bounded sample: rows of the grid per benchmark step so that the run stays within ~2 minutes
-    budget_s = 120.0
-    per_step_full = 0.6
-    frac = min(1.0, budget_s / max(1.0, (args.steps + args.warmup) * per_step_full))
-    rows = max(8, int(512 * frac) // 8 * 8)
-    lo_row = 256 - rows // 2
-    prim = wl.prim.reshape(wl.nvar, 512, 512)[:, lo_row:lo_row + rows, :].reshape(wl.nvar, -1)
-    o = Oracle(2, (512, rows), (0.0, lo_row / 512.0), (1.0, (lo_row + rows) / 512.0), wl.materials)
-    o.set_prim(np.ascontiguousarray(prim))
-    for _ in range(args.warmup):
-        o.step(o.compute_dt(0.8))
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        o.step(o.compute_dt(0.8))
-    el = time.perf_counter() - t0
-    cells = 512 * rows
-    value = cells * args.steps / el
-    sample = "each step: one FP64 oracle step on the 512x%d band through the body of the 512x512 grid" % rows
+    ncores = os.cpu_count() or 1
+    budget_cells = 150.0 * 9e5 / max(1, args.steps + args.warmup)     # ~150 s at the oracle's one-core rate
+    sizes = W.batch_sizes(args.batch_count)
+    picks = [i for i, n in enumerate(sizes) if n * n <= budget_cells][:ncores]
+    if not picks:
+        picks = [int(np.argmin(sizes))]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=reference_worker, args=(("ellipse", (i,)), args.warmup, args.steps, q)) for i in picks]
+    for p in ps:
+        p.start()
+    got = [q.get() for _ in ps]
+    for p in ps:
+        p.join()
+    cu = sum(g[0] for g in got)
+    el = max(g[1] for g in got)
+    value = cu / el
+    sample = ("%d processes (one per host core), process i advancing ellipse instance i of the batch "
+              "(sizes %s^2); each benchmark step = one FP64 oracle time step of each" %
+              (len(picks), "/".join(str(sizes[i]) for i in picks)))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": WORKLOAD, "global_batch": 1, "cells": cells, "precision": "fp64",
-                       "l2": "host run"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "ellipses_%d_instances_128-512sq_mach1.5-3" % args.batch_count,
+                       "global_batch": len(picks), "cells_per_step": int(sum(g[2] for g in got)),
+                       "precision": "fp64", "l2": "host run"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(picks), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def time_steps(torch, g, stream, flush, steps, profile):
-    """Per-step CUDA-event windows with an L2 flush before each step."""
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    if profile:
-        g.profile(True)
-    n0 = g.launch_count()
-    with torch.cuda.stream(stream):
-        for k in range(steps):
-            flush.fill_(k & 0x7F)
-            starts[k].record(stream)
-            g.run(1, 0.8, sync=False)
-            ends[k].record(stream)
-    stream.synchronize()
-    launches = g.launch_count() - n0
-    prof = g.profile(False) if profile else None
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    return ms, launches, prof
+# ------------------------------------------------------------ GPU side
 
-
-def run_batched(torch, B, W, stream, args):
-    """Batched workload: per-step CUDA-event timing of graph replays, per-phase
-    profile for the stage-kernel roofline, and the plain FP64 batch."""
-    peak, peak_kind = measured_peaks()
-    wls = [W.ellipse_instance(i) for i in range(args.batch_count)]
-    cells = int(sum(int(np.prod(wl.n)) for wl in wls))
-    out = {"workload": "ellipses_%d_instances_128-512sq_fp32" % args.batch_count, "cells": cells}
-    for prec, key in ((B.DFV_FP32, "fp32"), (B.DFV_FP64, "fp64")):
-        bt = B.Batch(wls, precision=prec, stream=stream)
-        bt.set_all_fields()
-        choice = bt.autotune(trial_steps=2, cfl=0.8)
-        bt.run(3, 0.8)
-        k = 30 if prec == B.DFV_FP32 else 4
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n0 = bt.launch_count()
-        stream.synchronize()
-        e0.record(stream)
-        bt.run(k, 0.8)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        launches = bt.launch_count() - n0
-        bt.profile(True)
-        bt.run(3, 0.8)
-        pms, pn = bt.profile(False)
-        w = 4 if prec == B.DFV_FP32 else 8
-        nvar = bt.nvar
-        stage_ms = float(pms[1] + pms[2] + pms[3]) / pn
-        achieved = 8 * nvar * w * cells / (stage_ms * 1e-3) / 1e9
-        rec = {"value": cells * k / (ms * 1e-3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
-               "autotune": {"ctas_per_sm": choice[0] if choice[0] > 0 else "one CTA per work item",
-                            "schedule": ["instance-order static", "largest-first static",
-                                         "largest-first dynamic"][choice[1]]},
-               "gpu_launches": int(launches),
-               "phase_ms_per_step": {"seed": pms[0] / pn, "stage1": pms[1] / pn, "stage2": pms[2] / pn,
-                                     "stage3": pms[3] / pn},
-               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "peak_kind": peak_kind,
-                            "kernel": "k_batch_stage (3 launches per step)",
-                            "algorithmic_bytes_per_step": 8 * nvar * w * cells}}
-        out[key] = rec
-        del bt
-        torch.cuda.synchronize()
-    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
-    return out
-
-
-def run_sphere(torch, B, W, stream):
-    """256^3 sphere workload, FP32: event-timed steps and the stage roofline."""
-    peak, peak_kind = measured_peaks()
-    wl = W.sphere_3d(256)
-    g = B.Grid.from_workload(wl, precision=B.DFV_FP32, stream=stream)
-    g.run(2, 0.8)
-    k = 10
+def event_window(torch, stream, fn):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream.synchronize()
     e0.record(stream)
-    g.run(k, 0.8)
+    fn()
     e1.record(stream)
     e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    g.profile(True)
-    g.run(3, 0.8)
-    pms, pn = g.profile(False)
-    stage_ms = float(pms[1] + pms[2] + pms[3]) / pn
-    achieved = 8 * wl.nvar * 4 * wl.ncell / (stage_ms * 1e-3) / 1e9
+    return e0.elapsed_time(e1)
+
+
+def roofline(achieved_bytes, ms, peak, peak_kind, kernel, extra=None):
+    gbs = achieved_bytes / (ms * 1e-3) / 1e9
+    r = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+         "peak_kind": peak_kind, "kernel": kernel, "algorithmic_bytes_per_launch": achieved_bytes,
+         "avg_launch_ms": ms}
+    if extra:
+        r.update(extra)
+    return r
+
+
+def time_grid(torch, g, stream, flush, steps):
+    """Per-step CUDA-event windows of graph-replayed single steps, with an L2
+    flush (256 MiB write) before each step when `flush` is given."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            if flush is not None:
+                flush.fill_(k & 0x7F)
+            starts[k].record(stream)
+            g.run(1, g._cfl, sync=False)
+            ends[k].record(stream)
+    stream.synchronize()
+    return sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+
+def single_grid_form(torch, B, W, stream, flush, spec, prec, steps, warmup):
+    wl = make_workload(spec)
+    g = B.Grid.from_workload(wl, precision=prec, stream=stream)
+    g._cfl = wl.cfl
+    g.run(warmup, wl.cfl)
+    n0 = g.launch_count()
+    ms = time_grid(torch, g, stream, flush, steps)
+    launches = g.launch_count() - n0
+    w = 4 if prec == B.DFV_FP32 else 8
+    bpc = bytes_per_cell_step(g.nvar, w)
+    peak, peak_kind = measured_peaks()
+    rec = {"value": wl.ncell * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+           "gpu_launches": int(launches),
+           "roofline": roofline(bpc * wl.ncell, ms / steps, peak, peak_kind,
+                                "one graph-replayed step (seeding + 3 stage launches)",
+                                {"bytes_per_cell_step": bpc})}
     del g
-    return {"workload": "sphere_3d_256^3_mach2.5_fp32", "cells": wl.ncell, "value": wl.ncell * k / (ms * 1e-3),
-            "unit": UNIT, "steps": k, "ms_per_step": ms / k,
-            "phase_ms_per_step": {"seed": pms[0] / pn, "stage1": pms[1] / pn, "stage2": pms[2] / pn,
-                                  "stage3": pms[3] / pn},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind,
-                         "kernel": "k_stage_z (3-D FP32, marching along z)"}}
+    torch.cuda.synchronize()
+    return rec, wl
+
+
+def run_headline(torch, B, W, stream, args, clocks_on):
+    """The batched FP32 form: autotune, warm-up, then `steps` graph-replayed
+    steps inside one CUDA-event window (the timed region)."""
+    peak, peak_kind = measured_peaks()
+    wls = [W.ellipse_instance(i) for i in range(args.batch_count)]
+    cells = int(sum(wl.ncell for wl in wls))
+    bt = B.Batch(wls, precision=B.DFV_FP32, stream=stream)
+    bt.set_all_fields()
+    choice = bt.autotune(trial_steps=2, cfl=0.8)
+    bt.run(args.warmup, 0.8)
+    n0 = bt.launch_count()
+    clocks = clocks_on()
+    ms = event_window(torch, stream, lambda: bt.run(args.steps, 0.8))
+    clk = clocks.stop() if clocks else None
+    launches = bt.launch_count() - n0
+    # per-phase shares from a second pass with events around every launch
+    bt.profile(True)
+    bt.run(5, 0.8)
+    pms, pn = bt.profile(False)
+    bpc = bytes_per_cell_step(bt.nvar, 4)
+    phases = {"seed": pms[0] / pn, "stage1": pms[1] / pn, "stage2": pms[2] / pn, "stage3": pms[3] / pn}
+    tot = sum(phases.values())
+    traffic = recorded_traffic("batch_step_ellipses_fp32.json")
+    tr_step = None
+    if traffic:
+        tr_step = traffic["dram_bytes_per_cell_step"] * cells
+    rl = roofline(bpc * cells, ms / args.steps, peak, peak_kind,
+                  "one graph-replayed step: k_batch_seed + 3 x k_batch_stage + k_batch_finalize",
+                  {"bytes_per_cell_step": bpc, "traffic": tr_step,
+                   "stage_share_of_step": (phases["stage1"] + phases["stage2"] + phases["stage3"]) / tot,
+                   "timing": "CUDA events around the timed region of %d graph-replayed steps" % args.steps})
+    sched = ["instance-order static", "largest-first static", "largest-first dynamic"][choice[1]]
+    rec = {"ms": ms, "cells": cells, "launches": launches, "clocks": clk, "roofline": rl,
+           "phase_ms_per_step_profiled": phases,
+           "autotune": {"ctas_per_sm": choice[0] if choice[0] > 0 else "one CTA per work item", "schedule": sched},
+           "nvar": bt.nvar}
+    del bt
+    torch.cuda.synchronize()
+    return rec, wls
+
+
+def run_batch_fp64(torch, B, wls, stream, steps):
+    peak, peak_kind = measured_peaks()
+    cells = int(sum(wl.ncell for wl in wls))
+    bt = B.Batch(wls, precision=B.DFV_FP64, stream=stream)
+    bt.set_all_fields()
+    bt.autotune(trial_steps=1, cfl=0.8)
+    bt.run(2, 0.8)
+    ms = event_window(torch, stream, lambda: bt.run(steps, 0.8))
+    bpc = bytes_per_cell_step(bt.nvar, 8)
+    rec = {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+           "roofline": roofline(bpc * cells, ms / steps, peak, peak_kind, "one graph-replayed step (FP64)",
+                                {"bytes_per_cell_step": bpc})}
+    del bt
+    torch.cuda.synchronize()
+    return rec
+
+
+def run_e2e(torch, B, wls, stream, job_steps):
+    """End to end through the C ABI with host buffers: every instance's
+    primitive fields in from pinned host memory, the configuration's steps,
+    every instance's fields back to pinned host memory."""
+    cells = int(sum(wl.ncell for wl in wls))
+    host_in = [torch.empty(wl.prim.shape, dtype=torch.float64, pin_memory=True) for wl in wls]
+    host_out = [torch.empty(wl.prim.shape, dtype=torch.float64, pin_memory=True) for wl in wls]
+    for h, wl in zip(host_in, wls):
+        h.numpy()[:] = wl.prim
+    bt = B.Batch(wls, precision=B.DFV_FP32, stream=stream)
+    bt.set_all_fields()
+    bt.autotune(trial_steps=2, cfl=0.8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, h in enumerate(host_in):
+        bt.set_fields(i, h.numpy())
+    bt.run(job_steps, 0.8)
+    for i, h in enumerate(host_out):
+        bt.get_fields(i, B.DFV_FIELDS_PRIMITIVE, out=h.numpy())
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    nbytes = int(sum(h.numel() * 8 for h in host_in))
+    del bt
+    return {"value": cells * job_steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes / job_steps,
+            "d2h_bytes_per_step": nbytes / job_steps,
+            "job": "set_fields(pinned host, %d instances) + %d steps + get_fields(pinned host), %.3f s" % (
+                len(wls), job_steps, el)}
+
+
+def gpu_accuracy_run(torch, B, stream, spec, checkpoints, batched):
+    """The FP32 form on the GPU (own CFL time step), conserved state at each
+    checkpoint."""
+    wl = make_workload(spec)
+    out, k = {}, 0
+    if batched:
+        bt = B.Batch([wl], precision=B.DFV_FP32, stream=stream)
+        bt.set_all_fields()
+        for c in checkpoints:
+            bt.run(c - k, wl.cfl)
+            k = c
+            out[c] = bt.get_fields(0, B.DFV_FIELDS_CONSERVED)
+        del bt
+    else:
+        g = B.Grid.from_workload(wl, precision=B.DFV_FP32, stream=stream)
+        for c in checkpoints:
+            g.run(c - k, wl.cfl)
+            k = c
+            out[c] = g.cons()
+        del g
+    torch.cuda.synchronize()
+    return out, wl
+
+
+# accuracy cases: (name, workload spec, checkpoints, batched)
+ACCURACY = [
+    ("batched_instance", ("ellipse", (0, 256)), (60, 300), True),
+    ("cylinder_2d", ("cylinder", (512,)), (40, 100), False),
+    ("dynamic_body_2d", ("dynamic_body", (512, 256)), (40, 100), False),
+    ("impact_2d", ("impact", (256,)), (40, 100), False),
+    ("sphere_3d", ("sphere", (64,)), (20, 50), False),
+]
 
 
 def run_ours(args):
     rank, world, local = dist_env()
-    import numpy as np
     import torch
     import torch.distributed as dist
+    # the oracle processes (spawned: safe beside the CUDA context) start first
+    # and run while the GPU is timed
+    pool = None
+    if rank == 0 and world == 1 and not args.no_accuracy:
+        import oracle
+        oracle.build()
+        pool = mp.get_context("spawn").Pool(len(ACCURACY))
+        jobs = {name: pool.apply_async(oracle_accuracy_job, (spec, list(cps))) for name, spec, cps, _ in ACCURACY}
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -312,93 +540,55 @@ def run_ours(args):
     import workloads as W
     from paper_2111_11806_gb300 import binding as B
     B.load()
-
-    wl = W.cylinder_2d(512)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    g32 = B.Grid.from_workload(wl, precision=B.DFV_FP32, device=dev, stream=stream)
-    g64 = B.Grid.from_workload(wl, precision=B.DFV_FP64, device=dev, stream=stream)
 
-    clocks = Clocks(local) if rank == 0 else None
-    # warm-up (untimed)
-    g32.run(args.warmup, 0.8)
-    g64.run(max(3, args.warmup // 2), 0.8)
-    torch.cuda.synchronize()
-
-    # --- kernel-only timed region: FP32 form (the headline)
+    # --- headline: the batched FP32 form (timed region)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    # one graph replay per step, no per-kernel events inside the step
-    ms32, launches32, _ = time_steps(torch, g32, stream, flush, args.steps, profile=False)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    # second timed pass of the same workload with CUDA events around every
-    # kernel (launched one by one) for the per-kernel durations of the roofline
-    kprof = max(20, min(args.steps, 200))
-    msp32, _, prof32 = time_steps(torch, g32, stream, flush, kprof, profile=True)
-    total_ms = sum(ms32)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    head, wls = run_headline(torch, B, W, stream, args, lambda: Clocks(local) if rank == 0 else None)
+    t = torch.tensor([head["ms"]], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
-    value = world * args.steps * N_CELL / (total_ms * 1e-3)
+    value = world * args.steps * head["cells"] / (total_ms * 1e-3)
 
-    # --- plain FP64 form, same procedure, fewer steps
-    k64 = max(5, min(args.steps, 50))
-    ms64, launches64, _ = time_steps(torch, g64, stream, flush, k64, profile=False)
-    value64 = world * k64 * N_CELL / (sum(ms64) * 1e-3)
+    extra = {}
+    if not args.no_extra:
+        extra["batched_fp64"] = run_batch_fp64(torch, B, wls, stream, 10)
+        extra["batched_fp64"]["fp32_over_fp64"] = value / world / extra["batched_fp64"]["value"]
+        e2e = run_e2e(torch, B, wls, stream, 300)
+        e2e["value"] *= world
+        flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        forms = [
+            ("cylinder_2d", "cylinder_2d_512x512_mach3", ("cylinder", (512,)), 200, 20, flush),
+            ("dynamic_body_2d", "dynamic_body_2d_1024x512_air_water", ("dynamic_body", ()), 40, 10, flush),
+            ("impact_2d", "impact_2d_1024x1024_aluminium_air", ("impact", (1024,)), 10, 4, flush),
+            ("sphere_3d", "sphere_3d_256^3_mach2.5", ("sphere", (256,)), 10, 3, None),
+        ]
+        for key, wname, spec, k32, k64, fl in forms:
+            r32, wl = single_grid_form(torch, B, W, stream, fl, spec, B.DFV_FP32, k32, 3)
+            r64, _ = single_grid_form(torch, B, W, stream, fl, spec, B.DFV_FP64, k64, 2)
+            extra[key] = {"workload": wname, "cells": wl.ncell, "nvar": wl.nvar, "fp32": r32, "fp64": r64,
+                          "fp32_over_fp64": r32["value"] / r64["value"],
+                          "l2": "flushed (256 MiB write) before every timed step" if fl is not None
+                          else "state larger than L2 (no flush)"}
+            del wl
+    else:
+        e2e = None
 
-    # --- end to end through the C ABI with host buffers: fields in from pinned
-    # host memory, the configuration's 500 steps, fields back to the host
-    job_steps = wl.steps
-    nvar = wl.nvar
-    host_in = torch.empty((nvar, N_CELL), dtype=torch.float64, pin_memory=True)
-    host_in.numpy()[:] = wl.prim
-    host_out = torch.empty((nvar, N_CELL), dtype=torch.float64, pin_memory=True)
-    g_e2e = B.Grid(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, precision=B.DFV_FP32, device=dev, stream=stream)
-    jobs = 2
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(jobs):
-        g_e2e.set_fields(host_in.numpy())
-        g_e2e.set_body()
-        g_e2e.run(job_steps, 0.8)
-        g_e2e.get_fields(B.DFV_FIELDS_PRIMITIVE, out=host_out.numpy())
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_val = world * jobs * job_steps * N_CELL / e2e_s
-    bytes_io = nvar * N_CELL * 8
-
-    # --- batched form: 256 independent instances of {128..512}^2 (about 27 M
-    # cells, 0.54 GB per FP32 state copy: larger than L2, so no flush is needed),
-    # persistent launches over the (instance, tile) work list in a CUDA graph,
-    # schedule chosen by the autotuner
-    batched = None
-    if not args.no_batched:
-        batched = run_batched(torch, B, W, stream, args)
-
-    # --- 3-D: Mach 2.5 shock over a rigid sphere, 256^3 cells (0.40 GB per FP32 state copy)
-    sphere = None
-    if not args.no_batched:
-        sphere = run_sphere(torch, B, W, stream)
-
-    clk = clocks.stop() if clocks else None
-
-    # --- accuracy of the FP32 form after the timed steps: relative L1 of the
-    # density against the FP64 form advanced the same number of steps
-    warm32 = args.warmup + args.steps
-    g_acc32 = B.Grid.from_workload(wl, precision=B.DFV_FP32, device=dev, stream=stream)
-    g_acc64 = B.Grid.from_workload(wl, precision=B.DFV_FP64, device=dev, stream=stream)
-    nacc = 200
-    g_acc32.run(nacc, 0.8)
-    g_acc64.run(nacc, 0.8)
-    r32, r64 = g_acc32.prim()[0], g_acc64.prim()[0]
-    l1 = float(np.abs(r32 - r64).sum() / np.abs(r64).sum())
-    row = lambda r: np.argmax(np.abs(np.diff(r.reshape(512, 512)[256])))
-    shock_cells = int(abs(row(r32) - row(r64)))
+    # --- accuracy of every FP32 form against the FP64 oracle
+    accuracy = None
+    if pool is not None:
+        accuracy = {}
+        for name, spec, cps, batched in ACCURACY:
+            got, wl = gpu_accuracy_run(torch, B, stream, spec, list(cps), batched)
+            ref, secs = jobs[name].get()
+            accuracy[name] = {"workload": wl.name, "cells": wl.ncell,
+                              "at": [accuracy_record(got[c], ref[c][0], wl, spec, ref[c][1], c) for c in cps],
+                              "oracle_seconds": secs}
+        pool.close()
+        pool.join()
 
     if rank != 0:
         if world > 1:
@@ -406,48 +596,30 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    peak, peak_kind = measured_peaks()
-    w32 = 4
-    stage_ms = float(prof32[0][1] + prof32[0][2] + prof32[0][3])
-    stage_launches = 3 * prof32[1]
-    bytes_per_launch = 8 * nvar * w32 * N_CELL / 3.0    # (2 + 3 + 3) nvar planes over the 3 stage launches
-    achieved = bytes_per_launch / (stage_ms * 1e-3 / stage_launches) / 1e9
-    traffic = recorded_traffic()
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        rate, sample = oracle_rate(15.0, rows=128)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        one, allc = oracle_rates(10.0, os.cpu_count() or 1)
+        cpu = dict(allc)
+        cpu["single_core"] = one
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": world, "cells_per_gpu": N_CELL, "nvar": nvar,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ellipses_%d_instances_128-512sq_mach1.5-3_fp32_graph" % args.batch_count,
+                   "global_batch": world * args.batch_count, "cells_per_gpu": head["cells"], "nvar": head["nvar"],
                    "precision": "fp32 bulk (FP64 polar/closure where phi<1e-6)",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed (256 MiB write) before every timed step"},
-        "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": sum(ms64) / k64,
-                 "fp32_over_fp64": value / value64},
-        "accuracy": {"fp32_vs_fp64_rel_l1_density": l1, "shock_position_diff_cells": shock_cells,
-                     "after_steps": nacc},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_stage (SSP-RK3 stage), FP32",
-                     "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "avg_launch_ms": stage_ms / stage_launches,
-                     "timing": "CUDA events around each kernel in a second timed pass of %d steps "
-                               "(launched one by one; that pass took %.4f ms per step)" % (kprof, sum(msp32) / kprof)},
-        "kernel_ms_per_step": {"seed": prof32[0][0] / prof32[1], "stage1": prof32[0][1] / prof32[1],
-                               "stage2": prof32[0][2] / prof32[1], "stage3": prof32[0][3] / prof32[1],
-                               "finalize": prof32[0][4] / prof32[1]},
+                   "l2": "inputs larger than L2 (0.54 GB per FP32 state copy), no flush",
+                   "autotune": head["autotune"]},
+        "roofline": head["roofline"],
+        "phase_ms_per_step_profiled": head["phase_ms_per_step_profiled"],
+        "gpu_launches": int(head["launches"]),
+        "e2e": e2e,
         "cpu_baseline": cpu,
-        "batched": batched,
-        "sphere_3d": sphere,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io / job_steps,
-                "d2h_bytes_per_step": bytes_io / job_steps,
-                "job": "set_fields(host) + %d steps + get_fields(host), %d jobs" % (job_steps, jobs)},
-        "gpu_launches": int(launches32),
-        "clocks": clk,
+        "accuracy": accuracy,
+        "clocks": head["clocks"],
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

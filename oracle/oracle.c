@@ -1007,8 +1007,9 @@ void o_elvira(const double b[9], double hx, double hy, double nrm[2])
  *  2. the probe point, stepped or fixed:
  *     stepped: s = 1.0, 1.5, ..., 4.0 dx_min along n [reading: step dx/2]; the
  *     first point whose 2^dim enclosing cell centres all lie in the domain (or
- *     wrap, for periodic directions) and have r < 0.5 is taken; no valid point
- *     -> the cell is unchanged;
+ *     wrap, for periodic directions) and have r < 0.5 is taken, a point
+ *     within PROBE_SNAP cells of a cell-centre line counting as on it (the
+ *     corners beyond carry no weight); no valid point -> the cell is unchanged;
  *     fixed: s = 1.5 dx_min, enclosing cells clamped into the domain (wrapped
  *     if periodic), whatever their r [reading];
  *     the primitives of U0 are interpolated multilinearly at the point;
@@ -1019,6 +1020,15 @@ void o_elvira(const double b[9], double hx, double hy, double nrm[2])
  *     Riemann-problem variant the right HLLC star state of (new, interpolated).
  * Every seeded state is computed from U0 alone [reading: all cells seeded at
  * once], so the result does not depend on the loop order. */
+/* A probe point within PROBE_SNAP cell widths of a cell-centre line is
+ * taken to lie on it: the corners beyond the line get weight 0 and are not
+ * part of the stencil (neither tested nor read) [reading: the paper's stencil
+ * is the set of cells the interpolated state is made of; on a symmetry axis
+ * the normal is axis-aligned, the probe steps are whole and half cells, and
+ * the probe point falls exactly on a cell-centre line, where a zero-weight
+ * corner would otherwise decide the step by the sign of a rounding error]. */
+#define PROBE_SNAP 1e-3
+
 void o_seed(ostate *s)
 {
     long nc = s->ncell;
@@ -1064,8 +1074,16 @@ void o_seed(ostate *s)
                         double xp = cell_centre(s, d, ijk[d]) + sdist * nrm[d];
                         double fi = (xp - s->lo[d]) / s->dx[d] - 0.5;
                         double fl = floor(fi);
+                        double fr = fi - fl;
+                        /* within PROBE_SNAP cells of a cell-centre line: on it */
+                        if (fr < PROBE_SNAP) {
+                            fr = 0.0;
+                        } else if (fr > 1.0 - PROBE_SNAP) {
+                            fr = 0.0;
+                            fl += 1.0;
+                        }
                         base[d] = (int)fl;
-                        frac[d] = fi - fl;
+                        frac[d] = fr;
                     }
                     int ncorner = 1 << s->dim;
                     int ok = 1;
@@ -1074,17 +1092,19 @@ void o_seed(ostate *s)
                     for (int m = 0; m < ncorner && ok; m++) {
                         int ci[3] = {0, 0, 0};
                         double wt = 1.0;
+                        int inside = 1;
                         for (int d = 0; d < s->dim; d++) {
                             int bit = (m >> d) & 1;
                             int ii = base[d] + bit;
-                            if (s->periodic[d] || s->probe_mode == 1) ii = map_index(s, d, ii);
-                            else if (ii < 0 || ii > s->n[d] - 1) { ok = 0; break; }
-                            ci[d] = ii;
+                            if (!s->periodic[d] && (ii < 0 || ii > s->n[d] - 1)) inside = 0;
+                            ci[d] = map_index(s, d, ii);
                             wt *= bit ? frac[d] : (1.0 - frac[d]);
                         }
-                        if (!ok) break;
                         long cc = cell_index(s, ci[0], ci[1], ci[2]);
-                        if (s->probe_mode == 0 && !(U0[s->ir * nc + cc] < 0.5)) ok = 0;
+                        /* the stepped probe needs fluid cells inside the domain;
+                         * a corner of weight 0 (a probe point on a cell-centre
+                         * line) is not part of the stencil */
+                        if (s->probe_mode == 0 && wt > 0.0 && (!inside || !(U0[s->ir * nc + cc] < 0.5))) ok = 0;
                         cidx[m] = cc;
                         wts[m] = wt;
                     }
@@ -1092,6 +1112,7 @@ void o_seed(ostate *s)
                     for (int v = 0; v < nv; v++) wint[v] = 0.0;
                     for (int m = 0; m < ncorner; m++) {
                         double q[OMAXV], w[OMAXV];
+                        if (wts[m] == 0.0) continue;
                         for (int v = 0; v < nv; v++) q[v] = U0[v * nc + cidx[m]];
                         cons_to_prim(s, q, w);
                         for (int v = 0; v < nv; v++) wint[v] += wts[m] * w[v];

@@ -421,8 +421,9 @@ class Batch:
         for i, wl in enumerate(self.wls):
             self.set_fields(i, wl.prim)
 
-    def get_fields(self, i, which=DFV_FIELDS_CONSERVED):
-        a = np.zeros((self.nvar, self.cells[i]))
+    def get_fields(self, i, which=DFV_FIELDS_CONSERVED, out=None):
+        a = np.zeros((self.nvar, self.cells[i])) if out is None else out
+        assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.nvar * self.cells[i]
         with self._ctx():
             _bcheck(load().dfv_batch_get_fields(self._h, int(i), _vp(a.ctypes.data), which, 0), self._h,
                     "dfv_batch_get_fields")

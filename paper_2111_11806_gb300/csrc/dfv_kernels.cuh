@@ -440,7 +440,8 @@ __device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R
 // |grad r| dx_min > 1e-10 get the outward normal n = -grad r/|grad r| (Youngs,
 // Sec. 3.3) or the ELVIRA normal; the stepped probe tries points at 1.0, 1.5,
 // ..., 4.0 dx_min along n and takes the first whose 2^dim enclosing cell
-// centres are in the domain (wrapped if periodic) with r < 0.5, the fixed probe
+// centres are in the domain (wrapped if periodic) with r < 0.5 (corners of
+// weight 0 excepted: probe_point), the fixed probe
 // takes 1.5 dx_min; the primitives are interpolated multilinearly there and
 // u <- (I - 2nn^T) u + 2 (v_r.n) n, V <- (I - 2nn^T) V (I - 2nn^T); the cell
 // gets that state (original variant) or the right HLLC star state between it
@@ -459,6 +460,43 @@ __device__ __forceinline__ void seed_star(const GridP &g, const R nv[3], const R
 // probe point, and lane 0 interpolates (in the order of the cells), reflects
 // and returns the state (the other lanes return false).
 constexpr int SEED_G = 8;
+
+// Probe point of step `step` of the ladder (s = 1.0 + step/2 dx_min along n):
+// base cell and fractions of the multilinear stencil.  A point within
+// PROBE_SNAP cell widths of a cell-centre line is taken to lie on it, so the
+// corners beyond the line get weight 0 exactly: on a symmetry axis of the body
+// the normal is axis-aligned, the steps are whole and half cells and the point
+// falls on the line, where a zero-weight corner would otherwise decide the step
+// by the sign of a rounding error (FP32 against FP64, or one contraction of the
+// arithmetic against another).
+#define PROBE_SNAP 1e-3
+
+template <class R, int DIM>
+__device__ __forceinline__ void probe_point(const GridC<R> &gc, const int ijk[3], const R nv[3], int step, int base[3],
+                                            R fr[3])
+{
+    const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        base[d] = 0;
+        fr[d] = R(0);
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        const R xp = gc.lo[d] + ((R)ijk[d] + R(0.5)) * gc.dx[d] + sd * nv[d];
+        const R fi = (xp - gc.lo[d]) / gc.dx[d] - R(0.5);
+        R fl = floor(fi);
+        R f = fi - fl;
+        if (f < R(PROBE_SNAP)) {
+            f = R(0);
+        } else if (f > R(1) - R(PROBE_SNAP)) {
+            f = R(0);
+            fl += R(1);
+        }
+        base[d] = (int)fl;
+        fr[d] = f;
+    }
+}
 
 // A band cell: rigid (r > 0.5) with a non-zero central-difference gradient of
 // r (Youngs); r of the cell and of its 2 DIM neighbours in one round of loads.
@@ -527,52 +565,35 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
         const bool fixed = g.probe_mode == 1;
         if (!fixed) {
             // a step is valid when its 2^DIM enclosing cells lie in the grid
-            // (or wrap, in a periodic direction) and all have r < 0.5
+            // (or wrap, in a periodic direction) and all have r < 0.5; corners
+            // of weight 0 (a probe point on a cell-centre line, see
+            // probe_point) are not part of the stencil
             bool ok = sub < 7;
-            R rmax = R(0);
             if (ok) {
-                const int step = sub;
-                const R sd = (R(1) + R(0.5) * (R)step) * gc.dxmin;
-                int base[3] = {0, 0, 0};
+                int base[3];
+                R fr[3];
+                probe_point<R, DIM>(gc, ijk, nv, sub, base, fr);
 #pragma unroll
-                for (int d = 0; d < DIM; d++) {
-                    const R xp = gc.lo[d] + ((R)ijk[d] + R(0.5)) * gc.dx[d] + sd * nv[d];
-                    const R fi = (xp - gc.lo[d]) / gc.dx[d] - R(0.5);
-                    base[d] = (int)floor(fi);
-                }
-                const bool anyper = g.periodic[0] || (DIM >= 2 && g.periodic[1]) || (DIM >= 3 && g.periodic[2]);
-                if (!anyper) {
-                    // nothing is loaded for a step whose cells leave the grid
+                for (int m = 0; m < NC; m++) {
+                    int ci[3] = {0, 0, 0};
+                    bool inside = true;
+                    R wt = R(1);
 #pragma unroll
-                    for (int d = 0; d < DIM; d++) ok = ok && base[d] >= 0 && base[d] <= g.n[d] - 2;
-                    if (ok) {
-                        const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
-                        const long long c0 = base[0] + sy * base[1] + sz * base[2];
-#pragma unroll
-                        for (int m = 0; m < NC; m++) {
-                            const long long cm = c0 + (m & 1) + ((m >> 1) & 1) * sy + ((m >> 2) & 1) * sz;
-                            const R rv = U[L::IR * P + cm];
-                            rmax = (rv < R(0.5)) ? rmax : R(1);
-                        }
+                    for (int d = 0; d < DIM; d++) {
+                        const int bit = (m >> d) & 1;
+                        const int ii = base[d] + bit;
+                        if (!g.periodic[d] && (ii < 0 || ii > g.n[d] - 1)) inside = false;
+                        ci[d] = map_idx(ii, g.n[d], g.periodic[d]);
+                        wt *= bit ? fr[d] : (R(1) - fr[d]);
                     }
-                } else {
-#pragma unroll
-                    for (int m = 0; m < NC; m++) {
-                        int ci[3] = {0, 0, 0};
-#pragma unroll
-                        for (int d = 0; d < DIM; d++) {
-                            int ii = base[d] + ((m >> d) & 1);
-                            if (g.periodic[d]) ii = map_idx(ii, g.n[d], 1);
-                            else if (ii < 0 || ii > g.n[d] - 1) ok = false;
-                            ci[d] = ii < 0 ? 0 : (ii > g.n[d] - 1 ? g.n[d] - 1 : ii);
-                        }
+                    if (wt > R(0)) {
                         const R rv =
                             U[L::IR * P + ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2])];
-                        rmax = (rv < R(0.5)) ? rmax : R(1);
+                        ok = ok && inside && rv < R(0.5);
                     }
                 }
             }
-            valid = (__ballot_sync(gm, ok && rmax == R(0)) >> gbase) & 0x7fu;
+            valid = (__ballot_sync(gm, ok) >> gbase) & 0x7fu;
         }
         if (!fixed && !valid) return false;
         first = fixed ? 1 : __ffs(valid) - 1;     // step 1 of the ladder is the fixed 1.5 dx_min
@@ -581,18 +602,11 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
         // their r)
         R wi[L::NVAR];
         {
-            const R sd = (R(1) + R(0.5) * (R)first) * gc.dxmin;
-            int base[3] = {0, 0, 0};
-            R fr[3] = {R(0), R(0), R(0)};
-#pragma unroll
-            for (int d = 0; d < DIM; d++) {
-                const R xp = gc.lo[d] + ((R)ijk[d] + R(0.5)) * gc.dx[d] + sd * nv[d];
-                const R fi = (xp - gc.lo[d]) / gc.dx[d] - R(0.5);
-                const R fl = floor(fi);
-                base[d] = (int)fl;
-                fr[d] = fi - fl;
-            }
-            // lane m: enclosing cell m and its weight
+            int base[3];
+            R fr[3];
+            probe_point<R, DIM>(gc, ijk, nv, first, base, fr);
+            // lane m: enclosing cell m and its weight (a corner of weight 0 is
+            // not read: it may be a rigid cell that another group is seeding)
             R wt = R(1), w[L::NVAR];
 #pragma unroll
             for (int v = 0; v < L::NVAR; v++) w[v] = R(0);
@@ -605,11 +619,13 @@ __device__ __forceinline__ bool seed_compute(const R *U, const Ctl *ctl, const G
                     ci[d] = map_idx(base[d] + bit, g.n[d], g.periodic[d]);
                     wt *= bit ? fr[d] : (R(1) - fr[d]);
                 }
-                const long long cc = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
-                R qc[L::NVAR];
+                if (wt > R(0)) {
+                    const long long cc = ci[0] + (long long)g.n[0] * (ci[1] + (long long)g.n[1] * ci[2]);
+                    R qc[L::NVAR];
 #pragma unroll
-                for (int v = 0; v < L::NVAR; v++) qc[v] = U[v * P + cc];
-                cons_to_prim<R, DIM, NMAT, SOLID>(g, qc, w);
+                    for (int v = 0; v < L::NVAR; v++) qc[v] = U[v * P + cc];
+                    cons_to_prim<R, DIM, NMAT, SOLID>(g, qc, w);
+                }
             }
             // lane 0 sums them in the order of the cells
 #pragma unroll
