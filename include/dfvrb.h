@@ -115,6 +115,12 @@ typedef struct {
                             until the 2^dim enclosing cells have r < 0.5; 1 fixed
                             1.5 dx_min whatever their r (seeded from the
                             step-start state: one extra launch per step) */
+    int general_stage;   /* 0: the SSP-RK3 stages of a 2-D FP32 grid of one ideal or
+                            stiffened gas (no solid, no periodic side, no HLLC-LM,
+                            a static body, n[0] a multiple of 4) run in the
+                            TMA-tiled gas kernel, the others in the general
+                            stage kernel; 1: always the general stage kernel.
+                            The two agree to FP32 rounding. */
 } dfv_options;
 
 typedef struct dfv_grid dfv_grid;

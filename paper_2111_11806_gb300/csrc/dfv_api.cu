@@ -4,6 +4,7 @@
 // buffers inside the caller's workspace, and the launch sequence of a step
 // (seed, three RK stages, finalize), optionally captured once into a CUDA
 // graph and replayed.  No device memory is allocated here.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -14,6 +15,7 @@
 #include <array>
 
 #include "../../include/dfvrb.h"
+#include "dfv_gas.cuh"
 #include "dfv_kernels.cuh"
 #include "dfv_ops.h"
 
@@ -48,6 +50,16 @@ struct dfv_grid {
     bool prof = false;                   // per-kernel event timing (dfv_profile)
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::array<cudaEvent_t, 6>> ev_steps;
+    // the 2-D single-gas FP32 stage kernel (dfv_gas.cuh): its tensor maps and
+    // instance record sit in the workspace, encoded at creation when the grid's
+    // shape allows it; it runs the stages whenever the material, the options
+    // and the body allow it too (gas_on)
+    bool gas_ready = false;
+    bool body_moving = false;
+    dfv::GasInst *d_ginst = nullptr;
+    CUtensorMap *d_tmaps = nullptr;
+    int gas_grid = 1;
+    long long gas_tiles = 0;
 };
 
 namespace {
@@ -73,7 +85,7 @@ int nvar_of(int dim, int nmat, int solid)
 int solid_kind(int solid) { return solid == 2 ? 2 : (solid ? 1 : 0); }
 
 struct Layout {
-    size_t off_ctl, off_part, off_U, off_U1, off_U3, off_stage, total;
+    size_t off_ctl, off_part, off_gas, off_U, off_U1, off_U3, off_stage, total;
     long long pitch, nb_stage, nb_cfl;
 };
 
@@ -103,6 +115,8 @@ Layout plan(int dim, const int n[3], int nmat, int solid, int precision)
     off += align256(sizeof(Ctl));
     L.off_part = off;
     off += align256(sizeof(double) * 4 * (size_t)nparts);
+    L.off_gas = off;   // three tensor maps, then the gas kernel's instance record
+    off += align256(3 * sizeof(CUtensorMap) + sizeof(dfv::GasInst));
     const size_t state = align256((size_t)w * nvar * (size_t)L.pitch);
     L.off_U = off;
     off += state;
@@ -239,6 +253,38 @@ cudaEvent_t take_event(dfv_grid *g)
 // needs only the rigid box that stage 3 folded.
 bool can_defer(const dfv_grid *g) { return !g->dynamic && g->g.probe_mode == 0; }
 
+// Whether the stages run in the gas kernel now (the tensor maps exist, and
+// the material, the options and the body allow it).
+bool gas_on(const dfv_grid *g)
+{
+    return g->gas_ready && g->nmat == 1 &&
+           dfv::gas_eligible(g->precision == DFV_FP32, g->dim, g->nmat, g->solid, g->g.mat[0].kind, g->g.periodic,
+                             g->g.hllc_lm, g->dynamic || g->body_moving, g->g.n[0]);
+}
+
+// One SSP-RK3 stage: the gas kernel when it applies, else the general one.
+dfv_status launch_stage(dfv_grid *g, int s, const void *in, const void *un, void *out, int want_force, int next)
+{
+    if (gas_on(g)) {
+        dfv::GasArgs a;
+        a.inst = g->d_ginst;
+        a.tmap = g->d_tmaps;
+        a.items = nullptr;
+        a.nitems = g->gas_tiles;
+        a.queue = nullptr;
+        a.un = (const float *)un;
+        a.out = (float *)out;
+        a.Gam = g->g.mc_f[0].Gam;
+        a.invGam = g->g.mc_f[0].invGam;
+        a.pref0 = g->g.mc_f[0].pref0;
+        (void)in;   // the tensor maps address the stage input (U^n, U1, U3 for stages 1-3)
+        DFV_CU(g, dfv::gas_stage(s, a, g->gas_grid, g->stream), "k_gas_stage");
+        return DFV_OK;
+    }
+    DFV_CU(g, g->ops->stage(s, g->g, in, un, out, g->ctl, g->partials, want_force, next, g->stream), "k_stage");
+    return DFV_OK;
+}
+
 // fin_in: mode of the previous step's deferred finalize to run in this step's
 // seeding launch (0: none); defer: leave this step's finalize pending.
 dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false, int fin_in = 0, bool defer = false)
@@ -255,13 +301,12 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false, int 
     }
     DFV_CU(g, g->ops->seed(g->g, g->U, g->U1, g->ctl, fin_in, g->stream), "k_seed");
     if (rec) DFV_CU(g, cudaEventRecord(ev[1], g->stream), "event");
-    DFV_CU(g, g->ops->stage(1, g->g, g->U, g->U, g->U1, g->ctl, g->partials, want_force, fin_in != 0 ? 1 : 0,
-                            g->stream),
-           "k_stage<1>");
+    dfv_status ss = launch_stage(g, 1, g->U, g->U, g->U1, want_force, fin_in != 0 ? 1 : 0);
+    if (ss != DFV_OK) return ss;
     if (rec) DFV_CU(g, cudaEventRecord(ev[2], g->stream), "event");
-    DFV_CU(g, g->ops->stage(2, g->g, g->U1, g->U, g->U3, g->ctl, g->partials, 0, 0, g->stream), "k_stage<2>");
+    if ((ss = launch_stage(g, 2, g->U1, g->U, g->U3, 0, 0)) != DFV_OK) return ss;
     if (rec) DFV_CU(g, cudaEventRecord(ev[3], g->stream), "event");
-    DFV_CU(g, g->ops->stage(3, g->g, g->U3, g->U, g->U, g->ctl, g->partials, 0, 0, g->stream), "k_stage<3>");
+    if ((ss = launch_stage(g, 3, g->U3, g->U, g->U, 0, 0)) != DFV_OK) return ss;
     if (rec) DFV_CU(g, cudaEventRecord(ev[4], g->stream), "event");
     // one block: CFL maximum (folded by the stage-3 tiles), force sum, body
     // update, next dt
@@ -377,6 +422,48 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
         delete g;
         return DFV_ERR_CUDA;
     }
+    // the gas kernel's tensor maps over U, U1, U3 and its instance record
+    g->d_tmaps = (CUtensorMap *)(g->ws + L.off_gas);
+    g->d_ginst = (dfv::GasInst *)(g->ws + L.off_gas + 3 * sizeof(CUtensorMap));
+    if (!opt->general_stage && precision == DFV_FP32 && dim == 2 && opt->nmat == 1 && g->solid == 0 &&
+        !p.periodic[0] && !p.periodic[1] && p.n[0] % 4 == 0) {
+        CUtensorMap maps[3];
+        const void *bases[3] = {g->U, g->U1, g->U3};
+        if (dfv::gas_encode_maps(maps, bases, 0, p.n[0], p.n[1], p.pitch)) {
+            dfv::GasInst I;
+            memset(&I, 0, sizeof(I));
+            I.n0 = p.n[0];
+            I.n1 = p.n[1];
+            I.tiles_x = (p.n[0] + dfv::GasT::TX - 1) / dfv::GasT::TX;
+            I.ntiles = I.tiles_x * ((p.n[1] + dfv::GasT::TY - 1) / dfv::GasT::TY);
+            I.off = 0;
+            I.pitch = p.pitch;
+            I.dx = (float)p.dx[0];
+            I.dy = (float)p.dx[1];
+            I.idx = (float)p.inv_dx[0];
+            I.idy = (float)p.inv_dx[1];
+            I.wall_x0 = p.wall[0][0];
+            I.wall_x1 = p.wall[0][1];
+            I.wall_y0 = p.wall[1][0];
+            I.wall_y1 = p.wall[1][1];
+            I.ctl = g->ctl;
+            int dev = 0, sms = 152;
+            e = dfv::gas_prepare();
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, g->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_ginst, &I, sizeof(I), cudaMemcpyHostToDevice, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+            if (e != cudaSuccess) {
+                delete g;
+                return DFV_ERR_CUDA;
+            }
+            g->gas_tiles = I.ntiles;
+            const long long persistent = (long long)sms * dfv::gas_max_ctas_per_sm();
+            g->gas_grid = (int)std::max(1LL, std::min(persistent, g->gas_tiles));
+            g->gas_ready = true;
+        }
+    }
     k_init_ctl<<<1, 1, 0, g->stream>>>(g->ctl);
     g->launches++;
     e = cudaGetLastError();
@@ -471,6 +558,7 @@ dfv_status dfv_set_body(dfv_grid *g, const double v[3], const double x[3], doubl
     g->launches++;
     DFV_CU(g, cudaGetLastError(), "k_set_body");
     g->dynamic = dynamic != 0;
+    g->body_moving = vv[0] != 0.0 || vv[1] != 0.0 || vv[2] != 0.0;
     g->smax_valid = false;   // the body speed enters the CFL bound
     g->dt_valid = false;
     g->graph_ready = false;

@@ -14,6 +14,7 @@
 
 #include "../../include/dfvrb.h"
 #include "dfv_batch.cuh"
+#include "dfv_gas.cuh"
 #include "dfv_ops.h"
 
 using dfv::BatchArgs;
@@ -28,8 +29,9 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Plan {
     size_t off_inst, off_items0, off_items1, off_ctl, off_ctlbak, off_part, off_queue, off_vbody;
+    size_t off_ginst, off_tmaps, off_gitems0, off_gitems1;   // the gas stage kernel's records
     size_t off_U, off_U1, off_U3, off_Ubak, off_stage, total;
-    long long elems, nitems, max_cells, ntiles_total;
+    long long elems, nitems, max_cells, ntiles_total, gas_nitems;
     std::vector<long long> inst_off, inst_part0;
     std::vector<int> tiles_x, tiles_y;
 };
@@ -63,6 +65,10 @@ bool plan_batch(int count, const dfv_instance_desc *desc, int precision, int nma
         P.nitems += (long long)P.tiles_x[i] * P.tiles_y[i];
         P.max_cells = std::max(P.max_cells, nc);
     }
+    P.gas_nitems = 0;
+    for (int i = 0; i < count; i++)
+        P.gas_nitems += (long long)((desc[i].n[0] + dfv::GasT::TX - 1) / dfv::GasT::TX) *
+                        ((desc[i].n[1] + dfv::GasT::TY - 1) / dfv::GasT::TY);
     P.ntiles_total = P.nitems;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -78,6 +84,10 @@ bool plan_batch(int count, const dfv_instance_desc *desc, int precision, int nma
     P.off_part = take(sizeof(double) * 4 * P.nitems);
     P.off_queue = take(sizeof(unsigned int) * 8);
     P.off_vbody = take(sizeof(double) * 3 * count);
+    P.off_ginst = take(sizeof(dfv::GasInst) * count);
+    P.off_tmaps = take(sizeof(CUtensorMap) * 3 * count);
+    P.off_gitems0 = take(sizeof(int2) * P.gas_nitems);
+    P.off_gitems1 = take(sizeof(int2) * P.gas_nitems);
     P.off_U = take((size_t)w * P.elems);
     P.off_U1 = take((size_t)w * P.elems);
     P.off_U3 = take((size_t)w * P.elems);
@@ -120,6 +130,13 @@ struct dfv_batch {
     bool graph_ready = false;
     long long graph_launches = 0;   // kernels in one replay of the step graph
     bool prof = false;
+    // the 2-D single-gas FP32 stage kernel (dfv_gas.cuh): tensor maps,
+    // instance records and (instance, tile) lists of its 32 x 16 tiles
+    bool gas = false;
+    int gas_max_ctas = 1;
+    dfv::GasInst *d_ginst = nullptr;
+    CUtensorMap *d_tmaps = nullptr;
+    int2 *d_gitems[2] = {nullptr, nullptr};
     std::vector<std::array<cudaEvent_t, 5>> ev_steps;
     std::vector<cudaEvent_t> ev_free;
     std::string err;
@@ -192,6 +209,26 @@ dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out
     // seeding: SEED_CTAS per instance (the launcher multiplies); finalize: one
     // per instance; CFL: one CTA per work item
     const bool per_inst = (ph == 0 || ph == 5 || ph == 6 || ph == 7);
+    if (b->gas && ph >= 1 && ph <= 3) {
+        const dfv::MatC<float> &m = b->hinst[0].g.mc_f[0];
+        dfv::GasArgs ga;
+        ga.inst = b->d_ginst;
+        ga.tmap = b->d_tmaps;
+        ga.items = b->d_gitems[b->schedule == 0 ? 0 : 1];
+        ga.nitems = b->plan.gas_nitems;
+        ga.queue = a.queue;
+        ga.un = (const float *)un;
+        ga.out = (float *)out;
+        ga.Gam = m.Gam;
+        ga.invGam = m.invGam;
+        ga.pref0 = m.pref0;
+        const long long n = b->plan.gas_nitems;
+        const long long persistent = (long long)b->sm_count * std::min(std::max(b->ctas_per_sm, 1), b->gas_max_ctas);
+        const int grid = (int)std::max(1LL, b->ctas_per_sm <= 0 ? n : std::min(persistent, n));
+        B_CU(b, dfv::gas_stage(ph, ga, grid, b->stream), "gas stage kernel");
+        b->launches++;
+        return DFV_OK;
+    }
     const int grid = per_inst ? b->count : (light ? (int)std::max(1LL, b->plan.nitems) : grid_size(b));
     B_CU(b, b->kern.launch(ph, grid, a, b->seed_opt, b->stream), "batch kernel");
     b->launches++;
@@ -383,6 +420,57 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    // the gas stage kernel: one FP32 gas, no HLLC-LM, every instance with a
+    // static body, no periodic side and rows of a multiple of 4 cells
+    b->d_ginst = (dfv::GasInst *)(b->ws + P.off_ginst);
+    b->d_tmaps = (CUtensorMap *)(b->ws + P.off_tmaps);
+    b->d_gitems[0] = (int2 *)(b->ws + P.off_gitems0);
+    b->d_gitems[1] = (int2 *)(b->ws + P.off_gitems1);
+    bool gas = !opt->general_stage && precision == DFV_FP32 && opt->nmat == 1 && !opt->hllc_lm;
+    for (int i = 0; i < count && gas; i++) {
+        const int per[3] = {b->hinst[i].g.periodic[0], b->hinst[i].g.periodic[1], 0};
+        const bool moving = desc[i].v_body[0] != 0.0 || desc[i].v_body[1] != 0.0 || desc[i].v_body[2] != 0.0;
+        gas = dfv::gas_eligible(1, 2, 1, 0, DFV_MAT_IDEAL, per, 0, moving, desc[i].n[0]);
+    }
+    std::vector<dfv::GasInst> ginst;
+    std::vector<CUtensorMap> gmaps;
+    std::vector<int2> gitems0, gitems1;
+    if (gas) {
+        ginst.resize(count);
+        gmaps.resize(3 * (size_t)count);
+        const void *bases[3] = {b->U, b->U1, b->U3};
+        for (int i = 0; i < count && gas; i++) {
+            const GridP &p = b->hinst[i].g;
+            dfv::GasInst &G = ginst[i];
+            memset(&G, 0, sizeof(G));
+            G.n0 = p.n[0];
+            G.n1 = p.n[1];
+            G.tiles_x = (p.n[0] + dfv::GasT::TX - 1) / dfv::GasT::TX;
+            G.ntiles = G.tiles_x * ((p.n[1] + dfv::GasT::TY - 1) / dfv::GasT::TY);
+            G.off = b->hinst[i].off;
+            G.pitch = p.pitch;
+            G.dx = (float)p.dx[0];
+            G.dy = (float)p.dx[1];
+            G.idx = (float)p.inv_dx[0];
+            G.idy = (float)p.inv_dx[1];
+            G.wall_x0 = p.wall[0][0];
+            G.wall_x1 = p.wall[0][1];
+            G.wall_y0 = p.wall[1][0];
+            G.wall_y1 = p.wall[1][1];
+            G.ctl = b->d_ctl + i;
+            gas = dfv::gas_encode_maps(&gmaps[3 * (size_t)i], bases, G.off, G.n0, G.n1, G.pitch);
+        }
+        if (gas) {
+            for (int i = 0; i < count; i++)
+                for (int t = 0; t < ginst[i].ntiles; t++) gitems0.push_back(make_int2(i, t));
+            std::vector<int> gord(count);
+            std::iota(gord.begin(), gord.end(), 0);
+            std::stable_sort(gord.begin(), gord.end(),
+                             [&](int x, int y) { return ginst[x].ntiles > ginst[y].ntiles; });
+            for (int i : gord)
+                for (int t = 0; t < ginst[i].ntiles; t++) gitems1.push_back(make_int2(i, t));
+        }
+    }
     cudaError_t e = b->kern.prepare();
     if (e == cudaSuccess) {
         b->max_ctas = b->kern.max_ctas_per_sm();
@@ -395,6 +483,25 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
                             b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_vbody, vb.data(), sizeof(double) * vb.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && gas) {
+        e = dfv::gas_prepare();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_ginst, ginst.data(), sizeof(dfv::GasInst) * count, cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_tmaps, gmaps.data(), sizeof(CUtensorMap) * gmaps.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_gitems[0], gitems0.data(), sizeof(int2) * gitems0.size(),
+                                cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_gitems[1], gitems1.data(), sizeof(int2) * gitems1.size(),
+                                cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) {
+            b->gas = true;
+            b->gas_max_ctas = dfv::gas_max_ctas_per_sm();
+        }
+    }
     if (e == cudaSuccess) {
         dfv::k_batch_init_ctl<<<(count + 255) / 256, 256, 0, b->stream>>>(b->d_ctl, count, b->d_vbody);
         e = cudaGetLastError();
@@ -533,8 +640,9 @@ dfv_status dfv_batch_autotune(dfv_batch *b, int trial_steps, double cfl, int cho
     int best_c = b->ctas_per_sm, best_s = b->schedule;
     const bool prof = b->prof;
     b->prof = false;
+    const int cmax = b->gas ? b->gas_max_ctas : b->max_ctas;
     for (int sched = 0; sched < 3; sched++)
-        for (int c = 0; c <= b->max_ctas; c++) {
+        for (int c = 0; c <= cmax; c++) {
             b->schedule = sched;
             b->ctas_per_sm = c;
             batch_step(b, false);   // warm
@@ -574,7 +682,7 @@ dfv_status dfv_batch_set_schedule(dfv_batch *b, int ctas_per_sm, int schedule)
     if (!b) return DFV_ERR_ARG;
     if (ctas_per_sm < 0 || schedule < 0 || schedule > 2)
         return bfail(b, DFV_ERR_ARG, "dfv_batch_set_schedule: bad arguments");
-    b->ctas_per_sm = std::min(ctas_per_sm, b->max_ctas);
+    b->ctas_per_sm = std::min(ctas_per_sm, b->gas ? b->gas_max_ctas : b->max_ctas);
     b->schedule = schedule;
     b->graph_ready = false;
     return DFV_OK;

@@ -203,7 +203,7 @@ __device__ __forceinline__ void ctl_sync_v(Ctl *c)
     for (int d = 0; d < 3; d++) c->vf[d] = (float)c->v[d];
 }
 
-enum { ERR_STATE = 1u, ERR_SOUND = 2u };
+enum { ERR_STATE = 1u, ERR_SOUND = 2u, ERR_TIMEOUT = 4u };   // ERR_TIMEOUT: a bounded device wait ran out
 
 // Programmatic dependent launch: the kernels of a step are launched with
 // launch_pdl, so a kernel's CTAs may be scheduled while the previous kernel

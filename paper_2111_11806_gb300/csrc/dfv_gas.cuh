@@ -1,0 +1,514 @@
+// dfv_gas.cuh -- the SSP-RK3 stage (Sec. 3.1) of 2-D single-gas grids in FP32
+// (ideal or stiffened gas, static body, transmissive or reflective sides):
+// the form of the cylinder and of the batched ellipse workloads.
+//
+// One persistent kernel per stage serves single grids and batches: a CTA
+// loops over (instance, tile) items, and while it computes one tile the
+// conserved planes of its next tile (32 x 16 cells, a halo of 2, five planes)
+// arrive in shared memory by one TMA tensor copy (cp.async.bulk.tensor, a
+// tensor map over the instance's planes in this GPU's memory, completion on an
+// mbarrier).  Per tile:
+//   1. conversion: each loaded cell to primitives (rho, u, v, p) once;
+//   2. slopes: each cell's van Leer slopes in x and y once, its two
+//      right/top face values to shared memory, its left/bottom ones kept;
+//   3. faces: each thread the HLLC flux of its cell's left x-face and bottom
+//      y-face (an extra warp the tile's closing faces);
+//   4. update: flux divergence with a compensated (TwoSum) sum, the rigid
+//      mask, the RK combination, and in stage 3 the CFL maximum and the box of
+//      the new rigid cells.
+// Without a moving body the upwind r flux vanishes and r needs no
+// reconstruction, so a halo of 2 suffices (MUSCL).  The arithmetic per face
+// and per cell is that of the general stage kernel (dfv_kernels.cuh) written
+// for one gas: p = p_ref + Gamma (rho E - rho |u|^2/2), c^2 = (Gamma p + p -
+// p_ref)/rho (Sec. 2.1.2).
+#pragma once
+
+#include <cuda.h>
+
+#include "dfv_kernels.cuh"
+
+namespace dfv {
+
+// one grid served by the gas stage kernel
+struct GasInst {
+    int n0, n1;
+    int tiles_x, ntiles;
+    long long off;       // element offset of the instance's planes
+    long long pitch;     // elements between planes
+    float idx, idy;      // 1/dx, 1/dy
+    float dx, dy;
+    int wall_x0, wall_x1, wall_y0, wall_y1;   // reflective sides
+    Ctl *ctl;
+    long long pad;
+};
+
+struct GasArgs {
+    const GasInst *inst;
+    const CUtensorMap *tmap;   // 3 per instance: the planes of U^n, U1, U3
+    const int2 *items;         // (instance, tile); nullptr: instance 0, tile = item
+    long long nitems;
+    unsigned int *queue;       // dynamic schedule counter (nullptr: static round-robin)
+    const float *un;           // U^n (instance planes at inst.off)
+    float *out;                // stage output
+    float Gam, invGam, pref0;  // the gas: Gamma, 1/Gamma, constant p_ref
+};
+
+struct GasT {
+    static constexpr int TX = 32, TY = 16, H = 2;
+    static constexpr int BX = TX + 8;          // TMA box width: x from ox-4 (16-byte aligned)
+    static constexpr int BY = TY + 2 * H;      // box height: y from oy-2
+    static constexpr int NP = 5;               // planes of the single-gas 2-D layout
+    static constexpr int BOX = BX * BY;        // cells of one plane of the box
+    static constexpr int PX = TX + 2 * H, PY = TY + 2 * H;   // primitives of the tile and halo
+    static constexpr int CELLS = TX * TY;
+    static constexpr int THREADS = CELLS + 32;               // + one warp for halo slopes and closing faces
+    static constexpr int NCONV = TY * PX + 2 * H * TX;       // loaded cells needed (corners not)
+    static constexpr int FXS = TX + 1;         // x-face arrays: columns -1 .. TX-1 (values) / 0 .. TX (fluxes)
+    static constexpr int FYS = TY + 1;
+    static constexpr unsigned BOX_BYTES = 4u * NP * BOX;
+};
+
+struct GasSmem {
+    float tile[2][GasT::NP][GasT::BOX];            // TMA destination, double-buffered
+    float prim[4][GasT::PY][GasT::PX];             // rho, u, v, p of the tile and halo
+    float fvx[4][GasT::TY][GasT::FXS];             // right-face values q_{i+1/2}^L, column i = -1 .. TX-1
+    float fvy[4][GasT::FYS][GasT::TX];             // top-face values, row j = -1 .. TY-1
+    float hrx[4][GasT::TY];                        // left-face values of column TX (closing x faces)
+    float hry[4][GasT::TX];                        // bottom-face values of row TY (closing y faces)
+    float fx[4][GasT::TY][GasT::FXS];              // fluxes of x faces i-1/2, i = 0 .. TX
+    float fy[4][GasT::FYS][GasT::TX];              // fluxes of y faces j-1/2, j = 0 .. TY
+    double red[32];
+    unsigned long long mbar[2];
+    long long item[2];
+    int flag;
+};
+
+// ------------------------------------------------------------ TMA, mbarrier
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase of parity `parity` to complete; false when the
+// iteration limit ran out (the caller reports it and stops).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (int it = 0; it < (1 << 22); it++) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// One 3-D tensor copy (x, y, plane) of a box into shared memory.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ------------------------------------------------------------ arithmetic
+
+// van Leer limited slope of a cell from its backward and forward differences
+__device__ __forceinline__ float gas_vanleer(float a, float b)
+{
+    const float ab = a * b;
+    return ab <= 0.f ? 0.f : 2.f * ab / (a + b);
+}
+
+// Conserved (rho, rho u, rho v, rho E) -> primitive (rho, u, v, p) of the gas.
+__device__ __forceinline__ void gas_prim(const GasArgs &a, float r, float mu, float mv, float E, float w[4])
+{
+    const float ir = 1.f / r;
+    const float u = mu * ir, v = mv * ir;
+    const float ke = 0.5f * r * u * u + 0.5f * r * v * v;
+    w[0] = r;
+    w[1] = u;
+    w[2] = v;
+    w[3] = a.pref0 + a.Gam * (E - ke);
+}
+
+// HLLC flux of the gas across a face (Sec. 3.1: Toro's HLLC with Davis wave
+// speeds), normal velocity un, tangential ut; F = (rho, normal momentum,
+// tangential momentum, energy).
+__device__ __forceinline__ void gas_hllc(const GasArgs &a, float rL, float unL, float utL, float pL, float rR,
+                                         float unR, float utR, float pR, float F[4])
+{
+    const float irL = 1.f / rL, irR = 1.f / rR;
+    const float cL = sqrtf((a.Gam * pL + (pL - a.pref0)) * irL);
+    const float cR = sqrtf((a.Gam * pR + (pR - a.pref0)) * irR);
+    const float SL = fminf(unL - cL, unR - cR);
+    const float SR = fmaxf(unL + cL, unR + cR);
+    // contact speed, the numerator's products rounded one by one (a wall face
+    // between mirror-image states gets S* = 0 exactly)
+    const float num = __fadd_rn(__fadd_rn(pR - pL, __fmul_rn(__fmul_rn(rL, unL), SL - unL)),
+                                -__fmul_rn(__fmul_rn(rR, unR), SR - unR));
+    const float Ss = num / (rL * (SL - unL) - rR * (SR - unR));
+    // regions: left of S_L, left star, right star, right of S_R
+    const int region = SL >= 0.f ? 0 : (Ss >= 0.f ? 1 : (SR > 0.f ? 2 : 3));
+    const bool left = region <= 1;
+    const float r = left ? rL : rR, un = left ? unL : unR, ut = left ? utL : utR, p = left ? pL : pR;
+    const float S = left ? SL : SR;
+    const float E = (p - a.pref0) * a.invGam + 0.5f * r * un * un + 0.5f * r * ut * ut;
+    const float m = r * un;
+    // physical flux of the upwind side
+    float Fr = m, Fn = m * un + p, Ft = m * ut, FE = (E + p) * un;
+    const bool star = region == 1 || region == 2;
+    if (star) {
+        // star state U*_K = rho_K (S_K - u_K)/(S_K - S*) [1, S*, u_t, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))]
+        const float chi = (S - un) / (S - Ss);
+        const float rs = r * chi;
+        const float Es = rs * (E / r + (Ss - un) * (Ss + p / (r * (S - un))));
+        Fr += S * (rs - r);
+        Fn += S * (rs * Ss - m);
+        Ft += S * (rs * ut - r * ut);
+        FE += S * (Es - E);
+    }
+    F[0] = Fr;
+    F[1] = Fn;
+    F[2] = Ft;
+    F[3] = FE;
+}
+
+// Loaded cell (lx, ly) of the tile at (ox, oy) -> box index; the halo beyond
+// a side is the nearest cell (transmissive) or the mirror image (wall; *fx,
+// *fy set).  Cells far outside the grid (halo of a ragged tile) map to some
+// loaded cell: they feed only faces outside the grid.
+__device__ __forceinline__ int gas_box_index(const GasInst &I, int ox, int oy, int lx, int ly, bool *fx, bool *fy)
+{
+    int gx = ox + lx, gy = oy + ly;
+    *fx = *fy = false;
+    if (gx < 0) {
+        if (I.wall_x0) {
+            gx = -1 - gx;
+            *fx = true;
+        } else {
+            gx = 0;
+        }
+    } else if (gx > I.n0 - 1) {
+        if (I.wall_x1) {
+            gx = 2 * I.n0 - 1 - gx;
+            *fx = true;
+        } else {
+            gx = I.n0 - 1;
+        }
+    }
+    if (gy < 0) {
+        if (I.wall_y0) {
+            gy = -1 - gy;
+            *fy = true;
+        } else {
+            gy = 0;
+        }
+    } else if (gy > I.n1 - 1) {
+        if (I.wall_y1) {
+            gy = 2 * I.n1 - 1 - gy;
+            *fy = true;
+        } else {
+            gy = I.n1 - 1;
+        }
+    }
+    int bx = gx - (ox - 4), by = gy - (oy - GasT::H);
+    bx = bx < 0 ? 0 : (bx > GasT::BX - 1 ? GasT::BX - 1 : bx);
+    by = by < 0 ? 0 : (by > GasT::BY - 1 ? GasT::BY - 1 : by);
+    return by * GasT::BX + bx;
+}
+
+__device__ __forceinline__ long long gas_next(const GasArgs &a, long long cur, int k)
+{
+    if (!a.queue) return (long long)blockIdx.x + (long long)(k + 1) * gridDim.x;
+    (void)cur;
+    return (long long)atomicAdd(a.queue, 1u);
+}
+
+// ------------------------------------------------------------ the stage
+
+template <int STAGE>
+__global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
+{
+    using T = GasT;
+    extern __shared__ __align__(128) unsigned char gas_smem_raw[];
+    GasSmem &S = *reinterpret_cast<GasSmem *>(gas_smem_raw);
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    pdl_enter();   // the previous kernel (its writes of the stage input) is complete
+    if (tid == 0) {
+        const long long first = a.queue ? (long long)atomicAdd(a.queue, 1u) : (long long)blockIdx.x;
+        S.item[0] = first;
+        S.flag = 0;
+        if (first < a.nitems) {
+            const int2 w = a.items ? a.items[first] : make_int2(0, (int)first);
+            const GasInst &I = a.inst[w.x];
+            mbar_expect_tx(&S.mbar[0], T::BOX_BYTES);
+            tma_load_3d(&S.tile[0][0][0], a.tmap + 3 * w.x + (STAGE - 1), (w.y % I.tiles_x) * T::TX - 4,
+                        (w.y / I.tiles_x) * T::TY - T::H, 0, &S.mbar[0]);
+        }
+    }
+    __syncthreads();
+
+    const float ca = STAGE == 2 ? 0.75f : (STAGE == 3 ? 1.f / 3.f : 0.f);
+    const float cb = STAGE == 2 ? 0.25f : (STAGE == 3 ? 2.f / 3.f : 1.f);
+    const int ci = tid & 31, cj = tid >> 5;   // the thread's cell (tid < CELLS)
+
+    for (int k = 0;; k++) {
+        const long long it = S.item[k & 1];
+        if (it >= a.nitems) break;
+        const int buf = k & 1;
+        const int2 w = a.items ? a.items[it] : make_int2(0, (int)it);
+        const GasInst &I = a.inst[w.x];
+        const int tile = w.y;
+        const int ox = (tile % I.tiles_x) * T::TX, oy = (tile / I.tiles_x) * T::TY;
+        // the next item's planes into the other buffer (its last reader, the
+        // previous item, is behind the barrier that ended it)
+        if (tid == 0) {
+            const long long nx = gas_next(a, it, k);
+            S.item[(k + 1) & 1] = nx;
+            if (nx < a.nitems) {
+                const int2 wn = a.items ? a.items[nx] : make_int2(0, (int)nx);
+                const GasInst &In = a.inst[wn.x];
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&S.mbar[buf ^ 1], T::BOX_BYTES);
+                tma_load_3d(&S.tile[buf ^ 1][0][0], a.tmap + 3 * wn.x + (STAGE - 1), (wn.y % In.tiles_x) * T::TX - 4,
+                            (wn.y / In.tiles_x) * T::TY - T::H, 0, &S.mbar[buf ^ 1]);
+            }
+        }
+        const bool ok = mbar_wait(&S.mbar[buf], (unsigned)((k >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            // a copy that never completed: report it, let the prefetch in
+            // flight land (bounded) and stop
+            if (tid == 0) {
+                atomicOr(&I.ctl->err, (unsigned)ERR_TIMEOUT);
+                if (S.item[(k + 1) & 1] < a.nitems) (void)mbar_wait(&S.mbar[buf ^ 1], (unsigned)(((k + 1) >> 1) & 1));
+            }
+            break;
+        }
+        const float *tl = &S.tile[buf][0][0];
+        const bool interior = ox >= 2 && ox + T::TX + 2 <= I.n0 && oy >= 2 && oy + T::TY + 2 <= I.n1;
+
+        // 1. primitives of the tile and its halo (corners not needed)
+        for (int q = tid; q < T::NCONV; q += T::THREADS) {
+            int lx, ly;
+            if (q < T::TY * T::PX) {
+                ly = q / T::PX;
+                lx = q - ly * T::PX - T::H;
+            } else {
+                const int r = q - T::TY * T::PX;
+                const int row = r / T::TX;
+                lx = r - row * T::TX;
+                ly = row < 2 ? row - 2 : T::TY + (row - 2);
+            }
+            bool fx = false, fy = false;
+            const int b = interior ? (ly + T::H) * T::BX + (lx + 4) : gas_box_index(I, ox, oy, lx, ly, &fx, &fy);
+            float wv[4];
+            gas_prim(a, tl[b], tl[T::BOX + b], tl[2 * T::BOX + b], tl[3 * T::BOX + b], wv);
+            if (fx) wv[1] = -wv[1];
+            if (fy) wv[2] = -wv[2];
+#pragma unroll
+            for (int v = 0; v < 4; v++) S.prim[v][ly + T::H][lx + T::H] = wv[v];
+        }
+        __syncthreads();
+
+        // 2. slopes once per cell; right/top face values to shared memory
+        float qRx[4], qRy[4];
+        if (tid < T::CELLS) {
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const float q = S.prim[v][cj + T::H][ci + T::H];
+                const float sx = gas_vanleer(q - S.prim[v][cj + T::H][ci + T::H - 1], S.prim[v][cj + T::H][ci + T::H + 1] - q);
+                const float sy = gas_vanleer(q - S.prim[v][cj + T::H - 1][ci + T::H], S.prim[v][cj + T::H + 1][ci + T::H] - q);
+                S.fvx[v][cj][ci + 1] = q + 0.5f * sx;
+                S.fvy[v][cj + 1][ci] = q + 0.5f * sy;
+                qRx[v] = q - 0.5f * sx;
+                qRy[v] = q - 0.5f * sy;
+            }
+        } else {
+            // the extra warp: right-face values of column -1 and top-face
+            // values of row -1, left-face values of column TX and bottom-face
+            // values of row TY
+            const int l = tid - T::CELLS, jh = l & 15;
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const float (*P)[T::PX] = S.prim[v];
+                const float qa = P[jh + T::H][T::H - 1];
+                const float sa = gas_vanleer(qa - P[jh + T::H][T::H - 2], P[jh + T::H][T::H] - qa);
+                const float qb = P[T::H - 1][l + T::H];
+                const float sb = gas_vanleer(qb - P[T::H - 2][l + T::H], P[T::H][l + T::H] - qb);
+                const float qc = P[jh + T::H][T::TX + T::H];
+                const float sc = gas_vanleer(qc - P[jh + T::H][T::TX + T::H - 1], P[jh + T::H][T::TX + T::H + 1] - qc);
+                const float qd = P[T::TY + T::H][l + T::H];
+                const float sd = gas_vanleer(qd - P[T::TY + T::H - 1][l + T::H], P[T::TY + T::H + 1][l + T::H] - qd);
+                if (l < 16) {
+                    S.fvx[v][jh][0] = qa + 0.5f * sa;
+                    S.hrx[v][jh] = qc - 0.5f * sc;
+                }
+                S.fvy[v][0][l] = qb + 0.5f * sb;
+                S.hry[v][l] = qd - 0.5f * sd;
+            }
+        }
+        __syncthreads();
+
+        // 3. faces: the cell's left x face and bottom y face
+        float Fxl[4], Fyl[4];
+        if (tid < T::CELLS) {
+            gas_hllc(a, S.fvx[0][cj][ci], S.fvx[1][cj][ci], S.fvx[2][cj][ci], S.fvx[3][cj][ci], qRx[0], qRx[1],
+                     qRx[2], qRx[3], Fxl);
+            float G[4];
+            gas_hllc(a, S.fvy[0][cj][ci], S.fvy[2][cj][ci], S.fvy[1][cj][ci], S.fvy[3][cj][ci], qRy[0], qRy[2],
+                     qRy[1], qRy[3], G);
+            // y face: normal momentum is rho v, tangential rho u
+            Fyl[0] = G[0];
+            Fyl[1] = G[2];
+            Fyl[2] = G[1];
+            Fyl[3] = G[3];
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                S.fx[v][cj][ci] = Fxl[v];
+                S.fy[v][cj][ci] = Fyl[v];
+            }
+        } else {
+            const int l = tid - T::CELLS, jh = l & 15;
+            float G[4];
+            if (l < 16) {
+                gas_hllc(a, S.fvx[0][jh][T::TX], S.fvx[1][jh][T::TX], S.fvx[2][jh][T::TX], S.fvx[3][jh][T::TX],
+                         S.hrx[0][jh], S.hrx[1][jh], S.hrx[2][jh], S.hrx[3][jh], G);
+#pragma unroll
+                for (int v = 0; v < 4; v++) S.fx[v][jh][T::TX] = G[v];
+            }
+            gas_hllc(a, S.fvy[0][T::TY][l], S.fvy[2][T::TY][l], S.fvy[1][T::TY][l], S.fvy[3][T::TY][l], S.hry[0][l],
+                     S.hry[2][l], S.hry[1][l], S.hry[3][l], G);
+            S.fy[0][T::TY][l] = G[0];
+            S.fy[1][T::TY][l] = G[2];
+            S.fy[2][T::TY][l] = G[1];
+            S.fy[3][T::TY][l] = G[3];
+        }
+        __syncthreads();
+
+        // 4. divergence, rigid mask, RK combination
+        Ctl *ctl = I.ctl;
+        const float dt = ctl_dt<float>(ctl);
+        const int gx = ox + ci, gy = oy + cj;
+        const bool inside = tid < T::CELLS && gx < I.n0 && gy < I.n1;
+        float smax_cell = 0.f;
+        bool rigid_new = false;
+        if (STAGE == 2 && tile == 0 && tid == 0) ctl_box_reset(ctl);
+        if (inside) {
+            const long long c = I.off + gx + (long long)I.n0 * gy;
+            const long long P = I.pitch;
+            const int bc = (cj + T::H) * T::BX + (ci + 4);
+            float o[5];
+            const float unr = a.un[c + 4 * P];
+            const bool masked = unr > 0.5f;
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const float unv = a.un[c + v * P];
+                const float div = (S.fx[v][cj][ci + 1] - Fxl[v]) * I.idx;
+                const float dvy = (S.fy[v][cj + 1][ci] - Fyl[v]) * I.idy;
+                Acc<float> D;
+                D.set(div);
+                D.add(dvy);
+                o[v] = masked ? unv : rk_combine<float>(STAGE, unv, tl[v * T::BOX + bc], D, dt, ca, cb);
+            }
+            {
+                // r: no flux without a moving body
+                Acc<float> D;
+                D.set(0.f);
+                D.add(0.f);
+                o[4] = rk_combine<float>(STAGE, unr, tl[4 * T::BOX + bc], D, dt, ca, cb);
+            }
+#pragma unroll
+            for (int v = 0; v < 5; v++) a.out[c + v * P] = o[v];
+            if (!(o[0] > 0.f) || !(o[3] == o[3])) atomicOr(&ctl->err, (unsigned)ERR_STATE);
+            if (STAGE == 3) {
+                rigid_new = o[4] > 0.5f;
+                float wv[4];
+                gas_prim(a, o[0], o[1], o[2], o[3], wv);
+                const float c2 = (a.Gam * wv[3] + (wv[3] - a.pref0)) / wv[0];
+                if (!(c2 > 0.f)) atomicOr(&ctl->err, (unsigned)ERR_SOUND);
+                const float cs = sqrtf(c2);
+                smax_cell = (fabsf(wv[1]) + cs) / I.dx + (fabsf(wv[2]) + cs) / I.dy;
+            }
+        }
+        if (STAGE == 3) {
+            // box of the new state's rigid cells and the tile's CFL maximum
+            if (__any_sync(0xffffffffu, rigid_new)) {
+                const int big = 0x7fffffff;
+                const int b6[4] = {rigid_new ? gx : big, rigid_new ? gy : big, rigid_new ? gx : -1,
+                                   rigid_new ? gy : -1};
+                const int mx0 = __reduce_min_sync(0xffffffffu, b6[0]), my0 = __reduce_min_sync(0xffffffffu, b6[1]);
+                const int mx1 = __reduce_max_sync(0xffffffffu, b6[2]), my1 = __reduce_max_sync(0xffffffffu, b6[3]);
+                if ((tid & 31) == 0) {
+                    atomicMin(&ctl->rnext[0], mx0);
+                    atomicMin(&ctl->rnext[1], my0);
+                    atomicMin(&ctl->rnext[2], 0);
+                    atomicMax(&ctl->rnext[3], mx1);
+                    atomicMax(&ctl->rnext[4], my1);
+                    atomicMax(&ctl->rnext[5], 0);
+                }
+            }
+            float *sr = reinterpret_cast<float *>(S.red);
+            const float m = block_max<T::THREADS, float>(smax_cell, sr);
+            if (tid == 0) {
+                double md = (double)m;
+                if (!(md >= 0.0)) md = __longlong_as_double(0x7ff0000000000000LL);   // NaN -> +inf: dt = 0
+                atomicMax(&ctl->smax_acc, (unsigned long long)__double_as_longlong(md));
+            }
+        }
+        __syncthreads();   // the item's buffers are free; S.item of the next item is visible
+    }
+}
+
+}  // namespace dfv
+
+namespace dfv {
+
+// Host side (dfv_gas_f32_k.cu).
+cudaError_t gas_prepare();                  // opt the kernels in to their shared memory
+int gas_max_ctas_per_sm();                  // resident CTAs per SM of the stage kernels
+cudaError_t gas_stage(int stage, const GasArgs &a, int grid, cudaStream_t st);
+// The three tensor maps (the planes of U^n, U1, U3) of one instance whose
+// planes start `off` elements into each buffer: 3-D (x, y, plane) over n0 x n1
+// x 5 floats with row stride n0 and plane stride pitch, box 40 x 20 x 5.
+bool gas_encode_maps(CUtensorMap maps[3], const void *const bases[3], long long off, int n0, int n1,
+                     long long pitch);
+
+// Whether a 2-D grid can take the gas stage kernel: FP32, one ideal or
+// stiffened gas, no solid, no periodic side, no HLLC-LM, a static body
+// (the upwind r flux vanishes) and rows whose byte length is a multiple of 16
+// (the tensor map's row stride).
+inline bool gas_eligible(int precision_fp32, int dim, int nmat, int solid, int mat_kind, const int periodic[3],
+                         int hllc_lm, bool moving_body, int n0)
+{
+    return precision_fp32 && dim == 2 && nmat == 1 && solid == 0 && (mat_kind == 0 || mat_kind == 1) &&
+           !periodic[0] && !periodic[1] && !hllc_lm && !moving_body && n0 % 4 == 0;
+}
+
+}  // namespace dfv

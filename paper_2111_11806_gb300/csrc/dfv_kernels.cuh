@@ -95,9 +95,11 @@ struct Acc {
     }
 };
 
-// out = ca*un + cb*(in - dt*D) with one final rounding in FP32 (error-free
-// products and TwoSum on every partial sum, the Dot2 scheme of Ogita, Rump &
-// Oishi); plain evaluation in FP64.
+// out = ca*un + cb*(in - dt*D), D = hi + lo the compensated (TwoSum) flux
+// divergence.  FP32: y = in - dt*lo - dt*hi as two fused multiply-adds (the
+// low part first), then ca*un rounded and cb*y added in a third fused
+// multiply-add -- three roundings, against the one of storing the result in
+// FP32; no error-free product is formed.  FP64: plain evaluation.
 template <class R>
 __device__ __forceinline__ R rk_combine(int stage, R un, R in, const Acc<R> &D, R dt, R ca, R cb)
 {
