@@ -147,8 +147,11 @@ dfv_status dfv_add_material(dfv_grid *g, int kind, const dfv_material_params *p,
  * variables uses the mixture rules of Sec. 2.2. */
 dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device);
 
-/* Copy the current fields out as FP64 planes: which = DFV_FIELDS_CONSERVED
- * or DFV_FIELDS_PRIMITIVE.  on_device selects a device or host destination. */
+/* Copy the current fields out as FP64 planes (layout above): which =
+ * DFV_FIELDS_CONSERVED, the vector U of the reduced system (Sec. 2.1.1,
+ * eq:sys_vec_form, with r, Sec. 2.3), or DFV_FIELDS_PRIMITIVE, the variables
+ * of the reconstruction (Sec. 3.1) from the mixture rules of Sec. 2.2.
+ * on_device selects a device or host destination; a host copy synchronises. */
 dfv_status dfv_get_fields(dfv_grid *g, double *out, int which, int on_device);
 
 /* Rigid-body velocity v_r (Sec. 2.3, eq:revo), position and mass.  dynamic =
@@ -157,7 +160,11 @@ dfv_status dfv_get_fields(dfv_grid *g, double *out, int which, int on_device);
  * v are used. */
 dfv_status dfv_set_body(dfv_grid *g, const double v[3], const double x[3], double mass, int dynamic);
 
-/* Force of the last step (evaluated after seeding), velocity and position. */
+/* The rigid body (Sec. 2.3): the pressure force of the last step, the sum
+ * of p grad(r) dV over the seeded state (the discrete form of the surface
+ * integral of -p n; not in the paper, which imposes v_r), and the body's
+ * velocity v_r and position.  Synchronises; DFV_ERR_NONPHYSICAL if a kernel
+ * flagged a state. */
 dfv_status dfv_get_body(dfv_grid *g, double force[3], double v[3], double x[3]);
 
 /* dt = cfl / max_cells sum_d (|u_d| + c)/dx_d (also covering the body speed)
@@ -201,6 +208,21 @@ dfv_status dfv_profile(dfv_grid *g, int enable, double ms_out[5], long long *ste
 /* Number of kernel launches issued by the library on this grid so far. */
 dfv_status dfv_launch_count(const dfv_grid *g, long long *count);
 
+/* Where the conserved state lies inside the caller's workspace, for reading
+ * it in place (checkpoints, in-situ analysis) without dfv_get_fields:
+ * off[0], off[1], off[2] = byte offsets of the planes of U^n (the current
+ * state) and of the SSP-RK3 stage buffers U1 and U3 (Sec. 3.1); *pitch =
+ * elements from one plane to the next (>= the cell count; the elements from
+ * the cell count to pitch-1 of every plane are never written); *nvar = planes
+ * (layout above); *elem_bytes = 8 (FP64) or 4 (FP32).  U^n is complete only
+ * after the stream has finished the last step (dfv_check).  Any output may be
+ * NULL. */
+dfv_status dfv_state_layout(const dfv_grid *g, size_t off[3], long long *pitch, int *nvar, int *elem_bytes);
+
+/* Release the grid's host memory (the grid of the problem statement,
+ * Sec. 3).  The workspace stays the caller's; work already issued on the
+ * stream is not waited for, so synchronise the stream before freeing the
+ * workspace. */
 dfv_status dfv_destroy(dfv_grid *g);
 
 /* ---------------------------------------------------------------- batches

@@ -24,7 +24,8 @@ MAT_KIND = {"ideal": 0, "stiffened": 1, "romenskii": 2}
 
 EXPORTS = ("dfv_workspace_bytes", "dfv_create_grid", "dfv_add_material", "dfv_set_fields", "dfv_get_fields",
            "dfv_set_body", "dfv_get_body", "dfv_compute_dt", "dfv_step", "dfv_run", "dfv_check",
-           "dfv_profile", "dfv_launch_count", "dfv_destroy", "dfv_last_error", "dfv_compute_dt_noalloc",
+           "dfv_profile", "dfv_launch_count", "dfv_state_layout", "dfv_destroy", "dfv_last_error",
+           "dfv_compute_dt_noalloc",
            "dfv_batch_workspace_bytes", "dfv_batch_create", "dfv_batch_add_material", "dfv_batch_set_fields",
            "dfv_batch_get_fields", "dfv_batch_run", "dfv_batch_autotune", "dfv_batch_set_schedule",
            "dfv_batch_get_time", "dfv_batch_profile", "dfv_batch_launch_count", "dfv_batch_destroy",
@@ -80,6 +81,7 @@ def load(path: str = LIB_PATH):
     L.dfv_check.argtypes = [_vp, ctypes.c_int]
     L.dfv_profile.argtypes = [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]
     L.dfv_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.dfv_state_layout.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_longlong), _ip, _ip]
     L.dfv_destroy.argtypes = [_vp]
     _bp = ctypes.POINTER(dfv_instance_desc)
     L.dfv_batch_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, _bp, ctypes.c_int, ctypes.POINTER(dfv_options),
@@ -193,7 +195,7 @@ class Grid:
 
     def __init__(self, dim, n, lo, hi, materials, solid=False, precision=DFV_FP64, periodic=None,
                  use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0, normal_method=0, probe_mode=0,
-                 walls=None, device="cuda:0", stream=None, general_stage=False):
+                 walls=None, device="cuda:0", stream=None, general_stage=False, workspace=None):
         import torch
         if not torch.cuda.is_available():
             raise DfvError("a CUDA device is required (no CPU fallback)")
@@ -211,7 +213,13 @@ class Grid:
         nbytes = workspace_bytes(dim, self.n, self.nmat, skind, precision)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            if workspace is None:
+                self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            else:
+                # a caller-owned uint8 device tensor of at least nbytes + 256 bytes
+                assert workspace.dtype == torch.uint8 and workspace.is_cuda and workspace.numel() >= nbytes + 256
+                self.workspace = workspace
+        self.workspace_bytes = nbytes
         base = self.workspace.data_ptr()
         aligned = (base + 255) & ~255
         bc = (ctypes.c_int * 6)(*bc_codes(dim, periodic, walls))
@@ -335,6 +343,20 @@ class Grid:
         c = ctypes.c_longlong()
         _check(load().dfv_launch_count(self._h, ctypes.byref(c)), self._h, "dfv_launch_count")
         return c.value
+
+    def state_layout(self):
+        """(byte offsets of U^n, U1, U3 from the workspace's aligned base,
+        plane pitch in elements, planes, bytes per element)."""
+        off = (ctypes.c_size_t * 3)()
+        pitch, nvar, eb = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        _check(load().dfv_state_layout(self._h, off, ctypes.byref(pitch), ctypes.byref(nvar), ctypes.byref(eb)),
+               self._h, "dfv_state_layout")
+        return tuple(off), pitch.value, nvar.value, eb.value
+
+    def aligned_offset(self):
+        """Offset of the library's 256-byte aligned workspace base in self.workspace."""
+        base = self.workspace.data_ptr()
+        return ((base + 255) & ~255) - base
 
 
 def _bcheck(status, handle, what):

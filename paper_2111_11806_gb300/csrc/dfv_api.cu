@@ -116,7 +116,7 @@ Layout plan(int dim, const int n[3], int nmat, int solid, int precision)
     L.off_part = off;
     off += align256(sizeof(double) * 4 * (size_t)nparts);
     L.off_gas = off;   // three tensor maps, then the gas kernel's instance record
-    off += align256(3 * sizeof(CUtensorMap) + sizeof(dfv::GasInst));
+    off += align256(dfv::GasT::NMAP * sizeof(CUtensorMap) + sizeof(dfv::GasInst));
     const size_t state = align256((size_t)w * nvar * (size_t)L.pitch);
     L.off_U = off;
     off += state;
@@ -424,10 +424,10 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
     }
     // the gas kernel's tensor maps over U, U1, U3 and its instance record
     g->d_tmaps = (CUtensorMap *)(g->ws + L.off_gas);
-    g->d_ginst = (dfv::GasInst *)(g->ws + L.off_gas + 3 * sizeof(CUtensorMap));
+    g->d_ginst = (dfv::GasInst *)(g->ws + L.off_gas + dfv::GasT::NMAP * sizeof(CUtensorMap));
     if (!opt->general_stage && precision == DFV_FP32 && dim == 2 && opt->nmat == 1 && g->solid == 0 &&
         !p.periodic[0] && !p.periodic[1] && p.n[0] % 4 == 0) {
-        CUtensorMap maps[3];
+        CUtensorMap maps[dfv::GasT::NMAP];
         const void *bases[3] = {g->U, g->U1, g->U3};
         if (dfv::gas_encode_maps(maps, bases, 0, p.n[0], p.n[1], p.pitch)) {
             dfv::GasInst I;
@@ -480,10 +480,8 @@ dfv_status dfv_add_material(dfv_grid *g, int kind, const dfv_material_params *m,
     if (!g) return DFV_ERR_ARG;
     if (!m) return fail(g, DFV_ERR_ARG, "dfv_add_material: null parameters");
     if (g->nmat >= g->nmat_opt) return fail(g, DFV_ERR_ARG, "dfv_add_material: all materials already added");
-    if (kind < DFV_MAT_IDEAL || kind > DFV_MAT_ROMENSKII) return fail(g, DFV_ERR_ARG, "dfv_add_material: bad kind");
-    if (kind != DFV_MAT_ROMENSKII && !(m->gamma > 1.0)) return fail(g, DFV_ERR_ARG, "dfv_add_material: gamma <= 1");
-    if (kind == DFV_MAT_ROMENSKII && !(m->rho0 > 0.0 && m->Gamma0 > 0.0 && m->alpha != 0.0))
-        return fail(g, DFV_ERR_ARG, "dfv_add_material: bad Romenskii parameters");
+    if (const char *why = dfv::material_problem(kind, m->gamma, m->rho0, m->Gamma0, m->alpha))
+        return fail(g, DFV_ERR_ARG, std::string("dfv_add_material: ") + why);
     dfv::MatP &p = g->g.mat[g->nmat];
     p.kind = kind;
     p.gamma = m->gamma;
@@ -730,6 +728,20 @@ dfv_status dfv_launch_count(const dfv_grid *g, long long *count)
 {
     if (!g || !count) return DFV_ERR_ARG;
     *count = g->launches;
+    return DFV_OK;
+}
+
+dfv_status dfv_state_layout(const dfv_grid *g, size_t off[3], long long *pitch, int *nvar, int *elem_bytes)
+{
+    if (!g) return DFV_ERR_ARG;
+    if (off) {
+        off[0] = (size_t)((const char *)g->U - g->ws);
+        off[1] = (size_t)((const char *)g->U1 - g->ws);
+        off[2] = (size_t)((const char *)g->U3 - g->ws);
+    }
+    if (pitch) *pitch = g->g.pitch;
+    if (nvar) *nvar = g->ops->nvar;
+    if (elem_bytes) *elem_bytes = g->precision == DFV_FP32 ? 4 : 8;
     return DFV_OK;
 }
 

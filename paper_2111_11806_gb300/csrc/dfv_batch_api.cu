@@ -85,7 +85,7 @@ bool plan_batch(int count, const dfv_instance_desc *desc, int precision, int nma
     P.off_queue = take(sizeof(unsigned int) * 8);
     P.off_vbody = take(sizeof(double) * 3 * count);
     P.off_ginst = take(sizeof(dfv::GasInst) * count);
-    P.off_tmaps = take(sizeof(CUtensorMap) * 3 * count);
+    P.off_tmaps = take(sizeof(CUtensorMap) * dfv::GasT::NMAP * count);
     P.off_gitems0 = take(sizeof(int2) * P.gas_nitems);
     P.off_gitems1 = take(sizeof(int2) * P.gas_nitems);
     P.off_U = take((size_t)w * P.elems);
@@ -437,7 +437,7 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     std::vector<int2> gitems0, gitems1;
     if (gas) {
         ginst.resize(count);
-        gmaps.resize(3 * (size_t)count);
+        gmaps.resize((size_t)dfv::GasT::NMAP * count);
         const void *bases[3] = {b->U, b->U1, b->U3};
         for (int i = 0; i < count && gas; i++) {
             const GridP &p = b->hinst[i].g;
@@ -458,7 +458,7 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
             G.wall_y0 = p.wall[1][0];
             G.wall_y1 = p.wall[1][1];
             G.ctl = b->d_ctl + i;
-            gas = dfv::gas_encode_maps(&gmaps[3 * (size_t)i], bases, G.off, G.n0, G.n1, G.pitch);
+            gas = dfv::gas_encode_maps(&gmaps[(size_t)dfv::GasT::NMAP * i], bases, G.off, G.n0, G.n1, G.pitch);
         }
         if (gas) {
             for (int i = 0; i < count; i++)

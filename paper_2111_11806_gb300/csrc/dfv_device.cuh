@@ -118,6 +118,19 @@ __host__ inline void apply_options(GridP &g, int use_thinc, double thinc_beta, i
     g.phi_guard = 1e-14;
 }
 
+// The checks of one material's parameters (kind 0 ideal, 1 stiffened, 2
+// Romenskii), shared by every entry point that takes materials: nullptr when
+// valid, else what is wrong.  Gases need gamma > 1 (Gamma = gamma - 1 > 0);
+// the Romenskii solid needs rho0 > 0, Gamma0 > 0 and alpha != 0 (Sec. 2.1.3,
+// eq:Romenskii divides by both).
+__host__ inline const char *material_problem(int kind, double gamma, double rho0, double Gamma0, double alpha)
+{
+    if (kind < 0 || kind > 2) return "bad material kind";
+    if (kind != 2 && !(gamma > 1.0)) return "gamma <= 1";
+    if (kind == 2 && !(rho0 > 0.0 && Gamma0 > 0.0 && alpha != 0.0)) return "bad Romenskii parameters";
+    return nullptr;
+}
+
 // Derive the per-precision constants from the double parameters; call after
 // every change of the grid or of a material.
 __host__ inline void finish_params(GridP &g)
@@ -406,6 +419,44 @@ __device__ __forceinline__ void stretch_log(const double A[3][3], double H[3][3]
     H[0][2] = H[2][0] = H[1][2] = H[2][1] = 0.0;
 }
 
+// The same in the compute precision T, for the closures (J^2 and dev H at
+// every face side and cell): the FP32 form keeps FP64 for the plastic
+// update's decomposition (plastic_return) only.  For T = double the
+// arithmetic is that of stretch_log.
+template <class T, int DIM>
+__device__ __forceinline__ void stretch_log_ct(const T A[3][3], T H[3][3], T &J2)
+{
+    T h0, h1, h2, c2, s2;
+    if (DIM == 1) {
+        h0 = T(0.5) * m_log(A[0][0] * A[0][0]);
+        h1 = T(0.5) * m_log(A[1][1] * A[1][1]);
+        h2 = T(0.5) * m_log(A[2][2] * A[2][2]);
+        c2 = T(1);
+        s2 = T(0);
+    } else {
+        const T b00 = A[0][0] * A[0][0] + A[0][1] * A[0][1];
+        const T b01 = A[0][0] * A[1][0] + A[0][1] * A[1][1];
+        const T b11 = A[1][0] * A[1][0] + A[1][1] * A[1][1];
+        const T b22 = A[2][2] * A[2][2];
+        const T mid = T(0.5) * (b00 + b11), half = T(0.5) * (b00 - b11);
+        const T rad = m_sqrt(half * half + b01 * b01);
+        h0 = T(0.5) * m_log(mid + rad);
+        h1 = T(0.5) * m_log(mid - rad);
+        h2 = T(0.5) * m_log(b22);
+        c2 = rad > T(0) ? half / rad : T(1);
+        s2 = rad > T(0) ? b01 / rad : T(0);
+    }
+    const T hm = (h0 + h1 + h2) * (T(1) / T(3));
+    const T d0 = h0 - hm, d1 = h1 - hm, d2 = h2 - hm;
+    J2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const T av = T(0.5) * (d0 + d1), df = T(0.5) * (d0 - d1);
+    H[0][0] = av + df * c2;
+    H[1][1] = av - df * c2;
+    H[0][1] = H[1][0] = df * s2;
+    H[2][2] = d2;
+    H[0][2] = H[2][0] = H[1][2] = H[2][1] = T(0);
+}
+
 // ------------------------------------------------------------- thermo
 
 // Closure weight of a transported volume fraction: clipped to [0, 1].
@@ -435,6 +486,18 @@ struct State {
     T H[DIM][DIM];     // dev(H), in-plane block
     T eps[NMAT];       // equivalent plastic strain (SOLID == 2)
 };
+
+template <class T, int DIM, int NMAT, int SOLID>
+__device__ __forceinline__ void unpack_A_ct(const T *w, T A[3][3])
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) A[a][b] = T(0);
+#pragma unroll
+    for (int c = 0; c < L::NV; c++) A[v_row(DIM, c)][v_col(DIM, c)] = w[L::IV + c];
+}
 
 template <class T, int DIM, int NMAT, int SOLID>
 __device__ __forceinline__ void unpack_A(const T *w, double A[3][3])
@@ -483,15 +546,13 @@ __device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, S
     }
     T J2 = T(0);
     if (SOLID) {
-        double A[3][3], H[3][3], j2;
-        Eig2 e;
-        unpack_A<T, DIM, NMAT, SOLID>(w, A);
-        stretch_log<DIM>(A, H, j2, e);
-        J2 = (T)j2;
+        T A[3][3], H[3][3];
+        unpack_A_ct<T, DIM, NMAT, SOLID>(w, A);
+        stretch_log_ct<T, DIM>(A, H, J2);
 #pragma unroll
         for (int a = 0; a < DIM; a++)
 #pragma unroll
-            for (int b = 0; b < DIM; b++) s.H[a][b] = (T)H[a][b];
+            for (int b = 0; b < DIM; b++) s.H[a][b] = H[a][b];
     }
     if constexpr (NMAT == 1) {
         // single material: the mixture rules reduce to the material's own closure
@@ -533,18 +594,27 @@ __device__ __forceinline__ void state_from_prim_ct(const GridP &g, const T *w, S
     s.c2 = Yn / s.rho * iden;
 }
 
+// The FP32 form's precision rule: the closure of a mixed cell -- at least two
+// materials present (fraction >= 1e-6) -- in which another material's fraction
+// is below 1e-6 runs in FP64.  A material below 1e-6 is absent (it takes its
+// reference density, reading of Sec. 2.2), so with two materials such a cell
+// does not exist; the rule acts from three materials on.
 template <class T, int NMAT>
 __device__ __forceinline__ bool needs_fp64(const T *phi_first)
 {
-    if (NMAT < 2) return false;
+    if (NMAT < 3) return false;
     T fsum = T(0), mn = T(1);
+    int present = 0;
 #pragma unroll
     for (int l = 0; l < NMAT - 1; l++) {
         mn = m_min(mn, phi_first[l]);
         fsum += phi_first[l];
+        present += phi_first[l] >= T(1e-6);
     }
-    mn = m_min(mn, T(1) - fsum);
-    return mn < T(1e-6);
+    const T last = T(1) - fsum;
+    mn = m_min(mn, last);
+    present += last >= T(1e-6);
+    return present >= 2 && mn < T(1e-6);
 }
 
 // State from primitives in the compute type T; the FP32 form switches to FP64
@@ -610,11 +680,9 @@ __device__ __forceinline__ void cons_to_prim_ct(const GridP &g, const T *q, T *w
     for (int a = 0; a < DIM; a++) u[a] = q[L::IMOM + a] * irho;
     T J2 = T(0);
     if (SOLID) {
-        double A[3][3], H[3][3], j2;
-        Eig2 e;
-        unpack_A<T, DIM, NMAT, SOLID>(q, A);
-        stretch_log<DIM>(A, H, j2, e);
-        J2 = (T)j2;
+        T A[3][3], H[3][3];
+        unpack_A_ct<T, DIM, NMAT, SOLID>(q, A);
+        stretch_log_ct<T, DIM>(A, H, J2);
     }
     T ke = T(0);
 #pragma unroll

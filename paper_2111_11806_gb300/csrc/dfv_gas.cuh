@@ -44,7 +44,8 @@ struct GasInst {
 
 struct GasArgs {
     const GasInst *inst;
-    const CUtensorMap *tmap;   // 3 per instance: the planes of U^n, U1, U3
+    const CUtensorMap *tmap;   // 4 per instance: the planes of U^n, U1, U3 (tile and halo),
+                               // and of U^n again (the tile's own cells)
     const int2 *items;         // (instance, tile); nullptr: instance 0, tile = item
     long long nitems;
     unsigned int *queue;       // dynamic schedule counter (nullptr: static round-robin)
@@ -66,10 +67,13 @@ struct GasT {
     static constexpr int FXS = TX + 1;         // x-face arrays: columns -1 .. TX-1 (values) / 0 .. TX (fluxes)
     static constexpr int FYS = TY + 1;
     static constexpr unsigned BOX_BYTES = 4u * NP * BOX;
+    static constexpr unsigned OWN_BYTES = 4u * NP * CELLS;   // U^n of the tile's own cells (stages 2, 3)
+    static constexpr int NMAP = 4;                           // tensor maps per instance
 };
 
 struct GasSmem {
     float tile[2][GasT::NP][GasT::BOX];            // TMA destination, double-buffered
+    float own[2][GasT::NP][GasT::CELLS];           // U^n of the tile's cells (stages 2, 3; TMA)
     float prim[4][GasT::PY][GasT::PX];             // rho, u, v, p of the tile and halo
     float fvx[4][GasT::TY][GasT::FXS];             // right-face values q_{i+1/2}^L, column i = -1 .. TX-1
     float fvy[4][GasT::FYS][GasT::TX];             // top-face values, row j = -1 .. TY-1
@@ -80,7 +84,8 @@ struct GasSmem {
     double red[32];
     unsigned long long mbar[2];
     long long item[2];
-    int flag;
+    GasInst inst[2];                               // the instance record of each buffered item
+    int2 w[2];                                     // (instance, tile) of each buffered item
 };
 
 // ------------------------------------------------------------ TMA, mbarrier
@@ -245,6 +250,26 @@ __device__ __forceinline__ long long gas_next(const GasArgs &a, long long cur, i
     return (long long)atomicAdd(a.queue, 1u);
 }
 
+// Thread 0: record item `it` in buffer `slot` (its work item and instance
+// record) and start the tensor copies of its planes into that buffer.
+template <int STAGE>
+__device__ __forceinline__ void gas_issue(const GasArgs &a, GasSmem &S, int slot, long long it)
+{
+    using T = GasT;
+    S.item[slot] = it;
+    if (it >= a.nitems) return;
+    const int2 w = a.items ? a.items[it] : make_int2(0, (int)it);
+    S.w[slot] = w;
+    S.inst[slot] = a.inst[w.x];
+    const GasInst &I = S.inst[slot];
+    const int ox = (w.y % I.tiles_x) * T::TX, oy = (w.y / I.tiles_x) * T::TY;
+    const CUtensorMap *m = a.tmap + T::NMAP * w.x;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&S.mbar[slot], T::BOX_BYTES + (STAGE > 1 ? T::OWN_BYTES : 0u));
+    tma_load_3d(&S.tile[slot][0][0], m + (STAGE - 1), ox - 4, oy - T::H, 0, &S.mbar[slot]);
+    if (STAGE > 1) tma_load_3d(&S.own[slot][0][0], m + 3, ox, oy, 0, &S.mbar[slot]);
+}
+
 // ------------------------------------------------------------ the stage
 
 template <int STAGE>
@@ -261,57 +286,29 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     pdl_enter();   // the previous kernel (its writes of the stage input) is complete
-    if (tid == 0) {
-        const long long first = a.queue ? (long long)atomicAdd(a.queue, 1u) : (long long)blockIdx.x;
-        S.item[0] = first;
-        S.flag = 0;
-        if (first < a.nitems) {
-            const int2 w = a.items ? a.items[first] : make_int2(0, (int)first);
-            const GasInst &I = a.inst[w.x];
-            mbar_expect_tx(&S.mbar[0], T::BOX_BYTES);
-            tma_load_3d(&S.tile[0][0][0], a.tmap + 3 * w.x + (STAGE - 1), (w.y % I.tiles_x) * T::TX - 4,
-                        (w.y / I.tiles_x) * T::TY - T::H, 0, &S.mbar[0]);
-        }
-    }
+    if (tid == 0) gas_issue<STAGE>(a, S, 0, a.queue ? (long long)atomicAdd(a.queue, 1u) : (long long)blockIdx.x);
     __syncthreads();
 
     const float ca = STAGE == 2 ? 0.75f : (STAGE == 3 ? 1.f / 3.f : 0.f);
     const float cb = STAGE == 2 ? 0.25f : (STAGE == 3 ? 2.f / 3.f : 1.f);
     const int ci = tid & 31, cj = tid >> 5;   // the thread's cell (tid < CELLS)
 
+    // No barrier ends an item: the next item's copies are started after its
+    // first barrier, which every thread passes only when done with this one.
     for (int k = 0;; k++) {
-        const long long it = S.item[k & 1];
+        const int slot = k & 1;
+        const long long it = S.item[slot];
         if (it >= a.nitems) break;
-        const int buf = k & 1;
-        const int2 w = a.items ? a.items[it] : make_int2(0, (int)it);
-        const GasInst &I = a.inst[w.x];
-        const int tile = w.y;
+        const GasInst &I = S.inst[slot];
+        const int tile = S.w[slot].y;
         const int ox = (tile % I.tiles_x) * T::TX, oy = (tile / I.tiles_x) * T::TY;
-        // the next item's planes into the other buffer (its last reader, the
-        // previous item, is behind the barrier that ended it)
-        if (tid == 0) {
-            const long long nx = gas_next(a, it, k);
-            S.item[(k + 1) & 1] = nx;
-            if (nx < a.nitems) {
-                const int2 wn = a.items ? a.items[nx] : make_int2(0, (int)nx);
-                const GasInst &In = a.inst[wn.x];
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&S.mbar[buf ^ 1], T::BOX_BYTES);
-                tma_load_3d(&S.tile[buf ^ 1][0][0], a.tmap + 3 * wn.x + (STAGE - 1), (wn.y % In.tiles_x) * T::TX - 4,
-                            (wn.y / In.tiles_x) * T::TY - T::H, 0, &S.mbar[buf ^ 1]);
-            }
-        }
-        const bool ok = mbar_wait(&S.mbar[buf], (unsigned)((k >> 1) & 1));
+        const bool ok = mbar_wait(&S.mbar[slot], (unsigned)((k >> 1) & 1));
         if (__syncthreads_or(!ok)) {
-            // a copy that never completed: report it, let the prefetch in
-            // flight land (bounded) and stop
-            if (tid == 0) {
-                atomicOr(&I.ctl->err, (unsigned)ERR_TIMEOUT);
-                if (S.item[(k + 1) & 1] < a.nitems) (void)mbar_wait(&S.mbar[buf ^ 1], (unsigned)(((k + 1) >> 1) & 1));
-            }
+            // a copy that never completed: report it and stop (no other copy is in flight)
+            if (tid == 0) atomicOr(&I.ctl->err, (unsigned)ERR_TIMEOUT);
             break;
         }
-        const float *tl = &S.tile[buf][0][0];
+        const float *tl = &S.tile[slot][0][0];
         const bool interior = ox >= 2 && ox + T::TX + 2 <= I.n0 && oy >= 2 && oy + T::TY + 2 <= I.n1;
 
         // 1. primitives of the tile and its halo (corners not needed)
@@ -336,6 +333,8 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
             for (int v = 0; v < 4; v++) S.prim[v][ly + T::H][lx + T::H] = wv[v];
         }
         __syncthreads();
+        // every thread is done with the previous item: its buffer takes the next one
+        if (tid == 0) gas_issue<STAGE>(a, S, slot ^ 1, gas_next(a, it, k));
 
         // 2. slopes once per cell; right/top face values to shared memory
         float qRx[4], qRy[4];
@@ -351,25 +350,24 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
                 qRy[v] = q - 0.5f * sy;
             }
         } else {
-            // the extra warp: right-face values of column -1 and top-face
-            // values of row -1, left-face values of column TX and bottom-face
-            // values of row TY
+            // the extra warp: lanes 0-15 the right-face values of column -1,
+            // lanes 16-31 the left-face values of column TX (row l % 16); every
+            // lane the top-face value of row -1 and the bottom-face value of
+            // row TY of column l
             const int l = tid - T::CELLS, jh = l & 15;
+            const bool west = l < 16;
+            const int col = west ? T::H - 1 : T::TX + T::H;
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 const float (*P)[T::PX] = S.prim[v];
-                const float qa = P[jh + T::H][T::H - 1];
-                const float sa = gas_vanleer(qa - P[jh + T::H][T::H - 2], P[jh + T::H][T::H] - qa);
+                const float qa = P[jh + T::H][col];
+                const float sa = gas_vanleer(qa - P[jh + T::H][col - 1], P[jh + T::H][col + 1] - qa);
                 const float qb = P[T::H - 1][l + T::H];
                 const float sb = gas_vanleer(qb - P[T::H - 2][l + T::H], P[T::H][l + T::H] - qb);
-                const float qc = P[jh + T::H][T::TX + T::H];
-                const float sc = gas_vanleer(qc - P[jh + T::H][T::TX + T::H - 1], P[jh + T::H][T::TX + T::H + 1] - qc);
                 const float qd = P[T::TY + T::H][l + T::H];
                 const float sd = gas_vanleer(qd - P[T::TY + T::H - 1][l + T::H], P[T::TY + T::H + 1][l + T::H] - qd);
-                if (l < 16) {
-                    S.fvx[v][jh][0] = qa + 0.5f * sa;
-                    S.hrx[v][jh] = qc - 0.5f * sc;
-                }
+                if (west) S.fvx[v][jh][0] = qa + 0.5f * sa;
+                else S.hrx[v][jh] = qa - 0.5f * sa;
                 S.fvy[v][0][l] = qb + 0.5f * sb;
                 S.hry[v][l] = qd - 0.5f * sd;
             }
@@ -424,12 +422,15 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
             const long long c = I.off + gx + (long long)I.n0 * gy;
             const long long P = I.pitch;
             const int bc = (cj + T::H) * T::BX + (ci + 4);
+            // U^n at the cell: the stage input itself in stage 1, its own copy after
+            const float *own = STAGE == 1 ? tl + bc : &S.own[slot][0][tid];
+            const int ostr = STAGE == 1 ? T::BOX : T::CELLS;
             float o[5];
-            const float unr = a.un[c + 4 * P];
+            const float unr = own[4 * ostr];
             const bool masked = unr > 0.5f;
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                const float unv = a.un[c + v * P];
+                const float unv = own[v * ostr];
                 const float div = (S.fx[v][cj][ci + 1] - Fxl[v]) * I.idx;
                 const float dvy = (S.fy[v][cj + 1][ci] - Fyl[v]) * I.idy;
                 Acc<float> D;
@@ -482,7 +483,6 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
                 atomicMax(&ctl->smax_acc, (unsigned long long)__double_as_longlong(md));
             }
         }
-        __syncthreads();   // the item's buffers are free; S.item of the next item is visible
     }
 }
 
@@ -494,10 +494,11 @@ namespace dfv {
 cudaError_t gas_prepare();                  // opt the kernels in to their shared memory
 int gas_max_ctas_per_sm();                  // resident CTAs per SM of the stage kernels
 cudaError_t gas_stage(int stage, const GasArgs &a, int grid, cudaStream_t st);
-// The three tensor maps (the planes of U^n, U1, U3) of one instance whose
-// planes start `off` elements into each buffer: 3-D (x, y, plane) over n0 x n1
-// x 5 floats with row stride n0 and plane stride pitch, box 40 x 20 x 5.
-bool gas_encode_maps(CUtensorMap maps[3], const void *const bases[3], long long off, int n0, int n1,
+// The four tensor maps of one instance whose planes start `off` elements
+// into each buffer: 3-D (x, y, plane) over n0 x n1 x 5 floats with row stride
+// n0 and plane stride pitch; maps 0-2 over U^n, U1, U3 with the box of a tile
+// and its halo (40 x 20 x 5), map 3 over U^n with the box of a tile (32 x 16 x 5).
+bool gas_encode_maps(CUtensorMap maps[GasT::NMAP], const void *const bases[3], long long off, int n0, int n1,
                      long long pitch);
 
 // Whether a 2-D grid can take the gas stage kernel: FP32, one ideal or

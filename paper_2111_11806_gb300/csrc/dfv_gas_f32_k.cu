@@ -57,21 +57,23 @@ cudaError_t gas_stage(int stage, const GasArgs &a, int grid, cudaStream_t st)
     return launch_pdl(k_gas_stage<3>, g, b, sm, st, a);
 }
 
-bool gas_encode_maps(CUtensorMap maps[3], const void *const bases[3], long long off, int n0, int n1,
+bool gas_encode_maps(CUtensorMap maps[GasT::NMAP], const void *const bases[3], long long off, int n0, int n1,
                      long long pitch)
 {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn || n0 % 4 != 0 || pitch % 4 != 0) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)n0, (cuuint64_t)n1, (cuuint64_t)GasT::NP};
     const cuuint64_t strides[2] = {(cuuint64_t)n0 * 4u, (cuuint64_t)pitch * 4u};
-    const cuuint32_t box[3] = {(cuuint32_t)GasT::BX, (cuuint32_t)GasT::BY, (cuuint32_t)GasT::NP};
+    const cuuint32_t halo_box[3] = {(cuuint32_t)GasT::BX, (cuuint32_t)GasT::BY, (cuuint32_t)GasT::NP};
+    const cuuint32_t own_box[3] = {(cuuint32_t)GasT::TX, (cuuint32_t)GasT::TY, (cuuint32_t)GasT::NP};
     const cuuint32_t estr[3] = {1, 1, 1};
-    for (int k = 0; k < 3; k++) {
-        void *base = (char *)const_cast<void *>(bases[k]) + 4 * off;
+    for (int k = 0; k < GasT::NMAP; k++) {
+        void *base = (char *)const_cast<void *>(bases[k < 3 ? k : 0]) + 4 * off;
         if (((uintptr_t)base & 15u) != 0) return false;
-        const CUresult r = fn(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const CUresult r = fn(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides,
+                              k < 3 ? halo_box : own_box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return false;
     }
     return true;

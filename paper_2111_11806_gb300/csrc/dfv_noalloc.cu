@@ -100,7 +100,8 @@ extern "C" dfv_status dfv_compute_dt_noalloc(int dim, const int n[3], const doub
     dfv::apply_options(p, opt->use_thinc, opt->thinc_beta, opt->hllc_lm, opt->seed_variant,
                        opt->normal_method, opt->probe_mode);
     for (int l = 0; l < opt->nmat; l++) {
-        if (kinds[l] < DFV_MAT_IDEAL || kinds[l] > DFV_MAT_ROMENSKII) return DFV_ERR_ARG;
+        if (dfv::material_problem(kinds[l], params[l].gamma, params[l].rho0, params[l].Gamma0, params[l].alpha))
+            return DFV_ERR_ARG;
         dfv::MatP &m = p.mat[l];
         m.kind = kinds[l];
         m.gamma = params[l].gamma;

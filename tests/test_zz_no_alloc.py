@@ -49,3 +49,16 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     n = (257, 256, 256)   # 16.8 M cells > DFV_NOALLOC_MAX_CELLS
     with pytest.raises(B.DfvError, match="TOO_LARGE"):
         B.compute_dt_noalloc(3, n, (0, 0, 0), (1, 1, 1), [W.AIR], dummy.data_ptr(), int(np.prod(n)), 0.8)
+
+
+def test_noalloc_rejects_bad_material_parameters():
+    """The same parameter checks as dfv_add_material: gamma <= 1 for a gas,
+    rho0 <= 0 for a Romenskii solid."""
+    import torch
+    dummy = torch.zeros(4 * 8 * 8, dtype=torch.float64, device="cuda")
+    bad_gas = dict(W.AIR, gamma=1.0)
+    with pytest.raises(B.DfvError, match="DFV_ERR_ARG"):
+        B.compute_dt_noalloc(2, (8, 8), (0, 0), (1, 1), [bad_gas], dummy.data_ptr(), 64, 0.8)
+    bad_solid = dict(W.ALUMINIUM, rho0=0.0)
+    with pytest.raises(B.DfvError, match="DFV_ERR_ARG"):
+        B.compute_dt_noalloc(2, (8, 8), (0, 0), (1, 1), [bad_solid], dummy.data_ptr(), 64, 0.8, solid=True)
