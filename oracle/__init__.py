@@ -63,13 +63,14 @@ def lib():
             L.o_step.argtypes = [ctypes.c_void_p, ctypes.c_double]
             L.o_seed_state.argtypes = [ctypes.c_void_p]
             L.o_force_state.argtypes = [ctypes.c_void_p, _dp]
-            L.o_plastic_state.argtypes = [ctypes.c_void_p]
+            L.o_plastic_state.argtypes = [ctypes.c_void_p, ctypes.c_double]
             L.o_cell_closure.argtypes = [ctypes.c_void_p, _dp, _dp]
             L.o_cell_prim_to_cons.argtypes = [ctypes.c_void_p, _dp, _dp]
             L.o_cell_cons_to_prim.argtypes = [ctypes.c_void_p, _dp, _dp]
             L.o_material_ref.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
             L.o_riemann.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
-            L.o_plastic_cons.argtypes = [ctypes.c_void_p, _dp]
+            L.o_plastic_cons.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double]
+            L.o_set_jc.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_double] * 7
             L.o_thinc.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]
             L.o_thinc.restype = ctypes.c_int
             L.o_sym_eig3.argtypes = [_dp, _dp, _dp]
@@ -136,6 +137,8 @@ class Oracle:
         lib().o_set_material(self._h, l, kind, m.get("gamma", 0.0), m.get("pinf", 0.0), m.get("rho0", 0.0),
                              m.get("K0", 0.0), m.get("G0", 0.0), m.get("alpha", 0.0), m.get("beta", 0.0),
                              m.get("Gamma0", 0.0), m.get("sigY", 0.0))
+        lib().o_set_jc(self._h, l, *[float(m.get(k, 0.0)) for k in
+                                     ("jc_c1", "jc_c2", "jc_c3", "jc_n", "jc_m", "jc_tmelt", "jc_cv")])
 
     def set_options(self, use_thinc=True, thinc_beta=1.6):
         lib().o_set_options(self._h, int(bool(use_thinc)), float(thinc_beta))
@@ -213,8 +216,10 @@ class Oracle:
         lib().o_force_state(self._h, _p(f))
         return f
 
-    def plastic(self):
-        lib().o_plastic_state(self._h)
+    def plastic(self, dt=0.0):
+        """The plastic update of every cell (dt: the step, for the strain rate
+        of Johnson-Cook materials; 0 = no rate term)."""
+        lib().o_plastic_state(self._h, float(dt))
 
     # ---- single-cell / single-face pieces, for pins
     def closure(self, q):
@@ -243,9 +248,9 @@ class Oracle:
         lib().o_riemann(self._h, d, _p(_arr(wL)), _p(_arr(wR)), _p(F), _p(us), _p(vr))
         return F, us, vr
 
-    def plastic_cons(self, q):
+    def plastic_cons(self, q, dt=0.0):
         a = _arr(q).copy()
-        lib().o_plastic_cons(self._h, _p(a))
+        lib().o_plastic_cons(self._h, _p(a), float(dt))
         return a
 
 

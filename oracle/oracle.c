@@ -45,6 +45,9 @@ typedef struct {
     double gamma, pinf;                         /* ideal / stiffened gas */
     double rho0, K0, G0, alpha, beta, Gamma0;   /* Romenskii solid */
     double sigY;                                /* yield stress (0 for fluids) */
+    int jc;                                     /* 1: Johnson-Cook flow stress instead of sigY */
+    double jc_c1, jc_c2, jc_c3, jc_n, jc_m;     /* Table 2 constants */
+    double jc_tmelt, jc_cv;                     /* melting temperature, specific heat */
 } omat;
 
 typedef struct {
@@ -1187,6 +1190,49 @@ void o_force(ostate *s, double F[3])
 
 /* ------------------------------------------------------ plastic update */
 
+/* Johnson-Cook flow stress of one material [readings: Table 2 gives the
+ * constants c1, c2, c3, n, m, T_melt and C_V of copper but not the law; the
+ * usual Johnson-Cook form is taken with the reference temperature JC_T0 and
+ * the reference plastic strain rate JC_RATE0]:
+ *   sigma_Y = (c1 + c2 eps^n) (1 + c3 ln max(rate/JC_RATE0, 1)) (1 - T*^m),
+ *   T* = (T - JC_T0)/(T_melt - JC_T0) clipped to [0, 1]. */
+#define JC_T0 298.0
+#define JC_RATE0 1.0
+
+static double jc_yield(const omat *m, double eps, double rate, double T)
+{
+    double ts = (T - JC_T0) / (m->jc_tmelt - JC_T0);
+    ts = ts < 0.0 ? 0.0 : (ts > 1.0 ? 1.0 : ts);
+    double r = rate / JC_RATE0;
+    double e = eps > 0.0 ? eps : 0.0;
+    return (m->jc_c1 + m->jc_c2 * pow(e, m->jc_n)) * (1.0 + m->jc_c3 * log(r > 1.0 ? r : 1.0)) *
+           (1.0 - pow(ts, m->jc_m));
+}
+
+/* Temperature of material l [reading: the thermal part of its
+ * Mie-Grueneisen energy over the specific heat, T = JC_T0 + (e - e_ref)/C_V
+ * with e - e_ref = (p - p_ref)/(rho_l Gamma_l) at the cell's pressure]. */
+static double jc_temperature(const omat *m, double p, double rhol, const double ref[6])
+{
+    return JC_T0 + (p - ref[2]) / (rhol * ref[0] * m->jc_cv);
+}
+
+/* Mixture yield stress of a cell for the return (Sec. 2.2 weights phi_l/Gamma_l),
+ * with Johnson-Cook materials at the cell's plastic-strain rate `rate`. */
+static double yield_mixture(const ostate *s, const othermo *t, double rate)
+{
+    double num = 0.0, den = 0.0;
+    for (int l = 0; l < s->nmat; l++) {
+        double ref[6];
+        o_mat_ref(&s->mat[l], t->rhol[l], t->J2, ref);
+        double sy = s->mat[l].sigY;
+        if (s->mat[l].jc) sy = jc_yield(&s->mat[l], t->eps[l], rate, jc_temperature(&s->mat[l], t->p, t->rhol[l], ref));
+        num += t->phi[l] * sy / ref[0];
+        den += t->phi[l] / ref[0];
+    }
+    return num / den;
+}
+
 /* Perfect plasticity by instantaneous radial return [reading; Sec. 2.1.1
  * defers the convex-potential closure to Barton 2019]: the stretch is
  * re-symmetrised by the left polar decomposition A = V R (A A^T = Q diag(lam) Q^T),
@@ -1194,8 +1240,12 @@ void o_force(ostate *s, double F[3])
  * s = min(1, sigma_Y/sigma_vm), sigma_vm = sqrt(3/2) 2 G |d|, with the mixture
  * G and sigma_Y weighted like the shear-modulus rule (Sec. 2.2), and
  * V <- Q diag(exp(s d_k)) Q^T (unimodular).  rho E, phi and phi rho are kept,
- * so the released shear energy becomes heat. */
-static void plastic_cell(const ostate *s, double *q)
+ * so the released shear energy becomes heat.  With Johnson-Cook materials the
+ * yield stress depends on the plastic strain, the temperature and the
+ * plastic-strain rate [reading: one explicit predictor; the rate is the
+ * equivalent plastic strain a return at the rate-free yield stress would
+ * remove, over the step dt (0 when dt = 0)]. */
+static void plastic_cell(const ostate *s, double *q, double dt)
 {
     double w[OMAXV];
     cons_to_prim(s, q, w);
@@ -1218,7 +1268,15 @@ static void plastic_cell(const ostate *s, double *q)
     }
     nd = sqrt(nd);
     double svm = sqrt(1.5) * 2.0 * t.G * nd;
-    double sc = (svm > t.sigY) ? t.sigY / svm : 1.0;
+    double sigY = t.sigY;
+    int any_jc = 0;
+    for (int l = 0; l < s->nmat; l++) any_jc |= s->mat[l].jc;
+    if (any_jc) {
+        double sy0 = yield_mixture(s, &t, 0.0);
+        double rate = (svm > sy0 && dt > 0.0) ? sqrt(2.0 / 3.0) * (1.0 - sy0 / svm) * nd / dt : 0.0;
+        sigY = yield_mixture(s, &t, rate);
+    }
+    double sc = (svm > sigY) ? sigY / svm : 1.0;
     /* equivalent plastic strain [reading: Sec. 2.1.1 names the history
      * variable without its evolution law]: the deviatoric log-strain removed
      * by the return, (1 - s) |d|, as the von Mises equivalent
@@ -1226,7 +1284,7 @@ static void plastic_cell(const ostate *s, double *q)
     if (s->hist && sc < 1.0) {
         double deps = sqrt(2.0 / 3.0) * (1.0 - sc) * nd;
         for (int l = 0; l < s->nmat; l++)
-            if (s->mat[l].sigY > 0.0) q[s->ih + l] += q[s->iar + l] * deps;
+            if (s->mat[l].sigY > 0.0 || s->mat[l].jc) q[s->ih + l] += q[s->iar + l] * deps;
     }
     double Vn[3][3];
     for (int i = 0; i < 3; i++)
@@ -1238,7 +1296,7 @@ static void plastic_cell(const ostate *s, double *q)
     vbar_pack(s, Vn, q);
 }
 
-void o_plastic(ostate *s)
+void o_plastic(ostate *s, double dt)
 {
     if (!s->solid) return;
     long nc = s->ncell;
@@ -1246,7 +1304,7 @@ void o_plastic(ostate *s)
         if (s->mask && s->mask[c]) continue;
         double q[OMAXV];
         for (int v = 0; v < s->nvar; v++) q[v] = s->U[v * nc + c];
-        plastic_cell(s, q);
+        plastic_cell(s, q, dt);
         for (int v = 0; v < s->nvar; v++) s->U[v * nc + c] = q[v];
     }
 }
@@ -1315,7 +1373,7 @@ void o_step(ostate *s, double dt)
                 out[st][a] = (st == 0) ? y : ca[st] * s->Un[a] + cb[st] * y;
             }
     }
-    o_plastic(s);
+    o_plastic(s, dt);
     if (s->dynamic && s->mass > 0.0) {
         for (int d = 0; d < 3; d++) {
             s->vr[d] += dt * s->force[d] / s->mass;
@@ -1500,11 +1558,11 @@ void o_compute_D(void *h, double *D)
 
 void o_seed_state(void *h) { o_seed((ostate *)h); }
 void o_force_state(void *h, double F[3]) { o_force((ostate *)h, F); }
-void o_plastic_state(void *h)
+void o_plastic_state(void *h, double dt)
 {
     ostate *s = (ostate *)h;
     memset(s->mask, 0, (size_t)s->ncell);
-    o_plastic(s);
+    o_plastic(s, dt);
 }
 
 /* Closure of one conserved cell vector: p, c, G, sigma_Y and J^2. */
@@ -1540,4 +1598,18 @@ void o_riemann(void *h, int d, const double *wL, const double *wR, double *F, do
     o_hllc(s, d, wL, wR, F, us, vrow);
 }
 
-void o_plastic_cons(void *h, double *q) { plastic_cell((ostate *)h, q); }
+void o_plastic_cons(void *h, double *q, double dt) { plastic_cell((ostate *)h, q, dt); }
+
+/* Johnson-Cook constants of material l (Table 2); c1 = c2 = 0 switches it off. */
+void o_set_jc(void *h, int l, double c1, double c2, double c3, double n, double m, double tmelt, double cv)
+{
+    omat *mt = &((ostate *)h)->mat[l];
+    mt->jc = (c1 > 0.0 || c2 > 0.0) ? 1 : 0;
+    mt->jc_c1 = c1;
+    mt->jc_c2 = c2;
+    mt->jc_c3 = c3;
+    mt->jc_n = n;
+    mt->jc_m = m;
+    mt->jc_tmelt = tmelt;
+    mt->jc_cv = cv;
+}

@@ -37,6 +37,11 @@ HELIUM = dict(kind="ideal", gamma=1.67, rho0=0.166)
 ALUMINIUM = dict(kind="romenskii", rho0=2700.0, K0=76.0e9, G0=26.0e9, alpha=0.627,
                  beta=2.288, Gamma0=1.484, sigY=0.3e9)
 
+# Copper: the paper's Table 1 Romenskii constants and Table 2 Johnson-Cook
+# constants (c1, c2 in Pa, T_melt in K, C_V in J/(kg K)).
+COPPER = dict(kind="romenskii", rho0=8960.0, K0=130.1e9, G0=43.33e9, alpha=1.0, beta=3.0, Gamma0=2.0,
+              jc_c1=0.09e9, jc_c2=0.292e9, jc_c3=0.025, jc_n=0.31, jc_m=1.09, jc_tmelt=1358.0, jc_cv=385.0)
+
 PHI_PURE = 1.0e-8   # residual volume fraction of an absent material
 
 
