@@ -89,6 +89,18 @@ typedef struct {
     double beta;     /* Romenskii: shear-modulus exponent */
     double Gamma0;   /* Romenskii: Grueneisen coefficient */
     double sigma_y;  /* yield stress for perfect plasticity (0: fluid) */
+    /* Johnson-Cook flow stress (the paper's Table 2 gives these for copper),
+     * used instead of sigma_y when jc_c1 > 0 or jc_c2 > 0:
+     *   sigma_Y = (c1 + c2 eps_p^n)(1 + c3 ln max(rate/1 s^-1, 1))(1 - T*^m),
+     *   T* = clip((T - 298 K)/(T_melt - 298 K), 0, 1),
+     * eps_p the material's equivalent plastic strain (its history plane with
+     * dfv_options.solid = 2, else 0), T = 298 K + (p - p_ref)/(rho Gamma C_V)
+     * and rate the plastic strain a return at the rate-free yield stress would
+     * remove over the step, divided by dt.  Needs T_melt > 298 K, C_V > 0. */
+    double jc_c1, jc_c2;   /* Pa */
+    double jc_c3, jc_n, jc_m;
+    double jc_tmelt;       /* K */
+    double jc_cv;          /* J/(kg K) */
 } dfv_material_params;
 
 typedef struct {

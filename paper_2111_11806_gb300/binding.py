@@ -34,7 +34,8 @@ EXPORTS = ("dfv_workspace_bytes", "dfv_create_grid", "dfv_add_material", "dfv_se
 
 class dfv_material_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
-                ("gamma", "pinf", "rho0", "K0", "G0", "alpha", "beta", "Gamma0", "sigma_y")]
+                ("gamma", "pinf", "rho0", "K0", "G0", "alpha", "beta", "Gamma0", "sigma_y",
+                 "jc_c1", "jc_c2", "jc_c3", "jc_n", "jc_m", "jc_tmelt", "jc_cv")]
 
 
 class dfv_options(ctypes.Structure):
@@ -138,6 +139,8 @@ def material_struct(m: dict) -> dfv_material_params:
     p.beta = m.get("beta", 0.0)
     p.Gamma0 = m.get("Gamma0", 0.0)
     p.sigma_y = m.get("sigY", 0.0)
+    for k in ("jc_c1", "jc_c2", "jc_c3", "jc_n", "jc_m", "jc_tmelt", "jc_cv"):
+        setattr(p, k, m.get(k, 0.0))
     return p
 
 

@@ -480,19 +480,11 @@ dfv_status dfv_add_material(dfv_grid *g, int kind, const dfv_material_params *m,
     if (!g) return DFV_ERR_ARG;
     if (!m) return fail(g, DFV_ERR_ARG, "dfv_add_material: null parameters");
     if (g->nmat >= g->nmat_opt) return fail(g, DFV_ERR_ARG, "dfv_add_material: all materials already added");
-    if (const char *why = dfv::material_problem(kind, m->gamma, m->rho0, m->Gamma0, m->alpha))
+    if (const char *why = dfv::material_problem(kind, m->gamma, m->rho0, m->Gamma0, m->alpha, m->jc_c1, m->jc_c2,
+                                                m->jc_n, m->jc_tmelt, m->jc_cv))
         return fail(g, DFV_ERR_ARG, std::string("dfv_add_material: ") + why);
     dfv::MatP &p = g->g.mat[g->nmat];
-    p.kind = kind;
-    p.gamma = m->gamma;
-    p.pinf = m->pinf;
-    p.rho0 = m->rho0;
-    p.K0 = m->K0;
-    p.G0 = m->G0;
-    p.alpha = m->alpha;
-    p.beta = m->beta;
-    p.Gamma0 = m->Gamma0;
-    p.sigY = m->sigma_y;
+    dfv::set_material(p, kind, *m);
     dfv::finish_params(g->g);
     if (id_out) *id_out = g->nmat;
     g->nmat++;

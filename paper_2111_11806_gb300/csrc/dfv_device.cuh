@@ -23,6 +23,8 @@ struct MatP {
     double gamma, pinf;
     double rho0, K0, G0, alpha, beta, Gamma0;
     double sigY;
+    int jc;                   // 1: Johnson-Cook flow stress instead of sigY
+    double jc_c1, jc_c2, jc_c3, jc_n, jc_m, jc_tmelt, jc_cv;
 };
 
 // Material and grid constants in the compute precision, derived on the host
@@ -67,6 +69,7 @@ struct GridP {
     MatC<float> mc_f[3];
     GridC<double> gc_d;
     GridC<float> gc_f;
+    int any_jc;         // some material has a Johnson-Cook flow stress
 };
 
 template <class T>
@@ -123,12 +126,41 @@ __host__ inline void apply_options(GridP &g, int use_thinc, double thinc_beta, i
 // valid, else what is wrong.  Gases need gamma > 1 (Gamma = gamma - 1 > 0);
 // the Romenskii solid needs rho0 > 0, Gamma0 > 0 and alpha != 0 (Sec. 2.1.3,
 // eq:Romenskii divides by both).
-__host__ inline const char *material_problem(int kind, double gamma, double rho0, double Gamma0, double alpha)
+__host__ inline const char *material_problem(int kind, double gamma, double rho0, double Gamma0, double alpha,
+                                             double jc_c1 = 0.0, double jc_c2 = 0.0, double jc_n = 0.0,
+                                             double jc_tmelt = 0.0, double jc_cv = 0.0)
 {
     if (kind < 0 || kind > 2) return "bad material kind";
     if (kind != 2 && !(gamma > 1.0)) return "gamma <= 1";
     if (kind == 2 && !(rho0 > 0.0 && Gamma0 > 0.0 && alpha != 0.0)) return "bad Romenskii parameters";
+    if ((jc_c1 > 0.0 || jc_c2 > 0.0) && !(jc_tmelt > 298.0 && jc_cv > 0.0 && jc_n >= 0.0 && jc_c1 >= 0.0 &&
+                                         jc_c2 >= 0.0))
+        return "bad Johnson-Cook parameters";
     return nullptr;
+}
+
+// Copy the caller's material parameters (dfvrb.h) into a MatP.
+template <class P>
+__host__ inline void set_material(MatP &m, int kind, const P &p)
+{
+    m.kind = kind;
+    m.gamma = p.gamma;
+    m.pinf = p.pinf;
+    m.rho0 = p.rho0;
+    m.K0 = p.K0;
+    m.G0 = p.G0;
+    m.alpha = p.alpha;
+    m.beta = p.beta;
+    m.Gamma0 = p.Gamma0;
+    m.sigY = p.sigma_y;
+    m.jc = (p.jc_c1 > 0.0 || p.jc_c2 > 0.0) ? 1 : 0;
+    m.jc_c1 = p.jc_c1;
+    m.jc_c2 = p.jc_c2;
+    m.jc_c3 = p.jc_c3;
+    m.jc_n = p.jc_n;
+    m.jc_m = p.jc_m;
+    m.jc_tmelt = p.jc_tmelt;
+    m.jc_cv = p.jc_cv;
 }
 
 // Derive the per-precision constants from the double parameters; call after
@@ -137,6 +169,8 @@ __host__ inline void finish_params(GridP &g)
 {
     fill_consts<double>(g, g.mc_d, g.gc_d);
     fill_consts<float>(g, g.mc_f, g.gc_f);
+    g.any_jc = 0;
+    for (int l = 0; l < 3; l++) g.any_jc |= g.mat[l].jc;
 }
 
 template <class T>
@@ -1013,13 +1047,17 @@ __device__ __forceinline__ void riemann(const GridP &g, const T *wL, const T *wR
 // sigma_vm = sqrt(3/2) 2 G |d| (mixture G and sigma_Y).  Energy, masses and
 // momenta are untouched.  Returns the equivalent plastic strain increment
 // sqrt(2/3) (1 - s) |d| (0 below yield).
-template <int DIM>
-__device__ __forceinline__ double plastic_return(double A[3][3], double G, double sigY)
+// yield(svm, |d|, J2) gives the yield stress for the trial von Mises stress
+// svm and deviatoric log-stretch norm |d| (Johnson-Cook: plastic strain,
+// temperature and rate); the constant-sigma_Y form ignores its arguments.
+template <int DIM, class Y>
+__device__ __forceinline__ double plastic_return_y(double A[3][3], double G, Y yield)
 {
     double H[3][3], J2;
     Eig2 e;
     stretch_log<DIM>(A, H, J2, e);
     const double svm = sqrt(1.5) * 2.0 * G * sqrt(J2);
+    const double sigY = yield(svm, sqrt(J2), J2);
     const double sc = (svm > sigY) ? sigY / svm : 1.0;
     // equivalent plastic strain of the removed deviatoric log-strain (1 - s)|d|
     const double deps = sc < 1.0 ? sqrt(2.0 / 3.0) * (1.0 - sc) * sqrt(J2) : 0.0;
@@ -1036,6 +1074,59 @@ __device__ __forceinline__ double plastic_return(double A[3][3], double G, doubl
         A[0][1] = A[1][0] = 0.0;
     }
     return deps;
+}
+
+template <int DIM>
+__device__ __forceinline__ double plastic_return(double A[3][3], double G, double sigY)
+{
+    return plastic_return_y<DIM>(A, G, [sigY](double, double, double) { return sigY; });
+}
+
+// Johnson-Cook flow stress of material m (the law, the reference temperature
+// 298 K and rate 1/s are readings of Table 2, which lists the constants only):
+// (c1 + c2 eps^n)(1 + c3 ln max(rate, 1))(1 - T*^m), T* = (T - 298)/(T_melt - 298)
+// clipped to [0, 1].
+__device__ __forceinline__ double jc_yield(const MatP &m, double eps, double rate, double T)
+{
+    double ts = (T - 298.0) / (m.jc_tmelt - 298.0);
+    ts = ts < 0.0 ? 0.0 : (ts > 1.0 ? 1.0 : ts);
+    const double e = eps > 0.0 ? eps : 0.0;
+    return (m.jc_c1 + m.jc_c2 * pow(e, m.jc_n)) * (1.0 + m.jc_c3 * log(rate > 1.0 ? rate : 1.0)) *
+           (1.0 - pow(ts, m.jc_m));
+}
+
+// Mixture yield stress of a cell with Johnson-Cook materials (weights
+// phi_l/Gamma_l, Sec. 2.2), each at its plastic strain and at the temperature
+// of its Mie-Grueneisen thermal energy, 298 K + (p - p_ref)/(rho_l Gamma_l C_V);
+// w: the cell's primitives, J2: its |dev ln V|^2.
+template <class R, int DIM, int NMAT, int SOLID>
+__device__ __forceinline__ double jc_mixture_yield(const GridP &g, const R *w, double J2, double rate)
+{
+    using L = Lay<DIM, NMAT, SOLID>;
+    double fsum = 0.0, phi[NMAT];
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; l++) {
+        phi[l] = (double)w[L::IPHI + l];
+        fsum += phi[l];
+    }
+    phi[NMAT - 1] = 1.0 - fsum;
+    double num = 0.0, den = 0.0;
+    const double p = (double)w[L::IE];
+#pragma unroll
+    for (int l = 0; l < NMAT; l++) {
+        const double ph = phi_clip(phi[l]);
+        const double rl = (double)w[L::IAR + l];
+        const Ref<double> r = mat_ref<double>(g.mc_d[l], rl, J2);
+        double sy = g.mat[l].sigY;
+        if (g.mat[l].jc) {
+            double eps = 0.0;
+            if constexpr (SOLID == 2) eps = (double)w[L::IH + l];
+            sy = jc_yield(g.mat[l], eps, rate, 298.0 + (p - r.pref) / (rl * r.Gam * g.mat[l].jc_cv));
+        }
+        num += ph * sy / r.Gam;
+        den += ph / r.Gam;
+    }
+    return num / den;
 }
 
 }  // namespace dfv

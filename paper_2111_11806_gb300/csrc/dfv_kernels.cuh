@@ -1148,14 +1148,26 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
             state_from_prim<R, DIM, NMAT, SOLID>(g, w, s);
             double A[3][3];
             unpack_A<R, DIM, NMAT, SOLID>(o, A);
-            const double deps = plastic_return<DIM>(A, (double)s.G, (double)s.sigY);
+            double deps;
+            if (g.any_jc) {
+                // Johnson-Cook: the rate is that of a return at the rate-free
+                // yield stress over the step (one explicit predictor)
+                const double G = (double)s.G, dtd = a.ctl->dt;
+                deps = plastic_return_y<DIM>(A, G, [&](double svm, double nd, double J2) {
+                    const double sy0 = jc_mixture_yield<R, DIM, NMAT, SOLID>(g, w, J2, 0.0);
+                    const double rate = (svm > sy0 && dtd > 0.0) ? sqrt(2.0 / 3.0) * (1.0 - sy0 / svm) * nd / dtd : 0.0;
+                    return jc_mixture_yield<R, DIM, NMAT, SOLID>(g, w, J2, rate);
+                });
+            } else {
+                deps = plastic_return<DIM>(A, (double)s.G, (double)s.sigY);
+            }
 #pragma unroll
             for (int cc = 0; cc < L::NV; cc++) o[L::IV + cc] = (R)A[v_row(DIM, cc)][v_col(DIM, cc)];
             if constexpr (SOLID == 2) {
                 // the strain removed by the return, added to every material with a yield stress
 #pragma unroll
                 for (int l = 0; l < NMAT; l++)
-                    if (matc<R>(g, l).sigY > R(0) && deps > 0.0)
+                    if ((matc<R>(g, l).sigY > R(0) || g.mat[l].jc) && deps > 0.0)
                         o[L::IH + l] = (R)((double)o[L::IH + l] + (double)o[L::IAR + l] * deps);
             }
         }

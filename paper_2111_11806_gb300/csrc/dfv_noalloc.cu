@@ -100,19 +100,11 @@ extern "C" dfv_status dfv_compute_dt_noalloc(int dim, const int n[3], const doub
     dfv::apply_options(p, opt->use_thinc, opt->thinc_beta, opt->hllc_lm, opt->seed_variant,
                        opt->normal_method, opt->probe_mode);
     for (int l = 0; l < opt->nmat; l++) {
-        if (dfv::material_problem(kinds[l], params[l].gamma, params[l].rho0, params[l].Gamma0, params[l].alpha))
+        const dfv_material_params &q = params[l];
+        if (dfv::material_problem(kinds[l], q.gamma, q.rho0, q.Gamma0, q.alpha, q.jc_c1, q.jc_c2, q.jc_n, q.jc_tmelt,
+                                  q.jc_cv))
             return DFV_ERR_ARG;
-        dfv::MatP &m = p.mat[l];
-        m.kind = kinds[l];
-        m.gamma = params[l].gamma;
-        m.pinf = params[l].pinf;
-        m.rho0 = params[l].rho0;
-        m.K0 = params[l].K0;
-        m.G0 = params[l].G0;
-        m.alpha = params[l].alpha;
-        m.beta = params[l].beta;
-        m.Gamma0 = params[l].Gamma0;
-        m.sigY = params[l].sigma_y;
+        dfv::set_material(p.mat[l], kinds[l], q);
     }
     dfv::finish_params(p);
 

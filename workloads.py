@@ -242,26 +242,28 @@ def wedge_2d(nx: int = 1200, mach: float = 10.0, angle_deg: float = 30.0) -> Wor
                     False, w, cfl=0.4, steps=0, t_end=0.2 if mach >= 5 else 1.2, walls=(0, 0, 1, 0, 0, 0))
 
 
-def impact_2d(n: int = 1024, seed_index: int = 4) -> Workload:
+def impact_2d(n: int = 1024, seed_index: int = 4, solid_material: Optional[dict] = None) -> Workload:
     """Aluminium-like block [0.005,0.025]x[0.03,0.07] m moving at 400 m/s into
     a static rigid wedge (apex (0.06,0.05), half-angle 30 deg) on [0,0.1]^2,
     surrounded by air at rest; V starts at the identity; 1e-6 x 400 m/s
-    Gaussian noise on both velocity components."""
+    Gaussian noise on both velocity components.  solid_material replaces the
+    aluminium (e.g. COPPER, with its Johnson-Cook flow stress)."""
+    mat = ALUMINIUM if solid_material is None else solid_material
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_index))
     lo, hi = (0.0, 0.0), (0.1, 0.1)
     X, Y, _ = cell_centres((n, n), lo, hi)
     dx = 0.1 / n
     w, L = _empty_prim(2, 2, True, n * n)
     block = (X >= 0.005) & (X <= 0.025) & (Y >= 0.03) & (Y <= 0.07)
-    w[L["iphi"]] = np.where(block, 1.0 - PHI_PURE, PHI_PURE)     # phi of aluminium
-    w[L["irho"]] = ALUMINIUM["rho0"]
+    w[L["iphi"]] = np.where(block, 1.0 - PHI_PURE, PHI_PURE)     # phi of the solid
+    w[L["irho"]] = mat["rho0"]
     w[L["irho"] + 1] = 1.225
     noise = 1.0e-6 * 400.0 * rng.standard_normal((2, n * n))
     w[L["iu"]] = np.where(block, 400.0, 0.0) + noise[0]
     w[L["iu"] + 1] = noise[1]
     w[L["ip"]] = 1.0e5
     w[L["ir"]] = rigid_profile(wedge_distance(X, Y), dx)
-    return Workload("impact_2d_%d" % n, 2, (n, n), lo, hi, (0, 0), [ALUMINIUM, AIR], True, w,
+    return Workload("impact_2d_%d" % n, 2, (n, n), lo, hi, (0, 0), [mat, AIR], True, w,
                     cfl=0.8, steps=3000)
 
 
