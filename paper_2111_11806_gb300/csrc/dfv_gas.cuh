@@ -55,6 +55,9 @@ struct GasArgs {
 };
 
 struct GasT {
+    // 16 rows (one warp each) plus a warp for the halo work; 15 rows (16
+    // warps, four per scheduler) measured no faster on the 256-ellipse batch
+    // (ragged last tiles, the halo spread over fewer cells)
     static constexpr int TX = 32, TY = 16, H = 2;
     static constexpr int BX = TX + 8;          // TMA box width: x from ox-4 (16-byte aligned)
     static constexpr int BY = TY + 2 * H;      // box height: y from oy-2
@@ -69,11 +72,17 @@ struct GasT {
     static constexpr unsigned BOX_BYTES = 4u * NP * BOX;
     static constexpr unsigned OWN_BYTES = 4u * NP * CELLS;   // U^n of the tile's own cells (stages 2, 3)
     static constexpr int NMAP = 4;                           // tensor maps per instance
+    // a tensor copy's shared-memory destination must be 128-byte aligned:
+    // every TMA buffer is padded to a multiple of 128 bytes
+    static constexpr int TILE_FLOATS = (NP * BOX + 31) / 32 * 32;
+    static constexpr int OWN_FLOATS = (NP * CELLS + 31) / 32 * 32;
 };
+static_assert((GasT::TILE_FLOATS * 4) % 128 == 0 && (GasT::OWN_FLOATS * 4) % 128 == 0,
+              "TMA buffers must keep 128-byte alignment");
 
-struct GasSmem {
-    float tile[2][GasT::NP][GasT::BOX];            // TMA destination, double-buffered
-    float own[2][GasT::NP][GasT::CELLS];           // U^n of the tile's cells (stages 2, 3; TMA)
+struct __align__(128) GasSmem {
+    float tile[2][GasT::TILE_FLOATS];              // TMA destination, double-buffered (planes of BOX cells)
+    float own[2][GasT::OWN_FLOATS];                // U^n of the tile's cells (stages 2, 3; TMA; planes of CELLS)
     float prim[4][GasT::PY][GasT::PX];             // rho, u, v, p of the tile and halo
     float fvx[4][GasT::TY][GasT::FXS];             // right-face values q_{i+1/2}^L, column i = -1 .. TX-1
     float fvy[4][GasT::FYS][GasT::TX];             // top-face values, row j = -1 .. TY-1
@@ -142,13 +151,13 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 __device__ __forceinline__ float gas_vanleer(float a, float b)
 {
     const float ab = a * b;
-    return ab <= 0.f ? 0.f : 2.f * ab / (a + b);
+    return ab <= 0.f ? 0.f : __fdividef(2.f * ab, a + b);
 }
 
 // Conserved (rho, rho u, rho v, rho E) -> primitive (rho, u, v, p) of the gas.
 __device__ __forceinline__ void gas_prim(const GasArgs &a, float r, float mu, float mv, float E, float w[4])
 {
-    const float ir = 1.f / r;
+    const float ir = __fdividef(1.f, r);
     const float u = mu * ir, v = mv * ir;
     const float ke = 0.5f * r * u * u + 0.5f * r * v * v;
     w[0] = r;
@@ -163,7 +172,7 @@ __device__ __forceinline__ void gas_prim(const GasArgs &a, float r, float mu, fl
 __device__ __forceinline__ void gas_hllc(const GasArgs &a, float rL, float unL, float utL, float pL, float rR,
                                          float unR, float utR, float pR, float F[4])
 {
-    const float irL = 1.f / rL, irR = 1.f / rR;
+    const float irL = __fdividef(1.f, rL), irR = __fdividef(1.f, rR);
     const float cL = sqrtf((a.Gam * pL + (pL - a.pref0)) * irL);
     const float cR = sqrtf((a.Gam * pR + (pR - a.pref0)) * irR);
     const float SL = fminf(unL - cL, unR - cR);
@@ -172,7 +181,7 @@ __device__ __forceinline__ void gas_hllc(const GasArgs &a, float rL, float unL, 
     // between mirror-image states gets S* = 0 exactly)
     const float num = __fadd_rn(__fadd_rn(pR - pL, __fmul_rn(__fmul_rn(rL, unL), SL - unL)),
                                 -__fmul_rn(__fmul_rn(rR, unR), SR - unR));
-    const float Ss = num / (rL * (SL - unL) - rR * (SR - unR));
+    const float Ss = __fdividef(num, rL * (SL - unL) - rR * (SR - unR));
     // regions: left of S_L, left star, right star, right of S_R
     const int region = SL >= 0.f ? 0 : (Ss >= 0.f ? 1 : (SR > 0.f ? 2 : 3));
     const bool left = region <= 1;
@@ -184,10 +193,13 @@ __device__ __forceinline__ void gas_hllc(const GasArgs &a, float rL, float unL, 
     float Fr = m, Fn = m * un + p, Ft = m * ut, FE = (E + p) * un;
     const bool star = region == 1 || region == 2;
     if (star) {
-        // star state U*_K = rho_K (S_K - u_K)/(S_K - S*) [1, S*, u_t, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))]
-        const float chi = (S - un) / (S - Ss);
+        // star state U*_K = rho_K chi [1, S*, u_t, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))],
+        // chi = (S_K - u_K)/(S_K - S*); with iD = 1/(S_K - S*) its energy is
+        // chi E_K + (S* - u_K)(rho_K chi S* + p_K iD): one reciprocal
+        const float iD = __fdividef(1.f, S - Ss);
+        const float chi = (S - un) * iD;
         const float rs = r * chi;
-        const float Es = rs * (E / r + (Ss - un) * (Ss + p / (r * (S - un))));
+        const float Es = chi * E + (Ss - un) * (rs * Ss + p * iD);
         Fr += S * (rs - r);
         Fn += S * (rs * Ss - m);
         Ft += S * (rs * ut - r * ut);
@@ -266,8 +278,8 @@ __device__ __forceinline__ void gas_issue(const GasArgs &a, GasSmem &S, int slot
     const CUtensorMap *m = a.tmap + T::NMAP * w.x;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&S.mbar[slot], T::BOX_BYTES + (STAGE > 1 ? T::OWN_BYTES : 0u));
-    tma_load_3d(&S.tile[slot][0][0], m + (STAGE - 1), ox - 4, oy - T::H, 0, &S.mbar[slot]);
-    if (STAGE > 1) tma_load_3d(&S.own[slot][0][0], m + 3, ox, oy, 0, &S.mbar[slot]);
+    tma_load_3d(&S.tile[slot][0], m + (STAGE - 1), ox - 4, oy - T::H, 0, &S.mbar[slot]);
+    if (STAGE > 1) tma_load_3d(&S.own[slot][0], m + 3, ox, oy, 0, &S.mbar[slot]);
 }
 
 // ------------------------------------------------------------ the stage
@@ -276,9 +288,17 @@ template <int STAGE>
 __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
 {
     using T = GasT;
+    // the dynamic shared memory is the kernel's only shared memory and starts
+    // the CTA's shared window (used directly, so that every access compiles to
+    // a shared-memory instruction); its alignment is checked below
     extern __shared__ __align__(128) unsigned char gas_smem_raw[];
     GasSmem &S = *reinterpret_cast<GasSmem *>(gas_smem_raw);
     const int tid = threadIdx.x;
+    if ((smem_u32(&S.tile[0][0]) & 127u) != 0) {
+        // never issue a misaligned tensor copy: report and stop
+        if (tid == 0 && a.nitems > 0) atomicOr(&a.inst[0].ctl->err, (unsigned)ERR_TIMEOUT);
+        return;
+    }
 
     if (tid == 0) {
         mbar_init(&S.mbar[0], 1);
@@ -308,7 +328,7 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
             if (tid == 0) atomicOr(&I.ctl->err, (unsigned)ERR_TIMEOUT);
             break;
         }
-        const float *tl = &S.tile[slot][0][0];
+        const float *tl = &S.tile[slot][0];
         const bool interior = ox >= 2 && ox + T::TX + 2 <= I.n0 && oy >= 2 && oy + T::TY + 2 <= I.n1;
 
         // 1. primitives of the tile and its halo (corners not needed)
@@ -350,12 +370,13 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
                 qRy[v] = q - 0.5f * sy;
             }
         } else {
-            // the extra warp: lanes 0-15 the right-face values of column -1,
-            // lanes 16-31 the left-face values of column TX (row l % 16); every
-            // lane the top-face value of row -1 and the bottom-face value of
-            // row TY of column l
-            const int l = tid - T::CELLS, jh = l & 15;
-            const bool west = l < 16;
+            // the extra warp: lanes 0 .. TY-1 the right-face values of column
+            // -1, lanes TY .. 2TY-1 the left-face values of column TX (row
+            // l mod TY); every lane the top-face value of row -1 and the
+            // bottom-face value of row TY of column l
+            const int l = tid - T::CELLS;
+            const bool west = l < T::TY, east = !west && l < 2 * T::TY;
+            const int jh = west ? l : (east ? l - T::TY : 0);
             const int col = west ? T::H - 1 : T::TX + T::H;
 #pragma unroll
             for (int v = 0; v < 4; v++) {
@@ -367,7 +388,7 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
                 const float qd = P[T::TY + T::H][l + T::H];
                 const float sd = gas_vanleer(qd - P[T::TY + T::H - 1][l + T::H], P[T::TY + T::H + 1][l + T::H] - qd);
                 if (west) S.fvx[v][jh][0] = qa + 0.5f * sa;
-                else S.hrx[v][jh] = qa - 0.5f * sa;
+                else if (east) S.hrx[v][jh] = qa - 0.5f * sa;
                 S.fvy[v][0][l] = qb + 0.5f * sb;
                 S.hry[v][l] = qd - 0.5f * sd;
             }
@@ -393,9 +414,9 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
                 S.fy[v][cj][ci] = Fyl[v];
             }
         } else {
-            const int l = tid - T::CELLS, jh = l & 15;
+            const int l = tid - T::CELLS, jh = l < T::TY ? l : 0;
             float G[4];
-            if (l < 16) {
+            if (l < T::TY) {
                 gas_hllc(a, S.fvx[0][jh][T::TX], S.fvx[1][jh][T::TX], S.fvx[2][jh][T::TX], S.fvx[3][jh][T::TX],
                          S.hrx[0][jh], S.hrx[1][jh], S.hrx[2][jh], S.hrx[3][jh], G);
 #pragma unroll
@@ -423,7 +444,7 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
             const long long P = I.pitch;
             const int bc = (cj + T::H) * T::BX + (ci + 4);
             // U^n at the cell: the stage input itself in stage 1, its own copy after
-            const float *own = STAGE == 1 ? tl + bc : &S.own[slot][0][tid];
+            const float *own = STAGE == 1 ? tl + bc : &S.own[slot][tid];
             const int ostr = STAGE == 1 ? T::BOX : T::CELLS;
             float o[5];
             const float unr = own[4 * ostr];
@@ -452,10 +473,10 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
                 rigid_new = o[4] > 0.5f;
                 float wv[4];
                 gas_prim(a, o[0], o[1], o[2], o[3], wv);
-                const float c2 = (a.Gam * wv[3] + (wv[3] - a.pref0)) / wv[0];
+                const float c2 = __fdividef(a.Gam * wv[3] + (wv[3] - a.pref0), wv[0]);
                 if (!(c2 > 0.f)) atomicOr(&ctl->err, (unsigned)ERR_SOUND);
                 const float cs = sqrtf(c2);
-                smax_cell = (fabsf(wv[1]) + cs) / I.dx + (fabsf(wv[2]) + cs) / I.dy;
+                smax_cell = (fabsf(wv[1]) + cs) * I.idx + (fabsf(wv[2]) + cs) * I.idy;
             }
         }
         if (STAGE == 3) {
