@@ -58,7 +58,7 @@ struct GasT {
     // 16 rows (one warp each) plus a warp for the halo work; 15 rows (16
     // warps, four per scheduler) measured no faster on the 256-ellipse batch
     // (ragged last tiles, the halo spread over fewer cells)
-    static constexpr int TX = 32, TY = 16, H = 2;
+    static constexpr int TX = 32, TY = 8, H = 2;
     static constexpr int BX = TX + 8;          // TMA box width: x from ox-4 (16-byte aligned)
     static constexpr int BY = TY + 2 * H;      // box height: y from oy-2
     static constexpr int NP = 5;               // planes of the single-gas 2-D layout
@@ -83,13 +83,15 @@ static_assert((GasT::TILE_FLOATS * 4) % 128 == 0 && (GasT::OWN_FLOATS * 4) % 128
 struct __align__(128) GasSmem {
     float tile[2][GasT::TILE_FLOATS];              // TMA destination, double-buffered (planes of BOX cells)
     float own[2][GasT::OWN_FLOATS];                // U^n of the tile's cells (stages 2, 3; TMA; planes of CELLS)
-    float prim[4][GasT::PY][GasT::PX];             // rho, u, v, p of the tile and halo
-    float fvx[4][GasT::TY][GasT::FXS];             // right-face values q_{i+1/2}^L, column i = -1 .. TX-1
-    float fvy[4][GasT::FYS][GasT::TX];             // top-face values, row j = -1 .. TY-1
-    float hrx[4][GasT::TY];                        // left-face values of column TX (closing x faces)
-    float hry[4][GasT::TX];                        // bottom-face values of row TY (closing y faces)
-    float fx[4][GasT::TY][GasT::FXS];              // fluxes of x faces i-1/2, i = 0 .. TX
-    float fy[4][GasT::FYS][GasT::TX];              // fluxes of y faces j-1/2, j = 0 .. TY
+    // one float4 per cell or face (one 128-bit access): (rho, u, v, p) for
+    // primitives and face values, (rho, rho u, rho v, rho E) for fluxes
+    float4 prim[GasT::PY][GasT::PX + 1];           // tile and halo; odd row length: a column read is conflict-free
+    float4 fvx[GasT::TY][GasT::FXS];               // right-face values q_{i+1/2}^L, column i = -1 .. TX-1
+    float4 fvy[GasT::FYS][GasT::TX];               // top-face values, row j = -1 .. TY-1
+    float4 hrx[GasT::TY];                          // left-face values of column TX (closing x faces)
+    float4 hry[GasT::TX];                          // bottom-face values of row TY (closing y faces)
+    float4 fx[GasT::TY][GasT::FXS];                // fluxes of x faces i-1/2, i = 0 .. TX
+    float4 fy[GasT::FYS][GasT::TX];                // fluxes of y faces j-1/2, j = 0 .. TY
     double red[32];
     unsigned long long mbar[2];
     long long item[2];
@@ -285,7 +287,7 @@ __device__ __forceinline__ void gas_issue(const GasArgs &a, GasSmem &S, int slot
 // ------------------------------------------------------------ the stage
 
 template <int STAGE>
-__global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
+__global__ void __launch_bounds__(GasT::THREADS, 4) k_gas_stage(GasArgs a)
 {
     using T = GasT;
     // the dynamic shared memory is the kernel's only shared memory and starts
@@ -349,8 +351,7 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
             gas_prim(a, tl[b], tl[T::BOX + b], tl[2 * T::BOX + b], tl[3 * T::BOX + b], wv);
             if (fx) wv[1] = -wv[1];
             if (fy) wv[2] = -wv[2];
-#pragma unroll
-            for (int v = 0; v < 4; v++) S.prim[v][ly + T::H][lx + T::H] = wv[v];
+            S.prim[ly + T::H][lx + T::H] = make_float4(wv[0], wv[1], wv[2], wv[3]);
         }
         __syncthreads();
         // every thread is done with the previous item: its buffer takes the next one
@@ -359,16 +360,24 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
         // 2. slopes once per cell; right/top face values to shared memory
         float qRx[4], qRy[4];
         if (tid < T::CELLS) {
+            const int py = cj + T::H, px = ci + T::H;
+            const float4 c4 = S.prim[py][px], w4 = S.prim[py][px - 1], e4 = S.prim[py][px + 1];
+            const float4 s4 = S.prim[py - 1][px], n4 = S.prim[py + 1][px];
+            const float q[4] = {c4.x, c4.y, c4.z, c4.w}, qw[4] = {w4.x, w4.y, w4.z, w4.w};
+            const float qe[4] = {e4.x, e4.y, e4.z, e4.w}, qs[4] = {s4.x, s4.y, s4.z, s4.w};
+            const float qn[4] = {n4.x, n4.y, n4.z, n4.w};
+            float lx4[4], ly4[4];
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                const float q = S.prim[v][cj + T::H][ci + T::H];
-                const float sx = gas_vanleer(q - S.prim[v][cj + T::H][ci + T::H - 1], S.prim[v][cj + T::H][ci + T::H + 1] - q);
-                const float sy = gas_vanleer(q - S.prim[v][cj + T::H - 1][ci + T::H], S.prim[v][cj + T::H + 1][ci + T::H] - q);
-                S.fvx[v][cj][ci + 1] = q + 0.5f * sx;
-                S.fvy[v][cj + 1][ci] = q + 0.5f * sy;
-                qRx[v] = q - 0.5f * sx;
-                qRy[v] = q - 0.5f * sy;
+                const float sx = gas_vanleer(q[v] - qw[v], qe[v] - q[v]);
+                const float sy = gas_vanleer(q[v] - qs[v], qn[v] - q[v]);
+                lx4[v] = q[v] + 0.5f * sx;
+                ly4[v] = q[v] + 0.5f * sy;
+                qRx[v] = q[v] - 0.5f * sx;
+                qRy[v] = q[v] - 0.5f * sy;
             }
+            S.fvx[cj][ci + 1] = make_float4(lx4[0], lx4[1], lx4[2], lx4[3]);
+            S.fvy[cj + 1][ci] = make_float4(ly4[0], ly4[1], ly4[2], ly4[3]);
         } else {
             // the extra warp: lanes 0 .. TY-1 the right-face values of column
             // -1, lanes TY .. 2TY-1 the left-face values of column TX (row
@@ -378,56 +387,55 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
             const bool west = l < T::TY, east = !west && l < 2 * T::TY;
             const int jh = west ? l : (east ? l - T::TY : 0);
             const int col = west ? T::H - 1 : T::TX + T::H;
+            const float4 a0 = S.prim[jh + T::H][col - 1], a1 = S.prim[jh + T::H][col], a2 = S.prim[jh + T::H][col + 1];
+            const float4 b0 = S.prim[T::H - 2][l + T::H], b1 = S.prim[T::H - 1][l + T::H], b2 = S.prim[T::H][l + T::H];
+            const float4 d0 = S.prim[T::TY + T::H - 1][l + T::H], d1 = S.prim[T::TY + T::H][l + T::H],
+                         d2 = S.prim[T::TY + T::H + 1][l + T::H];
+            const float A0[4] = {a0.x, a0.y, a0.z, a0.w}, A1[4] = {a1.x, a1.y, a1.z, a1.w}, A2[4] = {a2.x, a2.y, a2.z, a2.w};
+            const float B0[4] = {b0.x, b0.y, b0.z, b0.w}, B1[4] = {b1.x, b1.y, b1.z, b1.w}, B2[4] = {b2.x, b2.y, b2.z, b2.w};
+            const float D0[4] = {d0.x, d0.y, d0.z, d0.w}, D1[4] = {d1.x, d1.y, d1.z, d1.w}, D2[4] = {d2.x, d2.y, d2.z, d2.w};
+            float ra[4], rb[4], rd[4];
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                const float (*P)[T::PX] = S.prim[v];
-                const float qa = P[jh + T::H][col];
-                const float sa = gas_vanleer(qa - P[jh + T::H][col - 1], P[jh + T::H][col + 1] - qa);
-                const float qb = P[T::H - 1][l + T::H];
-                const float sb = gas_vanleer(qb - P[T::H - 2][l + T::H], P[T::H][l + T::H] - qb);
-                const float qd = P[T::TY + T::H][l + T::H];
-                const float sd = gas_vanleer(qd - P[T::TY + T::H - 1][l + T::H], P[T::TY + T::H + 1][l + T::H] - qd);
-                if (west) S.fvx[v][jh][0] = qa + 0.5f * sa;
-                else if (east) S.hrx[v][jh] = qa - 0.5f * sa;
-                S.fvy[v][0][l] = qb + 0.5f * sb;
-                S.hry[v][l] = qd - 0.5f * sd;
+                const float sa = gas_vanleer(A1[v] - A0[v], A2[v] - A1[v]);
+                const float sb = gas_vanleer(B1[v] - B0[v], B2[v] - B1[v]);
+                const float sd = gas_vanleer(D1[v] - D0[v], D2[v] - D1[v]);
+                ra[v] = west ? A1[v] + 0.5f * sa : A1[v] - 0.5f * sa;
+                rb[v] = B1[v] + 0.5f * sb;
+                rd[v] = D1[v] - 0.5f * sd;
             }
+            if (west) S.fvx[jh][0] = make_float4(ra[0], ra[1], ra[2], ra[3]);
+            else if (east) S.hrx[jh] = make_float4(ra[0], ra[1], ra[2], ra[3]);
+            S.fvy[0][l] = make_float4(rb[0], rb[1], rb[2], rb[3]);
+            S.hry[l] = make_float4(rd[0], rd[1], rd[2], rd[3]);
         }
         __syncthreads();
 
         // 3. faces: the cell's left x face and bottom y face
         float Fxl[4], Fyl[4];
         if (tid < T::CELLS) {
-            gas_hllc(a, S.fvx[0][cj][ci], S.fvx[1][cj][ci], S.fvx[2][cj][ci], S.fvx[3][cj][ci], qRx[0], qRx[1],
-                     qRx[2], qRx[3], Fxl);
+            const float4 Lx = S.fvx[cj][ci], Ly = S.fvy[cj][ci];
+            gas_hllc(a, Lx.x, Lx.y, Lx.z, Lx.w, qRx[0], qRx[1], qRx[2], qRx[3], Fxl);
             float G[4];
-            gas_hllc(a, S.fvy[0][cj][ci], S.fvy[2][cj][ci], S.fvy[1][cj][ci], S.fvy[3][cj][ci], qRy[0], qRy[2],
-                     qRy[1], qRy[3], G);
+            gas_hllc(a, Ly.x, Ly.z, Ly.y, Ly.w, qRy[0], qRy[2], qRy[1], qRy[3], G);
             // y face: normal momentum is rho v, tangential rho u
             Fyl[0] = G[0];
             Fyl[1] = G[2];
             Fyl[2] = G[1];
             Fyl[3] = G[3];
-#pragma unroll
-            for (int v = 0; v < 4; v++) {
-                S.fx[v][cj][ci] = Fxl[v];
-                S.fy[v][cj][ci] = Fyl[v];
-            }
+            S.fx[cj][ci] = make_float4(Fxl[0], Fxl[1], Fxl[2], Fxl[3]);
+            S.fy[cj][ci] = make_float4(Fyl[0], Fyl[1], Fyl[2], Fyl[3]);
         } else {
             const int l = tid - T::CELLS, jh = l < T::TY ? l : 0;
             float G[4];
             if (l < T::TY) {
-                gas_hllc(a, S.fvx[0][jh][T::TX], S.fvx[1][jh][T::TX], S.fvx[2][jh][T::TX], S.fvx[3][jh][T::TX],
-                         S.hrx[0][jh], S.hrx[1][jh], S.hrx[2][jh], S.hrx[3][jh], G);
-#pragma unroll
-                for (int v = 0; v < 4; v++) S.fx[v][jh][T::TX] = G[v];
+                const float4 L = S.fvx[jh][T::TX], R = S.hrx[jh];
+                gas_hllc(a, L.x, L.y, L.z, L.w, R.x, R.y, R.z, R.w, G);
+                S.fx[jh][T::TX] = make_float4(G[0], G[1], G[2], G[3]);
             }
-            gas_hllc(a, S.fvy[0][T::TY][l], S.fvy[2][T::TY][l], S.fvy[1][T::TY][l], S.fvy[3][T::TY][l], S.hry[0][l],
-                     S.hry[2][l], S.hry[1][l], S.hry[3][l], G);
-            S.fy[0][T::TY][l] = G[0];
-            S.fy[1][T::TY][l] = G[2];
-            S.fy[2][T::TY][l] = G[1];
-            S.fy[3][T::TY][l] = G[3];
+            const float4 L = S.fvy[T::TY][l], R = S.hry[l];
+            gas_hllc(a, L.x, L.z, L.y, L.w, R.x, R.z, R.y, R.w, G);
+            S.fy[T::TY][l] = make_float4(G[0], G[2], G[1], G[3]);
         }
         __syncthreads();
 
@@ -449,11 +457,13 @@ __global__ void __launch_bounds__(GasT::THREADS, 2) k_gas_stage(GasArgs a)
             float o[5];
             const float unr = own[4 * ostr];
             const bool masked = unr > 0.5f;
+            const float4 fe4 = S.fx[cj][ci + 1], fn4 = S.fy[cj + 1][ci];
+            const float Fxr[4] = {fe4.x, fe4.y, fe4.z, fe4.w}, Fyr[4] = {fn4.x, fn4.y, fn4.z, fn4.w};
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 const float unv = own[v * ostr];
-                const float div = (S.fx[v][cj][ci + 1] - Fxl[v]) * I.idx;
-                const float dvy = (S.fy[v][cj + 1][ci] - Fyl[v]) * I.idy;
+                const float div = (Fxr[v] - Fxl[v]) * I.idx;
+                const float dvy = (Fyr[v] - Fyl[v]) * I.idy;
                 Acc<float> D;
                 D.set(div);
                 D.add(dvy);
