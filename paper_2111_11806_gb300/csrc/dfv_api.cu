@@ -16,6 +16,7 @@
 
 #include "../../include/dfvrb.h"
 #include "dfv_gas.cuh"
+#include "dfv_gas3.cuh"
 #include "dfv_kernels.cuh"
 #include "dfv_ops.h"
 
@@ -55,6 +56,7 @@ struct dfv_grid {
     // shape allows it; it runs the stages whenever the material, the options
     // and the body allow it too (gas_on)
     bool gas_ready = false;
+    bool gas3_ready = false;   // the 3-D gas kernel is prepared (FP32 3-D single-material fluid grid)
     bool body_moving = false;
     dfv::GasInst *d_ginst = nullptr;
     CUtensorMap *d_tmaps = nullptr;
@@ -262,9 +264,41 @@ bool gas_on(const dfv_grid *g)
                              g->g.hllc_lm, g->dynamic || g->body_moving, g->g.n[0]);
 }
 
+// Whether the stages of a 3-D grid run in the 3-D gas kernel now: FP32, one
+// ideal or stiffened gas, no solid, no periodic side, no HLLC-LM, a static body.
+bool gas3_on(const dfv_grid *g)
+{
+    const int per[3] = {g->g.periodic[0], g->g.periodic[1], 0};
+    return g->gas3_ready && g->dim == 3 && g->nmat == 1 && !g->g.periodic[2] &&
+           dfv::gas_eligible(g->precision == DFV_FP32, 2, g->nmat, g->solid, g->g.mat[0].kind, per, g->g.hllc_lm,
+                             g->dynamic || g->body_moving, 0);
+}
+
 // One SSP-RK3 stage: the gas kernel when it applies, else the general one.
 dfv_status launch_stage(dfv_grid *g, int s, const void *in, const void *un, void *out, int want_force, int next)
 {
+    if (gas3_on(g)) {
+        dfv::Gas3Args a;
+        a.in = (const float *)in;
+        a.un = (const float *)un;
+        a.out = (float *)out;
+        a.ctl = g->ctl;
+        a.n0 = g->g.n[0];
+        a.n1 = g->g.n[1];
+        a.n2 = g->g.n[2];
+        a.pitch = g->g.pitch;
+        a.idx = (float)g->g.inv_dx[0];
+        a.idy = (float)g->g.inv_dx[1];
+        a.idz = (float)g->g.inv_dx[2];
+        for (int d = 0; d < 3; d++)
+            for (int k = 0; k < 2; k++) a.wall[d][k] = g->g.wall[d][k];
+        a.zc = dfv::Gas3T::ZCHUNK;
+        a.Gam = g->g.mc_f[0].Gam;
+        a.invGam = g->g.mc_f[0].invGam;
+        a.pref0 = g->g.mc_f[0].pref0;
+        DFV_CU(g, dfv::gas3_stage(s, a, g->stream), "k_gas3_stage");
+        return DFV_OK;
+    }
     if (gas_on(g)) {
         dfv::GasArgs a;
         a.inst = g->d_ginst;
@@ -421,6 +455,14 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
     if (e != cudaSuccess) {
         delete g;
         return DFV_ERR_CUDA;
+    }
+    if (!opt->general_stage && precision == DFV_FP32 && dim == 3 && opt->nmat == 1 && g->solid == 0) {
+        e = dfv::gas3_prepare();
+        if (e != cudaSuccess) {
+            delete g;
+            return DFV_ERR_CUDA;
+        }
+        g->gas3_ready = true;
     }
     // the gas kernel's tensor maps over U, U1, U3 and its instance record
     g->d_tmaps = (CUtensorMap *)(g->ws + L.off_gas);

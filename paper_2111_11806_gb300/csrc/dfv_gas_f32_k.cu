@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 
 #include "dfv_gas.cuh"
+#include "dfv_gas3.cuh"
 
 namespace dfv {
 
@@ -77,6 +78,25 @@ bool gas_encode_maps(CUtensorMap maps[GasT::NMAP], const void *const bases[3], l
         if (r != CUDA_SUCCESS) return false;
     }
     return true;
+}
+
+cudaError_t gas3_prepare()
+{
+    const int bytes = (int)sizeof(Gas3Smem);
+    cudaError_t e = cudaFuncSetAttribute(k_gas3_stage<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gas3_stage<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gas3_stage<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+cudaError_t gas3_stage(int stage, const Gas3Args &a, cudaStream_t st)
+{
+    const dim3 g((a.n0 + Gas3T::TX - 1) / Gas3T::TX, (a.n1 + Gas3T::TY - 1) / Gas3T::TY, (a.n2 + a.zc - 1) / a.zc);
+    const dim3 b(Gas3T::THREADS);
+    const size_t sm = sizeof(Gas3Smem);
+    if (stage == 1) return launch_pdl(k_gas3_stage<1>, g, b, sm, st, a);
+    if (stage == 2) return launch_pdl(k_gas3_stage<2>, g, b, sm, st, a);
+    return launch_pdl(k_gas3_stage<3>, g, b, sm, st, a);
 }
 
 }  // namespace dfv

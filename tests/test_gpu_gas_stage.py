@@ -1,4 +1,4 @@
-"""GPU parity of the TMA-tiled stage kernel of 2-D single-gas FP32 grids
+"""GPU parity of the stage kernels of single-gas FP32 grids (2-D: TMA-tiled; 3-D: marching)
 (dfv_gas.cuh): against the FP64 oracle (relative L1 per conserved plane
 <= 1e-4) on grids with ragged last tiles in x and y, a single tile, a grid
 smaller than one tile, reflective walls on every side, a stiffened gas, with
@@ -81,3 +81,37 @@ def test_moving_body_takes_the_general_kernel():
     o, g = run_both(wl, 10, B.DFV_FP32)
     err = rel_l1(g.cons(), o.cons(), wl)
     assert np.all(err <= 1e-4), err
+
+
+# ---- the 3-D gas kernel (dfv_gas3.cuh): marching columns, ring of planes
+
+CASES3 = [
+    ("three_chunks_40x30x75", lambda: W.random_state(3, (40, 30, 75), 1, False, seed=221)),
+    ("ragged_37x21x33", lambda: W.random_state(3, (37, 21, 33), 1, False, seed=222)),
+    ("walls_all_34x18x40", lambda: walled(W.random_state(3, (34, 18, 40), 1, False, seed=223), (1, 1, 1, 1, 1, 1))),
+    ("walls_z_33x26x40", lambda: walled(W.random_state(3, (33, 26, 40), 1, False, seed=224), (0, 0, 0, 0, 1, 1))),
+    ("thin_z_35x9x3", lambda: W.random_state(3, (35, 9, 3), 1, False, seed=225)),
+    ("one_plane_40x10x1", lambda: W.random_state(3, (40, 10, 1), 1, False, seed=226, body=False)),
+    ("sphere_48", lambda: W.sphere_3d(48)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES3, ids=[c[0] for c in CASES3])
+def test_gas3_kernel_matches_oracle(name, make):
+    wl = make()
+    for steps in (1, 10):
+        o, g = run_both(wl, steps, B.DFV_FP32)
+        err = rel_l1(g.cons(), o.cons(), wl)
+        assert np.all(err <= 1e-4), (steps, err)
+
+
+@pytest.mark.parametrize("name,make", [CASES3[0], CASES3[2], CASES3[6]], ids=[CASES3[i][0] for i in (0, 2, 6)])
+def test_gas3_kernel_matches_general_kernel(name, make):
+    wl = make()
+    g1 = B.Grid.from_workload(wl, precision=B.DFV_FP32)
+    g2 = B.Grid.from_workload(wl, precision=B.DFV_FP32, general_stage=True)
+    t1 = g1.run(8, 0.8)
+    t2 = g2.run(8, 0.8)
+    assert t1 == pytest.approx(t2, rel=1e-5)
+    err = rel_l1(g1.cons(), g2.cons(), wl)
+    assert np.all(err <= 1e-5), err
