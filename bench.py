@@ -52,7 +52,8 @@ METRIC = "cell-updates/s FP32 & batched vs plain FP64 at stated L1 error; % HBM 
 UNIT = "cell-updates/s"
 BATCH_COUNT = 256
 KERNEL_SOURCES = ["paper_2111_11806_gb300/csrc/dfv_device.cuh", "paper_2111_11806_gb300/csrc/dfv_kernels.cuh",
-                  "paper_2111_11806_gb300/csrc/dfv_batch.cuh"]
+                  "paper_2111_11806_gb300/csrc/dfv_batch.cuh", "paper_2111_11806_gb300/csrc/dfv_gas.cuh",
+                  "paper_2111_11806_gb300/csrc/dfv_gas_f32_k.cu"]
 
 
 def parse():
