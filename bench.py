@@ -53,7 +53,7 @@ UNIT = "cell-updates/s"
 BATCH_COUNT = 256
 KERNEL_SOURCES = ["paper_2111_11806_gb300/csrc/dfv_device.cuh", "paper_2111_11806_gb300/csrc/dfv_kernels.cuh",
                   "paper_2111_11806_gb300/csrc/dfv_batch.cuh", "paper_2111_11806_gb300/csrc/dfv_gas.cuh",
-                  "paper_2111_11806_gb300/csrc/dfv_gas_f32_k.cu"]
+                  "paper_2111_11806_gb300/csrc/dfv_gas_f32_k.cu", "paper_2111_11806_gb300/csrc/dfv_gasw.cuh"]
 
 
 def parse():

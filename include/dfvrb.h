@@ -129,10 +129,14 @@ typedef struct {
                             step-start state: one extra launch per step) */
     int general_stage;   /* 0: the SSP-RK3 stages of a 2-D FP32 grid of one ideal or
                             stiffened gas (no solid, no periodic side, no HLLC-LM,
-                            a static body, n[0] a multiple of 4) run in the
-                            TMA-tiled gas kernel, the others in the general
-                            stage kernel; 1: always the general stage kernel.
-                            The two agree to FP32 rounding. */
+                            a static body) run in the warp-marching gas kernel,
+                            the others in the general stage kernel; 1: always
+                            the general stage kernel.  The two agree to FP32
+                            rounding. */
+    int gas_rows;        /* rows per work item of the gas kernel (a strip of 28
+                            columns marches through that many rows): 0 chooses
+                            from the total cell count (8 to 64), else 1 to 4096;
+                            results do not depend on it */
 } dfv_options;
 
 typedef struct dfv_grid dfv_grid;

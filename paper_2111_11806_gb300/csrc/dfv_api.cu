@@ -15,8 +15,8 @@
 #include <array>
 
 #include "../../include/dfvrb.h"
-#include "dfv_gas.cuh"
 #include "dfv_gas3.cuh"
+#include "dfv_gasw.cuh"
 #include "dfv_kernels.cuh"
 #include "dfv_ops.h"
 
@@ -51,15 +51,13 @@ struct dfv_grid {
     bool prof = false;                   // per-kernel event timing (dfv_profile)
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::array<cudaEvent_t, 6>> ev_steps;
-    // the 2-D single-gas FP32 stage kernel (dfv_gas.cuh): its tensor maps and
-    // instance record sit in the workspace, encoded at creation when the grid's
-    // shape allows it; it runs the stages whenever the material, the options
-    // and the body allow it too (gas_on)
+    // the 2-D single-gas FP32 stage kernel (dfv_gasw.cuh): its instance record
+    // sits in the workspace, written at creation; it runs the stages whenever
+    // the material, the options and the body allow it (gas_on)
     bool gas_ready = false;
     bool gas3_ready = false;   // the 3-D gas kernel is prepared (FP32 3-D single-material fluid grid)
     bool body_moving = false;
     dfv::GasInst *d_ginst = nullptr;
-    CUtensorMap *d_tmaps = nullptr;
     int gas_grid = 1;
     long long gas_tiles = 0;
 };
@@ -117,8 +115,8 @@ Layout plan(int dim, const int n[3], int nmat, int solid, int precision)
     off += align256(sizeof(Ctl));
     L.off_part = off;
     off += align256(sizeof(double) * 4 * (size_t)nparts);
-    L.off_gas = off;   // three tensor maps, then the gas kernel's instance record
-    off += align256(dfv::GasT::NMAP * sizeof(CUtensorMap) + sizeof(dfv::GasInst));
+    L.off_gas = off;   // the gas kernel's instance record
+    off += align256(sizeof(dfv::GasInst));
     const size_t state = align256((size_t)w * nvar * (size_t)L.pitch);
     L.off_U = off;
     off += state;
@@ -255,13 +253,13 @@ cudaEvent_t take_event(dfv_grid *g)
 // needs only the rigid box that stage 3 folded.
 bool can_defer(const dfv_grid *g) { return !g->dynamic && g->g.probe_mode == 0; }
 
-// Whether the stages run in the gas kernel now (the tensor maps exist, and
+// Whether the stages run in the gas kernel now (its record exists, and
 // the material, the options and the body allow it).
 bool gas_on(const dfv_grid *g)
 {
     return g->gas_ready && g->nmat == 1 &&
            dfv::gas_eligible(g->precision == DFV_FP32, g->dim, g->nmat, g->solid, g->g.mat[0].kind, g->g.periodic,
-                             g->g.hllc_lm, g->dynamic || g->body_moving, g->g.n[0]);
+                             g->g.hllc_lm, g->dynamic || g->body_moving);
 }
 
 // Whether the stages of a 3-D grid run in the 3-D gas kernel now: FP32, one
@@ -271,7 +269,7 @@ bool gas3_on(const dfv_grid *g)
     const int per[3] = {g->g.periodic[0], g->g.periodic[1], 0};
     return g->gas3_ready && g->dim == 3 && g->nmat == 1 && !g->g.periodic[2] &&
            dfv::gas_eligible(g->precision == DFV_FP32, 2, g->nmat, g->solid, g->g.mat[0].kind, per, g->g.hllc_lm,
-                             g->dynamic || g->body_moving, 0);
+                             g->dynamic || g->body_moving);
 }
 
 // One SSP-RK3 stage: the gas kernel when it applies, else the general one.
@@ -300,19 +298,18 @@ dfv_status launch_stage(dfv_grid *g, int s, const void *in, const void *un, void
         return DFV_OK;
     }
     if (gas_on(g)) {
-        dfv::GasArgs a;
+        dfv::GaswArgs a;
         a.inst = g->d_ginst;
-        a.tmap = g->d_tmaps;
         a.items = nullptr;
         a.nitems = g->gas_tiles;
         a.queue = nullptr;
+        a.in = (const float *)in;
         a.un = (const float *)un;
         a.out = (float *)out;
         a.Gam = g->g.mc_f[0].Gam;
         a.invGam = g->g.mc_f[0].invGam;
         a.pref0 = g->g.mc_f[0].pref0;
-        (void)in;   // the tensor maps address the stage input (U^n, U1, U3 for stages 1-3)
-        DFV_CU(g, dfv::gas_stage(s, a, g->gas_grid, g->stream), "k_gas_stage");
+        DFV_CU(g, dfv::gasw_stage(s, a, g->gas_grid, g->stream), "k_gasw_stage");
         return DFV_OK;
     }
     DFV_CU(g, g->ops->stage(s, g->g, in, un, out, g->ctl, g->partials, want_force, next, g->stream), "k_stage");
@@ -384,6 +381,7 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
     *out = nullptr;
     if (dim < 1 || dim > 3 || opt->nmat < 1 || opt->nmat > 3) return DFV_ERR_ARG;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
+    if (opt->gas_rows < 0 || opt->gas_rows > 4096) return DFV_ERR_ARG;
     int n3[3] = {1, 1, 1};
     for (int d = 0; d < dim; d++) {
         if (n[d] < 1 || !(hi[d] > lo[d])) return DFV_ERR_ARG;
@@ -464,47 +462,43 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
         }
         g->gas3_ready = true;
     }
-    // the gas kernel's tensor maps over U, U1, U3 and its instance record
-    g->d_tmaps = (CUtensorMap *)(g->ws + L.off_gas);
-    g->d_ginst = (dfv::GasInst *)(g->ws + L.off_gas + dfv::GasT::NMAP * sizeof(CUtensorMap));
+    // the gas kernel's instance record: strips of 28 columns x chunks of rows
+    g->d_ginst = (dfv::GasInst *)(g->ws + L.off_gas);
     if (!opt->general_stage && precision == DFV_FP32 && dim == 2 && opt->nmat == 1 && g->solid == 0 &&
-        !p.periodic[0] && !p.periodic[1] && p.n[0] % 4 == 0) {
-        CUtensorMap maps[dfv::GasT::NMAP];
-        const void *bases[3] = {g->U, g->U1, g->U3};
-        if (dfv::gas_encode_maps(maps, bases, 0, p.n[0], p.n[1], p.pitch)) {
-            dfv::GasInst I;
-            memset(&I, 0, sizeof(I));
-            I.n0 = p.n[0];
-            I.n1 = p.n[1];
-            I.tiles_x = (p.n[0] + dfv::GasT::TX - 1) / dfv::GasT::TX;
-            I.ntiles = I.tiles_x * ((p.n[1] + dfv::GasT::TY - 1) / dfv::GasT::TY);
-            I.off = 0;
-            I.pitch = p.pitch;
-            I.dx = (float)p.dx[0];
-            I.dy = (float)p.dx[1];
-            I.idx = (float)p.inv_dx[0];
-            I.idy = (float)p.inv_dx[1];
-            I.wall_x0 = p.wall[0][0];
-            I.wall_x1 = p.wall[0][1];
-            I.wall_y0 = p.wall[1][0];
-            I.wall_y1 = p.wall[1][1];
-            I.ctl = g->ctl;
-            int dev = 0, sms = 152;
-            e = dfv::gas_prepare();
-            if (e == cudaSuccess) e = cudaGetDevice(&dev);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, g->stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_ginst, &I, sizeof(I), cudaMemcpyHostToDevice, g->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-            if (e != cudaSuccess) {
-                delete g;
-                return DFV_ERR_CUDA;
-            }
-            g->gas_tiles = I.ntiles;
-            const long long persistent = (long long)sms * dfv::gas_max_ctas_per_sm();
-            g->gas_grid = (int)std::max(1LL, std::min(persistent, g->gas_tiles));
-            g->gas_ready = true;
+        !p.periodic[0] && !p.periodic[1]) {
+        dfv::GasInst I;
+        memset(&I, 0, sizeof(I));
+        I.n0 = p.n[0];
+        I.n1 = p.n[1];
+        I.rows = opt->gas_rows > 0 ? opt->gas_rows : dfv::gasw_rows((long long)p.n[0] * p.n[1]);
+        I.tiles_x = dfv::gasw_strips(p.n[0]);
+        I.ntiles = I.tiles_x * ((p.n[1] + I.rows - 1) / I.rows);
+        I.off = 0;
+        I.pitch = p.pitch;
+        I.dx = (float)p.dx[0];
+        I.dy = (float)p.dx[1];
+        I.idx = (float)p.inv_dx[0];
+        I.idy = (float)p.inv_dx[1];
+        I.wall_x0 = p.wall[0][0];
+        I.wall_x1 = p.wall[0][1];
+        I.wall_y0 = p.wall[1][0];
+        I.wall_y1 = p.wall[1][1];
+        I.ctl = g->ctl;
+        int dev = 0, sms = 152;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_ginst, &I, sizeof(I), cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            delete g;
+            return DFV_ERR_CUDA;
         }
+        g->gas_tiles = I.ntiles;
+        // CTAs of independent warps: a persistent grid, or one warp per item when there are fewer
+        const long long persistent = (long long)sms * dfv::gasw_max_ctas_per_sm();
+        const long long ctas = (g->gas_tiles + dfv::GaswT::WARPS - 1) / dfv::GaswT::WARPS;
+        g->gas_grid = (int)std::max(1LL, std::min(persistent, ctas));
+        g->gas_ready = true;
     }
     k_init_ctl<<<1, 1, 0, g->stream>>>(g->ctl);
     g->launches++;

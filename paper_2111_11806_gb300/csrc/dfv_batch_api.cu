@@ -14,7 +14,7 @@
 
 #include "../../include/dfvrb.h"
 #include "dfv_batch.cuh"
-#include "dfv_gas.cuh"
+#include "dfv_gasw.cuh"
 #include "dfv_ops.h"
 
 using dfv::BatchArgs;
@@ -29,9 +29,10 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Plan {
     size_t off_inst, off_items0, off_items1, off_ctl, off_ctlbak, off_part, off_queue, off_vbody;
-    size_t off_ginst, off_tmaps, off_gitems0, off_gitems1;   // the gas stage kernel's records
+    size_t off_ginst, off_gitems0, off_gitems1;   // the gas stage kernel's records
     size_t off_U, off_U1, off_U3, off_Ubak, off_stage, total;
     long long elems, nitems, max_cells, ntiles_total, gas_nitems;
+    int gas_rows;
     std::vector<long long> inst_off, inst_part0;
     std::vector<int> tiles_x, tiles_y;
 };
@@ -42,7 +43,7 @@ int tile_y(int precision) { return precision == DFV_FP32 ? dfv::Tile<2, 4>::TY :
 
 int nvar_2d(int nmat) { return (nmat - 1) + nmat + 2 + 1 + 1; }
 
-bool plan_batch(int count, const dfv_instance_desc *desc, int precision, int nmat, Plan &P)
+bool plan_batch(int count, const dfv_instance_desc *desc, int precision, int nmat, int gas_rows, Plan &P)
 {
     const int w = precision == DFV_FP32 ? 4 : 8;
     const int nvar = nvar_2d(nmat);
@@ -65,10 +66,13 @@ bool plan_batch(int count, const dfv_instance_desc *desc, int precision, int nma
         P.nitems += (long long)P.tiles_x[i] * P.tiles_y[i];
         P.max_cells = std::max(P.max_cells, nc);
     }
+    // the gas stage kernel's work items: strips of 28 columns x chunks of rows
+    long long cells = 0;
+    for (int i = 0; i < count; i++) cells += (long long)desc[i].n[0] * desc[i].n[1];
+    P.gas_rows = gas_rows > 0 ? gas_rows : dfv::gasw_rows(cells);
     P.gas_nitems = 0;
     for (int i = 0; i < count; i++)
-        P.gas_nitems += (long long)((desc[i].n[0] + dfv::GasT::TX - 1) / dfv::GasT::TX) *
-                        ((desc[i].n[1] + dfv::GasT::TY - 1) / dfv::GasT::TY);
+        P.gas_nitems += (long long)dfv::gasw_strips(desc[i].n[0]) * ((desc[i].n[1] + P.gas_rows - 1) / P.gas_rows);
     P.ntiles_total = P.nitems;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -85,7 +89,6 @@ bool plan_batch(int count, const dfv_instance_desc *desc, int precision, int nma
     P.off_queue = take(sizeof(unsigned int) * 8);
     P.off_vbody = take(sizeof(double) * 3 * count);
     P.off_ginst = take(sizeof(dfv::GasInst) * count);
-    P.off_tmaps = take(sizeof(CUtensorMap) * dfv::GasT::NMAP * count);
     P.off_gitems0 = take(sizeof(int2) * P.gas_nitems);
     P.off_gitems1 = take(sizeof(int2) * P.gas_nitems);
     P.off_U = take((size_t)w * P.elems);
@@ -130,12 +133,11 @@ struct dfv_batch {
     bool graph_ready = false;
     long long graph_launches = 0;   // kernels in one replay of the step graph
     bool prof = false;
-    // the 2-D single-gas FP32 stage kernel (dfv_gas.cuh): tensor maps,
-    // instance records and (instance, tile) lists of its 32 x 16 tiles
+    // the 2-D single-gas FP32 stage kernel (dfv_gasw.cuh): instance records
+    // and (instance, item) lists of its strips x chunks
     bool gas = false;
     int gas_max_ctas = 1;
     dfv::GasInst *d_ginst = nullptr;
-    CUtensorMap *d_tmaps = nullptr;
     int2 *d_gitems[2] = {nullptr, nullptr};
     std::vector<std::array<cudaEvent_t, 5>> ev_steps;
     std::vector<cudaEvent_t> ev_free;
@@ -211,21 +213,22 @@ dfv_status phase(dfv_batch *b, int ph, const void *in, const void *un, void *out
     const bool per_inst = (ph == 0 || ph == 5 || ph == 6 || ph == 7);
     if (b->gas && ph >= 1 && ph <= 3) {
         const dfv::MatC<float> &m = b->hinst[0].g.mc_f[0];
-        dfv::GasArgs ga;
+        dfv::GaswArgs ga;
         ga.inst = b->d_ginst;
-        ga.tmap = b->d_tmaps;
         ga.items = b->d_gitems[b->schedule == 0 ? 0 : 1];
         ga.nitems = b->plan.gas_nitems;
         ga.queue = a.queue;
+        ga.in = (const float *)in;
         ga.un = (const float *)un;
         ga.out = (float *)out;
         ga.Gam = m.Gam;
         ga.invGam = m.invGam;
         ga.pref0 = m.pref0;
-        const long long n = b->plan.gas_nitems;
+        // CTAs of independent warps, one warp per item at a time
+        const long long n = (b->plan.gas_nitems + dfv::GaswT::WARPS - 1) / dfv::GaswT::WARPS;
         const long long persistent = (long long)b->sm_count * std::min(std::max(b->ctas_per_sm, 1), b->gas_max_ctas);
         const int grid = (int)std::max(1LL, b->ctas_per_sm <= 0 ? n : std::min(persistent, n));
-        B_CU(b, dfv::gas_stage(ph, ga, grid, b->stream), "gas stage kernel");
+        B_CU(b, dfv::gasw_stage(ph, ga, grid, b->stream), "gas stage kernel");
         b->launches++;
         return DFV_OK;
     }
@@ -307,8 +310,9 @@ dfv_status dfv_batch_workspace_bytes(int dim, int count, const dfv_instance_desc
     if (!desc || !opt || !bytes || count < 1) return DFV_ERR_ARG;
     if (dim != 2 || opt->solid || opt->nmat < 1 || opt->nmat > 2) return DFV_ERR_UNSUPPORTED;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
+    if (opt->gas_rows < 0 || opt->gas_rows > 4096) return DFV_ERR_ARG;
     Plan P;
-    if (!plan_batch(count, desc, precision, opt->nmat, P)) return DFV_ERR_ARG;
+    if (!plan_batch(count, desc, precision, opt->nmat, opt->gas_rows, P)) return DFV_ERR_ARG;
     *bytes = P.total;
     return DFV_OK;
 }
@@ -321,6 +325,7 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     *out = nullptr;
     if (dim != 2 || opt->solid || opt->nmat < 1 || opt->nmat > 2) return DFV_ERR_UNSUPPORTED;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
+    if (opt->gas_rows < 0 || opt->gas_rows > 4096) return DFV_ERR_ARG;
     dfv_batch *b = new dfv_batch();
     b->count = count;
     b->precision = precision;
@@ -328,7 +333,7 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     b->nmat_opt = opt->nmat;
     b->seed_opt = (opt->normal_method == 1 ? 1 : 0) | (opt->seed_variant == 1 ? 2 : 0);
     b->desc.assign(desc, desc + count);
-    if (!plan_batch(count, desc, precision, opt->nmat, b->plan)) {
+    if (!plan_batch(count, desc, precision, opt->nmat, opt->gas_rows, b->plan)) {
         delete b;
         return DFV_ERR_ARG;
     }
@@ -420,33 +425,30 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
-    // the gas stage kernel: one FP32 gas, no HLLC-LM, every instance with a
-    // static body, no periodic side and rows of a multiple of 4 cells
+    // the gas stage kernel (dfv_gasw.cuh): one FP32 gas, no HLLC-LM, every
+    // instance with a static body and no periodic side
     b->d_ginst = (dfv::GasInst *)(b->ws + P.off_ginst);
-    b->d_tmaps = (CUtensorMap *)(b->ws + P.off_tmaps);
     b->d_gitems[0] = (int2 *)(b->ws + P.off_gitems0);
     b->d_gitems[1] = (int2 *)(b->ws + P.off_gitems1);
     bool gas = !opt->general_stage && precision == DFV_FP32 && opt->nmat == 1 && !opt->hllc_lm;
     for (int i = 0; i < count && gas; i++) {
         const int per[3] = {b->hinst[i].g.periodic[0], b->hinst[i].g.periodic[1], 0};
         const bool moving = desc[i].v_body[0] != 0.0 || desc[i].v_body[1] != 0.0 || desc[i].v_body[2] != 0.0;
-        gas = dfv::gas_eligible(1, 2, 1, 0, DFV_MAT_IDEAL, per, 0, moving, desc[i].n[0]);
+        gas = dfv::gas_eligible(1, 2, 1, 0, DFV_MAT_IDEAL, per, 0, moving);
     }
     std::vector<dfv::GasInst> ginst;
-    std::vector<CUtensorMap> gmaps;
     std::vector<int2> gitems0, gitems1;
     if (gas) {
         ginst.resize(count);
-        gmaps.resize((size_t)dfv::GasT::NMAP * count);
-        const void *bases[3] = {b->U, b->U1, b->U3};
-        for (int i = 0; i < count && gas; i++) {
+        for (int i = 0; i < count; i++) {
             const GridP &p = b->hinst[i].g;
             dfv::GasInst &G = ginst[i];
             memset(&G, 0, sizeof(G));
             G.n0 = p.n[0];
             G.n1 = p.n[1];
-            G.tiles_x = (p.n[0] + dfv::GasT::TX - 1) / dfv::GasT::TX;
-            G.ntiles = G.tiles_x * ((p.n[1] + dfv::GasT::TY - 1) / dfv::GasT::TY);
+            G.rows = P.gas_rows;
+            G.tiles_x = dfv::gasw_strips(p.n[0]);
+            G.ntiles = G.tiles_x * ((p.n[1] + G.rows - 1) / G.rows);
             G.off = b->hinst[i].off;
             G.pitch = p.pitch;
             G.dx = (float)p.dx[0];
@@ -458,9 +460,8 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
             G.wall_y0 = p.wall[1][0];
             G.wall_y1 = p.wall[1][1];
             G.ctl = b->d_ctl + i;
-            gas = dfv::gas_encode_maps(&gmaps[(size_t)dfv::GasT::NMAP * i], bases, G.off, G.n0, G.n1, G.pitch);
         }
-        if (gas) {
+        {
             for (int i = 0; i < count; i++)
                 for (int t = 0; t < ginst[i].ntiles; t++) gitems0.push_back(make_int2(i, t));
             std::vector<int> gord(count);
@@ -484,13 +485,8 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_vbody, vb.data(), sizeof(double) * vb.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && gas) {
-        e = dfv::gas_prepare();
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_ginst, ginst.data(), sizeof(dfv::GasInst) * count, cudaMemcpyHostToDevice,
-                                b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_tmaps, gmaps.data(), sizeof(CUtensorMap) * gmaps.size(), cudaMemcpyHostToDevice,
-                                b->stream);
+        e = cudaMemcpyAsync(b->d_ginst, ginst.data(), sizeof(dfv::GasInst) * count, cudaMemcpyHostToDevice,
+                            b->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->d_gitems[0], gitems0.data(), sizeof(int2) * gitems0.size(),
                                 cudaMemcpyHostToDevice, b->stream);
@@ -499,7 +495,7 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
                                 cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) {
             b->gas = true;
-            b->gas_max_ctas = dfv::gas_max_ctas_per_sm();
+            b->gas_max_ctas = dfv::gasw_max_ctas_per_sm();
         }
     }
     if (e == cudaSuccess) {

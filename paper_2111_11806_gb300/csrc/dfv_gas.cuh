@@ -39,7 +39,8 @@ struct GasInst {
     float dx, dy;
     int wall_x0, wall_x1, wall_y0, wall_y1;   // reflective sides
     Ctl *ctl;
-    long long pad;
+    int rows;            // rows per chunk (the warp-marching kernel, dfv_gasw.cuh)
+    int pad;
 };
 
 struct GasArgs {
@@ -156,8 +157,10 @@ __device__ __forceinline__ float gas_vanleer(float a, float b)
     return ab <= 0.f ? 0.f : __fdividef(2.f * ab, a + b);
 }
 
-// Conserved (rho, rho u, rho v, rho E) -> primitive (rho, u, v, p) of the gas.
-__device__ __forceinline__ void gas_prim(const GasArgs &a, float r, float mu, float mv, float E, float w[4])
+// Conserved (rho, rho u, rho v, rho E) -> primitive (rho, u, v, p) of the gas
+// (a: any argument block with the gas constants Gam, invGam, pref0).
+template <class A>
+__device__ __forceinline__ void gas_prim(const A &a, float r, float mu, float mv, float E, float w[4])
 {
     const float ir = __fdividef(1.f, r);
     const float u = mu * ir, v = mv * ir;
@@ -171,7 +174,8 @@ __device__ __forceinline__ void gas_prim(const GasArgs &a, float r, float mu, fl
 // HLLC flux of the gas across a face (Sec. 3.1: Toro's HLLC with Davis wave
 // speeds), normal velocity un, tangential ut; F = (rho, normal momentum,
 // tangential momentum, energy).
-__device__ __forceinline__ void gas_hllc(const GasArgs &a, float rL, float unL, float utL, float pL, float rR,
+template <class A>
+__device__ __forceinline__ void gas_hllc(const A &a, float rL, float unL, float utL, float pL, float rR,
                                          float unR, float utR, float pR, float F[4])
 {
     const float irL = __fdividef(1.f, rL), irR = __fdividef(1.f, rR);
@@ -533,14 +537,13 @@ bool gas_encode_maps(CUtensorMap maps[GasT::NMAP], const void *const bases[3], l
                      long long pitch);
 
 // Whether a 2-D grid can take the gas stage kernel: FP32, one ideal or
-// stiffened gas, no solid, no periodic side, no HLLC-LM, a static body
-// (the upwind r flux vanishes) and rows whose byte length is a multiple of 16
-// (the tensor map's row stride).
+// stiffened gas, no solid, no periodic side, no HLLC-LM and a static body
+// (the upwind r flux vanishes).
 inline bool gas_eligible(int precision_fp32, int dim, int nmat, int solid, int mat_kind, const int periodic[3],
-                         int hllc_lm, bool moving_body, int n0)
+                         int hllc_lm, bool moving_body)
 {
     return precision_fp32 && dim == 2 && nmat == 1 && solid == 0 && (mat_kind == 0 || mat_kind == 1) &&
-           !periodic[0] && !periodic[1] && !hllc_lm && !moving_body && n0 % 4 == 0;
+           !periodic[0] && !periodic[1] && !hllc_lm && !moving_body;
 }
 
 }  // namespace dfv

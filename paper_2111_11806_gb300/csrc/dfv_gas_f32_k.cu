@@ -6,6 +6,7 @@
 
 #include "dfv_gas.cuh"
 #include "dfv_gas3.cuh"
+#include "dfv_gasw.cuh"
 
 namespace dfv {
 
@@ -78,6 +79,34 @@ bool gas_encode_maps(CUtensorMap maps[GasT::NMAP], const void *const bases[3], l
         if (r != CUDA_SUCCESS) return false;
     }
     return true;
+}
+
+int gasw_max_ctas_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gasw_stage<3>, GaswT::THREADS, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    return n < 1 ? 1 : n;
+}
+
+cudaError_t gasw_stage(int stage, const GaswArgs &a, int grid, cudaStream_t st)
+{
+    const dim3 g(grid < 1 ? 1 : grid), b(GaswT::THREADS);
+    if (stage == 1) return launch_pdl(k_gasw_stage<1>, g, b, 0, st, a);
+    if (stage == 2) return launch_pdl(k_gasw_stage<2>, g, b, 0, st, a);
+    return launch_pdl(k_gasw_stage<3>, g, b, 0, st, a);
+}
+
+int gasw_rows(long long cells)
+{
+    // about 14,600 items of 28 columns (four per resident warp of 152 SMs at
+    // 24 warps) before the chunks grow past 8 rows
+    const long long target = 4LL * 152 * 24;
+    int rows = 8;
+    while (rows < 64 && cells / (28LL * rows * 2) >= target) rows *= 2;
+    return rows;
 }
 
 cudaError_t gas3_prepare()

@@ -1,9 +1,11 @@
-"""GPU parity of the stage kernels of single-gas FP32 grids (2-D: TMA-tiled; 3-D: marching)
-(dfv_gas.cuh): against the FP64 oracle (relative L1 per conserved plane
-<= 1e-4) on grids with ragged last tiles in x and y, a single tile, a grid
-smaller than one tile, reflective walls on every side, a stiffened gas, with
-and without a body; and against the general stage kernel on the same input
-(both FP32: they differ by rounding only)."""
+"""GPU parity of the stage kernels of single-gas FP32 grids (2-D: warp-marching
+strips, dfv_gasw.cuh; 3-D: marching columns, dfv_gas3.cuh): against the FP64
+oracle (relative L1 per conserved plane <= 1e-4) on grids with ragged last
+strips and chunks, odd widths, a single strip, grids narrower than the halo,
+reflective walls on every side, a stiffened gas, with and without a body;
+against the general stage kernel on the same input (both FP32: they differ by
+rounding only); and across chunk lengths (bit-identical: a cell's arithmetic
+does not depend on how the grid is cut into work items)."""
 import numpy as np
 import pytest
 
@@ -40,6 +42,10 @@ CASES = [
     ("water_64x40", lambda: water(W.random_state(2, (64, 40), 1, False, seed=207))),
     ("no_body_96x48", lambda: W.random_state(2, (96, 48), 1, False, seed=208, body=False)),
     ("cylinder_192", lambda: W.cylinder_2d(192)),
+    ("odd_37x29", lambda: W.random_state(2, (37, 29), 1, False, seed=211)),
+    ("walls_odd_45x31", lambda: walled(W.random_state(2, (45, 31), 1, False, seed=212), (1, 1, 1, 1))),
+    ("one_row_57x1", lambda: W.random_state(2, (57, 1), 1, False, seed=213, body=False)),
+    ("narrow_3x40_walls", lambda: walled(W.random_state(2, (3, 40), 1, False, seed=214, body=False), (1, 1, 0, 0))),
 ]
 
 
@@ -62,6 +68,39 @@ def test_gas_kernel_matches_general_kernel(name, make):
     assert t1 == pytest.approx(t2, rel=1e-5)
     err = rel_l1(g1.cons(), g2.cons(), wl)
     assert np.all(err <= 1e-5), err
+
+
+@pytest.mark.parametrize("name,make", [CASES[0], CASES[4], CASES[8], CASES[10]],
+                         ids=[CASES[i][0] for i in (0, 4, 8, 10)])
+def test_gas_kernel_chunk_lengths_are_bit_identical(name, make):
+    """Work items of 1, 3, 8, 64 and 4096 rows: the same bits."""
+    wl = make()
+    ref = B.Grid.from_workload(wl, precision=B.DFV_FP32, gas_rows=8)
+    t_ref = ref.run(6, 0.8)
+    for rows in (1, 3, 64, 4096):
+        g = B.Grid.from_workload(wl, precision=B.DFV_FP32, gas_rows=rows)
+        assert g.run(6, 0.8) == t_ref
+        np.testing.assert_array_equal(g.cons(), ref.cons())
+
+
+def test_gas_kernel_batch_with_long_chunks_matches_single_grids():
+    """A batch whose work items are 64 rows long (the length the 256-instance
+    batch takes) against single grids with 8-row items: the same bits."""
+    wls = [W.ellipse_instance(i, n=n) for i, n in enumerate((150, 97, 64, 130))]
+    b = B.Batch(wls, precision=B.DFV_FP32, gas_rows=64)
+    b.set_all_fields()
+    b.run(5, 0.8)
+    for i, wl in enumerate(wls):
+        g = B.Grid.from_workload(wl, precision=B.DFV_FP32, gas_rows=8)
+        g.run(5, 0.8)
+        np.testing.assert_array_equal(b.get_fields(i), g.cons())
+
+
+def test_gas_rows_out_of_range_is_rejected():
+    wl = W.cylinder_2d(64)
+    for rows in (-1, 4097):
+        with pytest.raises(B.DfvError):
+            B.Grid.from_workload(wl, precision=B.DFV_FP32, gas_rows=rows)
 
 
 def test_gas_kernel_device_dt_run():
