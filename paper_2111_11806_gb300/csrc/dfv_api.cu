@@ -59,7 +59,7 @@ struct dfv_grid {
     bool body_moving = false;
     dfv::GasInst *d_ginst = nullptr;
     int gas_grid = 1;
-    long long gas_tiles = 0;
+    long long gas_items = 0;
 };
 
 namespace {
@@ -301,7 +301,7 @@ dfv_status launch_stage(dfv_grid *g, int s, const void *in, const void *un, void
         dfv::GaswArgs a;
         a.inst = g->d_ginst;
         a.items = nullptr;
-        a.nitems = g->gas_tiles;
+        a.nitems = g->gas_items;
         a.queue = nullptr;
         a.in = (const float *)in;
         a.un = (const float *)un;
@@ -471,12 +471,10 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
         I.n0 = p.n[0];
         I.n1 = p.n[1];
         I.rows = opt->gas_rows > 0 ? opt->gas_rows : dfv::gasw_rows((long long)p.n[0] * p.n[1]);
-        I.tiles_x = dfv::gasw_strips(p.n[0]);
-        I.ntiles = I.tiles_x * ((p.n[1] + I.rows - 1) / I.rows);
+        I.strips = dfv::gasw_strips(p.n[0]);
+        I.nitems = I.strips * ((p.n[1] + I.rows - 1) / I.rows);
         I.off = 0;
         I.pitch = p.pitch;
-        I.dx = (float)p.dx[0];
-        I.dy = (float)p.dx[1];
         I.idx = (float)p.inv_dx[0];
         I.idy = (float)p.inv_dx[1];
         I.wall_x0 = p.wall[0][0];
@@ -493,10 +491,10 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
             delete g;
             return DFV_ERR_CUDA;
         }
-        g->gas_tiles = I.ntiles;
+        g->gas_items = I.nitems;
         // CTAs of independent warps: a persistent grid, or one warp per item when there are fewer
         const long long persistent = (long long)sms * dfv::gasw_max_ctas_per_sm();
-        const long long ctas = (g->gas_tiles + dfv::GaswT::WARPS - 1) / dfv::GaswT::WARPS;
+        const long long ctas = (g->gas_items + dfv::GaswT::WARPS - 1) / dfv::GaswT::WARPS;
         g->gas_grid = (int)std::max(1LL, std::min(persistent, ctas));
         g->gas_ready = true;
     }

@@ -447,12 +447,10 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
             G.n0 = p.n[0];
             G.n1 = p.n[1];
             G.rows = P.gas_rows;
-            G.tiles_x = dfv::gasw_strips(p.n[0]);
-            G.ntiles = G.tiles_x * ((p.n[1] + G.rows - 1) / G.rows);
+            G.strips = dfv::gasw_strips(p.n[0]);
+            G.nitems = G.strips * ((p.n[1] + G.rows - 1) / G.rows);
             G.off = b->hinst[i].off;
             G.pitch = p.pitch;
-            G.dx = (float)p.dx[0];
-            G.dy = (float)p.dx[1];
             G.idx = (float)p.inv_dx[0];
             G.idy = (float)p.inv_dx[1];
             G.wall_x0 = p.wall[0][0];
@@ -463,13 +461,13 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
         }
         {
             for (int i = 0; i < count; i++)
-                for (int t = 0; t < ginst[i].ntiles; t++) gitems0.push_back(make_int2(i, t));
+                for (int t = 0; t < ginst[i].nitems; t++) gitems0.push_back(make_int2(i, t));
             std::vector<int> gord(count);
             std::iota(gord.begin(), gord.end(), 0);
             std::stable_sort(gord.begin(), gord.end(),
-                             [&](int x, int y) { return ginst[x].ntiles > ginst[y].ntiles; });
+                             [&](int x, int y) { return ginst[x].nitems > ginst[y].nitems; });
             for (int i : gord)
-                for (int t = 0; t < ginst[i].ntiles; t++) gitems1.push_back(make_int2(i, t));
+                for (int t = 0; t < ginst[i].nitems; t++) gitems1.push_back(make_int2(i, t));
         }
     }
     cudaError_t e = b->kern.prepare();

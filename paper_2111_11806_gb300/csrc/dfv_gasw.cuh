@@ -40,7 +40,7 @@ struct GaswT {
 };
 
 struct GaswArgs {
-    const GasInst *inst;   // per instance: tiles_x = strips, ntiles = strips x chunks, rows per chunk
+    const GasInst *inst;   // per instance: strips, items (strips x chunks), rows per chunk
     const int2 *items;     // (instance, strip + strips * chunk); nullptr: instance 0, item = index
     long long nitems;
     unsigned int *queue;   // dynamic schedule counter (nullptr: static round-robin over the warps)
@@ -158,7 +158,7 @@ __device__ __forceinline__ void gasw_item(const GaswArgs &a, const GasInst &I, i
 {
     using T = GaswT;
     const int n0 = I.n0, n1 = I.n1, rows = I.rows;
-    const int strip = tile % I.tiles_x, chunk = tile / I.tiles_x;
+    const int strip = tile % I.strips, chunk = tile / I.strips;
     const int y0 = chunk * rows, yend = min(y0 + rows, n1);
     const int gx = strip * T::OWN - T::H + lane;
     const int wy0 = I.wall_y0, wy1 = I.wall_y1;
