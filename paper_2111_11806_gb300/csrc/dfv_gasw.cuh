@@ -84,23 +84,36 @@ __device__ __forceinline__ float4 gasw_prim(const A &a, const float c[4], bool f
     return make_float4(w[0], fx ? -w[1] : w[1], fy ? -w[2] : w[2], w[3]);
 }
 
-// van Leer face values of cell c between neighbours m and p along one
-// direction: lo at its face towards m, hi at its face towards p
-__device__ __forceinline__ void gasw_faces(const float4 &m, const float4 &c, const float4 &p, float4 &lo, float4 &hi)
+// van Leer face values of cell c from its backward and forward differences
+// db = c - m, df = p - c along one direction: lo at its face towards m, hi
+// at its face towards p
+__device__ __forceinline__ void gasw_faces_d(const float4 &c, const float4 &db, const float4 &df, float4 &lo,
+                                             float4 &hi)
 {
     float s;
-    s = gas_vanleer(c.x - m.x, p.x - c.x);
-    lo.x = c.x - 0.5f * s;
-    hi.x = c.x + 0.5f * s;
-    s = gas_vanleer(c.y - m.y, p.y - c.y);
-    lo.y = c.y - 0.5f * s;
-    hi.y = c.y + 0.5f * s;
-    s = gas_vanleer(c.z - m.z, p.z - c.z);
-    lo.z = c.z - 0.5f * s;
-    hi.z = c.z + 0.5f * s;
-    s = gas_vanleer(c.w - m.w, p.w - c.w);
-    lo.w = c.w - 0.5f * s;
-    hi.w = c.w + 0.5f * s;
+    s = gas_vanleer(db.x, df.x);
+    lo.x = fmaf(-0.5f, s, c.x);
+    hi.x = fmaf(0.5f, s, c.x);
+    s = gas_vanleer(db.y, df.y);
+    lo.y = fmaf(-0.5f, s, c.y);
+    hi.y = fmaf(0.5f, s, c.y);
+    s = gas_vanleer(db.z, df.z);
+    lo.z = fmaf(-0.5f, s, c.z);
+    hi.z = fmaf(0.5f, s, c.z);
+    s = gas_vanleer(db.w, df.w);
+    lo.w = fmaf(-0.5f, s, c.w);
+    hi.w = fmaf(0.5f, s, c.w);
+}
+
+__device__ __forceinline__ float4 gasw_sub(const float4 &p, const float4 &q)
+{
+    return make_float4(p.x - q.x, p.y - q.y, p.z - q.z, p.w - q.w);
+}
+
+// the same from the neighbours m and p
+__device__ __forceinline__ void gasw_faces(const float4 &m, const float4 &c, const float4 &p, float4 &lo, float4 &hi)
+{
+    gasw_faces_d(c, gasw_sub(c, m), gasw_sub(p, c), lo, hi);
 }
 
 // HLLC flux (rho, rho u, rho v, rho E) of an x face and of a y face
@@ -136,8 +149,8 @@ template <int STAGE>
 __device__ __forceinline__ float gasw_update(float unv, float inv, float fxl, float fxr, float fyl, float fyr,
                                              float idx, float idy, float dt, float ca, float cb, bool masked)
 {
-    const float div = (fxr - fxl) * idx;
-    const float dvy = (fyr - fyl) * idy;
+    const float div = __fmul_rn(fxr - fxl, idx);
+    const float dvy = __fmul_rn(fyr - fyl, idy);
     Acc<float> D;
     D.set(div);
     D.add(dvy);
@@ -224,8 +237,10 @@ __device__ __forceinline__ void gasw_item(const GaswArgs &a, const GasInst &I, i
         gasw_faces(P0, P1, P2, qB1, qT1);
         const float4 FyT = gasw_flux_y(a, qT, qB1);
         // x faces of row j
+        // (forward difference to the next lane; the backward one is the previous lane's forward one)
         float4 qL, qR;
-        gasw_faces(gasw_shfl_up(P0), P0, gasw_shfl_down(P0), qL, qR);
+        const float4 dF = gasw_sub(gasw_shfl_down(P0), P0);
+        gasw_faces_d(P0, gasw_shfl_up(dF), dF, qL, qR);
         const float4 FxL = gasw_flux_x(a, gasw_shfl_up(qR), qL);   // face i - 1/2
         const float4 FxR = gasw_shfl_down(FxL);                     // face i + 1/2
 
@@ -256,10 +271,10 @@ __device__ __forceinline__ void gasw_item(const GaswArgs &a, const GasInst &I, i
                 }
                 float wv[4];
                 gas_prim(a, o[0], o[1], o[2], o[3], wv);
-                const float c2 = __fdividef(a.Gam * wv[3] + (wv[3] - a.pref0), wv[0]);
+                const float c2 = __fmul_rn(fmaf(a.Gam, wv[3], wv[3] - a.pref0), gas_rcp(wv[0]));
                 if (!(c2 > 0.f)) atomicOr(&ctl->err, (unsigned)ERR_SOUND);
                 const float cs = sqrtf(c2);
-                smax = fmaxf(smax, (fabsf(wv[1]) + cs) * idx + (fabsf(wv[2]) + cs) * idy);
+                smax = fmaxf(smax, fmaf(fabsf(wv[1]) + cs, idx, __fmul_rn(fabsf(wv[2]) + cs, idy)));
             }
         }
         P0 = P1;
