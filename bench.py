@@ -424,7 +424,7 @@ def run_headline(torch, B, W, stream, args, clocks_on):
     if traffic:
         tr_step = traffic["dram_bytes_per_cell_step"] * cells
     rl = roofline(bpc * cells, ms / args.steps, peak, peak_kind,
-                  "one graph-replayed step: k_batch_seed + 3 x k_batch_stage + k_batch_finalize",
+                  "one graph-replayed step: k_batch_seed + 3 x k_gasw_stage + k_batch_finalize",
                   {"bytes_per_cell_step": bpc, "traffic": tr_step,
                    "stage_share_of_step": (phases["stage1"] + phases["stage2"] + phases["stage3"]) / tot,
                    "timing": "CUDA events around the timed region of %d graph-replayed steps" % args.steps})
