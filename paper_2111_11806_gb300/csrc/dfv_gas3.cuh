@@ -54,6 +54,11 @@ struct Gas3Smem {
     float fxe[Gas3T::TY][Gas3T::FXS];                    //  and rho E
     float4 fya[Gas3T::FYS][Gas3T::TX];
     float fye[Gas3T::FYS][Gas3T::TX];
+    // per thread: the conserved values of its cells of the next plane
+    // (asynchronous copies, read back by the same thread only) and, per
+    // column, the carried top z-face value and bottom z-face flux
+    float stage[Gas3T::K][5][Gas3T::THREADS];
+    float zcarry[10][Gas3T::CELLS];
     double red[32];
 };
 
@@ -115,12 +120,19 @@ __device__ __forceinline__ void gas_hllc3(const Gas3Args &a, const float L[5], c
     F[4] = FE;
 }
 
-// The conserved values of one plane (with its x, y halo) fetched into the
-// registers of the CTA's threads, mirror flags of each cell (3 bits).
+// A plane (with its x, y halo) in flight: its conserved values are copied
+// asynchronously into the threads' stage slots; the mirror flags of each of a
+// thread's cells (3 bits each) stay in a register.
 struct Gas3Plane {
-    float q[Gas3T::K][5];
     unsigned flip;
 };
+
+__device__ __forceinline__ void gas3_cp4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
 
 __device__ __forceinline__ int gas3_map(int i, int n, int wlo, int whi, bool *flip)
 {
@@ -158,7 +170,8 @@ __device__ __forceinline__ void gas3_cell(int q, int &lx, int &ly)
     }
 }
 
-__device__ __forceinline__ void gas3_fetch(const Gas3Args &a, Gas3Plane &f, int ox, int oy, int z, bool interior)
+__device__ __forceinline__ void gas3_fetch(const Gas3Args &a, Gas3Smem &S, Gas3Plane &f, int ox, int oy, int z,
+                                           bool interior)
 {
     using T = Gas3T;
     bool fz = false;
@@ -179,8 +192,9 @@ __device__ __forceinline__ void gas3_fetch(const Gas3Args &a, Gas3Plane &f, int 
         f.flip |= ((fx ? 1u : 0u) | (fy ? 2u : 0u) | (fz ? 4u : 0u)) << (3 * k);
         const long long c = gx + (long long)a.n0 * (gy + (long long)a.n1 * gz);
 #pragma unroll
-        for (int v = 0; v < 5; v++) f.q[k][v] = a.in[c + v * a.pitch];
+        for (int v = 0; v < 5; v++) gas3_cp4(&S.stage[k][v][threadIdx.x], a.in + c + v * a.pitch);
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 __device__ __forceinline__ void gas3_prim(const Gas3Args &a, const float q[5], unsigned flip, float w[5])
@@ -198,14 +212,17 @@ __device__ __forceinline__ void gas3_prim(const Gas3Args &a, const float q[5], u
 __device__ __forceinline__ void gas3_commit(const Gas3Args &a, const Gas3Plane &f, Gas3Smem &S, int slot)
 {
     using T = Gas3T;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // this thread's copies have landed
 #pragma unroll
     for (int k = 0; k < T::K; k++) {
         const int q = threadIdx.x + k * T::THREADS;
         if (q >= T::NCONV) continue;
         int lx, ly;
         gas3_cell(q, lx, ly);
-        float w[5];
-        gas3_prim(a, f.q[k], (f.flip >> (3 * k)) & 7u, w);
+        float c5[5], w[5];
+#pragma unroll
+        for (int v = 0; v < 5; v++) c5[v] = S.stage[k][v][threadIdx.x];
+        gas3_prim(a, c5, (f.flip >> (3 * k)) & 7u, w);
         S.pa[slot][ly + T::H][lx + T::H] = make_float4(w[0], w[1], w[2], w[3]);
         S.pp[slot][ly + T::H][lx + T::H] = w[4];
     }
@@ -268,7 +285,7 @@ __device__ __forceinline__ void gas3_unorient(const float F[5], int d, float o[5
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(Gas3T::THREADS, 2) k_gas3_stage(Gas3Args a)
+__global__ void __launch_bounds__(Gas3T::THREADS, 3) k_gas3_stage(Gas3Args a)
 {
     pdl_enter();
     using T = Gas3T;
@@ -292,12 +309,11 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 2) k_gas3_stage(Gas3Args a)
     // (committed by the first plane's step 1);
     // the column's planes z0-2, z0-1 for its first z slopes
     Gas3Plane fp;
-    gas3_fetch(a, fp, ox, oy, z0, interior);
+    gas3_fetch(a, S, fp, ox, oy, z0, interior);
     gas3_commit(a, fp, S, z0 % T::RING);
-    gas3_fetch(a, fp, ox, oy, z0 + 1, interior);
+    gas3_fetch(a, S, fp, ox, oy, z0 + 1, interior);
     gas3_commit(a, fp, S, (z0 + 1) % T::RING);
-    gas3_fetch(a, fp, ox, oy, z0 + 2, interior);
-    float qLz[5], Fzlo[5];
+    gas3_fetch(a, S, fp, ox, oy, z0 + 2, interior);
     __syncthreads();
     if (own) {
         float wm2[5], wm1[5], w0[5], w1[5], lo[5], hi[5], hiM[5], A[5], B[5], F[5];
@@ -310,9 +326,13 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 2) k_gas3_stage(Gas3Args a)
         gas3_orient(hiM, 2, A);
         gas3_orient(lo, 2, B);
         gas_hllc3(a, A, B, F);
+        float Fzlo[5];
         gas3_unorient(F, 2, Fzlo);           // the bottom z face of plane z0
 #pragma unroll
-        for (int v = 0; v < 5; v++) qLz[v] = hi[v];
+        for (int v = 0; v < 5; v++) {
+            S.zcarry[v][tid] = hi[v];
+            S.zcarry[5 + v][tid] = Fzlo[v];
+        }
     }
 
     float smax_cell = 0.f;
@@ -323,16 +343,7 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 2) k_gas3_stage(Gas3Args a)
         // readers are behind the previous plane's barriers); plane z+3 and
         // the cell's own stage input and step-start values fetched
         gas3_commit(a, fp, S, s2);
-        if (z + 3 <= z1 + 1) gas3_fetch(a, fp, ox, oy, z + 3, interior);
-        const long long c = gx + (long long)a.n0 * (gy + (long long)a.n1 * z);
-        float cin[6], cun[6];
-        if (col) {
-#pragma unroll
-            for (int v = 0; v < 6; v++) {
-                cin[v] = a.in[c + v * a.pitch];
-                cun[v] = a.un[c + v * a.pitch];
-            }
-        }
+        if (z + 3 <= z1 + 1) gas3_fetch(a, S, fp, ox, oy, z + 3, interior);
         __syncthreads();
 
         // 2. slopes: x and y of plane z (face values to shared memory), z of plane z+1
@@ -410,7 +421,7 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 2) k_gas3_stage(Gas3Args a)
                 gas3_unorient(F, 1, Fyl);
             }
 #pragma unroll
-            for (int v = 0; v < 5; v++) Lw[v] = qLz[v];
+            for (int v = 0; v < 5; v++) Lw[v] = S.zcarry[v][tid];
             gas3_orient(Lw, 2, A);
             gas3_orient(qRz1, 2, B);
             gas_hllc3(a, A, B, F);
@@ -445,8 +456,16 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 2) k_gas3_stage(Gas3Args a)
         }
         __syncthreads();
 
-        // 4. update of plane z
+        // 4. update of plane z: the cell's stage input and step-start values
+        // (loaded here, not held through the faces: three CTAs fit an SM)
+        const long long c = gx + (long long)a.n0 * (gy + (long long)a.n1 * z);
         if (col) {
+            float cin[6], cun[6];
+#pragma unroll
+            for (int v = 0; v < 6; v++) {
+                cin[v] = a.in[c + v * a.pitch];
+                cun[v] = a.un[c + v * a.pitch];
+            }
             const float4 e4 = S.fxa[cj][ci + 1], n4 = S.fya[cj + 1][ci];
             const float Fxr[5] = {e4.x, e4.y, e4.z, e4.w, S.fxe[cj][ci + 1]};
             const float Fyr[5] = {n4.x, n4.y, n4.z, n4.w, S.fye[cj + 1][ci]};
@@ -457,7 +476,7 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 2) k_gas3_stage(Gas3Args a)
                 Acc<float> D;
                 D.set((Fxr[v] - Fxl[v]) * a.idx);
                 D.add((Fyr[v] - Fyl[v]) * a.idy);
-                D.add((Fzhi[v] - Fzlo[v]) * a.idz);
+                D.add((Fzhi[v] - S.zcarry[5 + v][tid]) * a.idz);
                 o[v] = masked ? cun[v] : rk_combine<float>(STAGE, cun[v], cin[v], D, dt, ca, cb);
             }
             {
@@ -488,8 +507,8 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 2) k_gas3_stage(Gas3Args a)
         if (own) {
 #pragma unroll
             for (int v = 0; v < 5; v++) {
-                Fzlo[v] = Fzhi[v];
-                qLz[v] = qLz1[v];
+                S.zcarry[v][tid] = qLz1[v];
+                S.zcarry[5 + v][tid] = Fzhi[v];
             }
         }
     }
