@@ -135,7 +135,7 @@ typedef struct {
                             rounding. */
     int gas_rows;        /* rows per work item of the gas kernel (a strip of 28
                             columns marches through that many rows): 0 chooses
-                            from the total cell count (8 to 32), else 1 to 4096;
+                            from the total cell count (4 to 32), else 1 to 4096;
                             results do not depend on it */
 } dfv_options;
 

@@ -26,11 +26,13 @@ cudaError_t gasw_stage(int stage, const GaswArgs &a, int grid, cudaStream_t st)
 
 int gasw_rows(long long cells)
 {
-    // chunks grow from 8 to at most 32 rows while at least four items remain
-    // per resident warp (152 SMs x 20 warps); 64-row chunks measured 2 %
-    // slower on the 256-ellipse batch
+    // measured on the cylinders and the 256-ellipse batch: 4-row chunks
+    // below 2^19 cells (512^2: 5.7e9 against 5.2e9 cell-updates/s at 8
+    // rows), then 8, growing to at most 32 while at least four items remain
+    // per resident warp (152 SMs x 20 warps); 64-row chunks were 2 % slower
+    // than 32 on the batch
     const long long target = 4LL * 152 * GaswT::MIN_CTAS * GaswT::WARPS;
-    int rows = 8;
+    int rows = cells < (1LL << 19) ? 4 : 8;
     while (rows < 32 && cells / ((long long)GaswT::OWN * rows * 2) >= target) rows *= 2;
     return rows;
 }

@@ -36,7 +36,7 @@ struct GaswT {
     static constexpr int OWN = 32 - 2 * H;   // owned columns of a strip: lanes H .. 31 - H
     static constexpr int WARPS = 4;          // warps of a CTA (independent)
     static constexpr int THREADS = 32 * WARPS;
-    static constexpr int MIN_CTAS = 5;       // resident CTAs per SM the registers are sized for
+    static constexpr int MIN_CTAS = 5;       // resident CTAs per SM the registers are sized for (stages 2, 3)
 };
 
 struct GaswArgs {
@@ -309,7 +309,8 @@ __device__ __forceinline__ void gasw_item(const GaswArgs &a, const GasInst &I, i
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(GaswT::THREADS, GaswT::MIN_CTAS) k_gasw_stage(GaswArgs a)
+// stage 1 (no U^n stream of its own) fits in 80 registers: six CTAs per SM
+__global__ void __launch_bounds__(GaswT::THREADS, STAGE == 1 ? 6 : GaswT::MIN_CTAS) k_gasw_stage(GaswArgs a)
 {
     using T = GaswT;
     const int lane = threadIdx.x & 31;
