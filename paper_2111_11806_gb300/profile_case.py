@@ -57,9 +57,9 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     bt = B.Batch(wls, precision=prec, stream=stream)
     bt.set_all_fields()
-    # the schedule the autotuner picks for the 256-ellipse batch: largest
-    # instances first from a dynamic queue, as many CTAs per SM as fit
-    bt.set_schedule(16, 2)
+    # the schedule the autotuner picks for the 256-ellipse batch: one CTA
+    # per four work items, largest instances first
+    bt.set_schedule(0, 1)
     bt.run(1, 0.8)
     bt.profile(True)
     bt.run(args.steps, 0.8)
