@@ -88,3 +88,26 @@ def test_batch_autotune_restores_state():
     ref.run(5, 0.8)
     for i in range(len(wls)):
         np.testing.assert_array_equal(b.get_fields(i), ref.get_fields(i))
+
+
+def test_full_size_batch_sampled_instances_match_oracle():
+    """The benchmark's workload in the benchmark's launch configuration: the
+    256-instance FP32 batch, autotuned, one step.  The smallest, a middle and
+    the largest instance against the FP64 oracle stepped with that instance's
+    own time step (relative L1 per conserved plane <= 1e-4); every instance's
+    error word clear (dfv_batch_get_time raises otherwise)."""
+    from oracle import Oracle
+    wls = [W.ellipse_instance(i) for i in range(256)]
+    b = B.Batch(wls, precision=B.DFV_FP32)
+    b.set_all_fields()
+    b.autotune(trial_steps=2, cfl=0.8)          # restores the state it tuned on
+    b.run(1, 0.8)
+    order = np.argsort([wl.ncell for wl in wls], kind="stable")
+    for i in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        t, _ = b.time(i)
+        o = Oracle.from_workload(wls[i])
+        o.step(t)
+        err = rel_l1(b.get_fields(i), o.cons(), wls[i])
+        assert np.all(err <= 1e-4), (i, wls[i].n, err)
+    for i in range(len(wls)):
+        b.time(i)
