@@ -56,6 +56,8 @@ struct dfv_grid {
     // the material, the options and the body allow it (gas_on)
     bool gas_ready = false;
     bool gas3_ready = false;   // the 3-D gas kernel is prepared (FP32 3-D single-material fluid grid)
+    bool gas3_tma = false;     // ... with the tensor maps of its plane boxes over U, U1, U3
+    CUtensorMap gas3_map[3];
     bool body_moving = false;
     dfv::GasInst *d_ginst = nullptr;
     int gas_grid = 1;
@@ -294,7 +296,11 @@ dfv_status launch_stage(dfv_grid *g, int s, const void *in, const void *un, void
         a.Gam = g->g.mc_f[0].Gam;
         a.invGam = g->g.mc_f[0].invGam;
         a.pref0 = g->g.mc_f[0].pref0;
-        DFV_CU(g, dfv::gas3_stage(s, a, g->stream), "k_gas3_stage");
+        // the stage input's tensor map (the plane boxes by TMA), else per-thread copies
+        const CUtensorMap *map = nullptr;
+        if (g->gas3_tma)
+            map = in == g->U ? &g->gas3_map[0] : (in == g->U1 ? &g->gas3_map[1] : (in == g->U3 ? &g->gas3_map[2] : nullptr));
+        DFV_CU(g, dfv::gas3_stage(s, a, map, g->stream), "k_gas3_stage");
         return DFV_OK;
     }
     if (gas_on(g)) {
@@ -461,6 +467,10 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
             return DFV_ERR_CUDA;
         }
         g->gas3_ready = true;
+        const void *bases[3] = {g->U, g->U1, g->U3};
+        g->gas3_tma = true;
+        for (int k = 0; k < 3 && g->gas3_tma; k++)
+            g->gas3_tma = dfv::gas3_encode_map(&g->gas3_map[k], bases[k], p.n[0], p.n[1], p.n[2], p.pitch);
     }
     // the gas kernel's instance record: strips of 28 columns x chunks of rows
     g->d_ginst = (dfv::GasInst *)(g->ws + L.off_gas);

@@ -21,9 +21,48 @@
 // flux vanishes and r is not reconstructed (MUSCL only).
 #pragma once
 
+#include <cuda.h>
+
 #include "dfv_gas.cuh"
 
 namespace dfv {
+
+// ------------------------------------------------------------ TMA, mbarrier
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase of parity `parity` to complete; false when the
+// iteration limit ran out (the caller reports it and stops).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (int it = 0; it < (1 << 22); it++) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
 
 struct Gas3T {
     static constexpr int TX = 32, TY = 8, H = 2;
@@ -36,10 +75,21 @@ struct Gas3T {
     static constexpr int NP = 6;                             // rho, rho u, rho v, rho w, rho E, r
     static constexpr int FXS = TX + 1, FYS = TY + 1;
     static constexpr int ZCHUNK = 32;                        // planes per CTA
+    // the TMA box of a plane: x from ox-4 (a 16-byte boundary) to ox+35, y
+    // from oy-2 to oy+9, the five conserved planes rho .. rho E
+    static constexpr int BX = TX + 8, BY = PY, BV = 5;
+    static constexpr int BOXF = BX * BY * BV;
+    static constexpr int XFER = K * 5 * THREADS > BOXF ? K * 5 * THREADS : BOXF;   // floats of the fetch slot
 };
+static_assert((Gas3T::BOXF * 4) % 128 == 0, "the TMA box keeps 128-byte multiples");
 
 // primitives (rho, u, v, w) and p of one cell or face value
-struct Gas3Smem {
+struct __align__(128) Gas3Smem {
+    // the fetch slot of the next plane, first (a tensor copy's destination
+    // is 128-byte aligned): its TMA box [v][y][x], or per thread the conserved
+    // values of its cells (asynchronous copies read back by the same thread)
+    float xfer[Gas3T::XFER];
+    unsigned long long mbar;                             // completion of the slot's tensor copy
     float4 pa[Gas3T::RING][Gas3T::PY][Gas3T::PX + 1];   // odd row length: column reads conflict-free
     float pp[Gas3T::RING][Gas3T::PY][Gas3T::PX + 1];
     float4 fvxa[Gas3T::TY][Gas3T::FXS];                  // right-face values, column -1 .. TX-1
@@ -54,10 +104,7 @@ struct Gas3Smem {
     float fxe[Gas3T::TY][Gas3T::FXS];                    //  and rho E
     float4 fya[Gas3T::FYS][Gas3T::TX];
     float fye[Gas3T::FYS][Gas3T::TX];
-    // per thread: the conserved values of its cells of the next plane
-    // (asynchronous copies, read back by the same thread only) and, per
-    // column, the carried top z-face value and bottom z-face flux
-    float stage[Gas3T::K][5][Gas3T::THREADS];
+    // per column: the carried top z-face value and bottom z-face flux
     float zcarry[10][Gas3T::CELLS];
     double red[32];
 };
@@ -120,18 +167,30 @@ __device__ __forceinline__ void gas_hllc3(const Gas3Args &a, const float L[5], c
     F[4] = FE;
 }
 
-// A plane (with its x, y halo) in flight: its conserved values are copied
-// asynchronously into the threads' stage slots; the mirror flags of each of a
-// thread's cells (3 bits each) stay in a register.
+// A plane (with its x, y halo) in flight: its conserved values arrive in the
+// fetch slot, by one tensor copy (TMA) or by every thread's asynchronous
+// copies; the mirror flags of a thread's cells (3 bits each, cp.async path)
+// or of the plane (TMA path) and the copy's mbarrier phase stay in registers.
 struct Gas3Plane {
     unsigned flip;
+    int gz;           // plane read
+    unsigned phase;   // tensor copies issued so far (TMA path)
 };
 
 __device__ __forceinline__ void gas3_cp4(float *dst, const float *src)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// One 4-D tensor copy (x, y, plane z, variable) of a box into shared memory.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int v,
+                                            unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(v), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ int gas3_map(int i, int n, int wlo, int whi, bool *flip)
@@ -170,12 +229,26 @@ __device__ __forceinline__ void gas3_cell(int q, int &lx, int &ly)
     }
 }
 
-__device__ __forceinline__ void gas3_fetch(const Gas3Args &a, Gas3Smem &S, Gas3Plane &f, int ox, int oy, int z,
-                                           bool interior)
+// Start the fetch of plane z into the slot.  TMA: thread 0 issues one tensor
+// copy of the box (the slot's previous contents have been read: the caller
+// fetches after a barrier); otherwise every thread copies its own cells.
+template <bool TMA>
+__device__ __forceinline__ void gas3_fetch(const Gas3Args &a, const CUtensorMap *map, Gas3Smem &S, Gas3Plane &f,
+                                           int ox, int oy, int z, bool interior)
 {
     using T = Gas3T;
     bool fz = false;
     const int gz = gas3_map(z, a.n2, a.wall[2][0], a.wall[2][1], &fz);
+    if constexpr (TMA) {
+        f.flip = fz ? 4u : 0u;
+        f.gz = gz;
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&S.mbar, 4u * T::BOXF);
+            tma_load_4d(S.xfer, map, ox - 4, oy - T::H, gz, 0, &S.mbar);
+        }
+        return;
+    }
     f.flip = 0u;
 #pragma unroll
     for (int k = 0; k < T::K; k++) {
@@ -192,7 +265,7 @@ __device__ __forceinline__ void gas3_fetch(const Gas3Args &a, Gas3Smem &S, Gas3P
         f.flip |= ((fx ? 1u : 0u) | (fy ? 2u : 0u) | (fz ? 4u : 0u)) << (3 * k);
         const long long c = gx + (long long)a.n0 * (gy + (long long)a.n1 * gz);
 #pragma unroll
-        for (int v = 0; v < 5; v++) gas3_cp4(&S.stage[k][v][threadIdx.x], a.in + c + v * a.pitch);
+        for (int v = 0; v < 5; v++) gas3_cp4(&S.xfer[(k * 5 + v) * T::THREADS + threadIdx.x], a.in + c + v * a.pitch);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -209,10 +282,20 @@ __device__ __forceinline__ void gas3_prim(const Gas3Args &a, const float q[5], u
     w[4] = a.pref0 + a.Gam * (q[4] - ke);
 }
 
-__device__ __forceinline__ void gas3_commit(const Gas3Args &a, const Gas3Plane &f, Gas3Smem &S, int slot)
+// Convert the fetched plane into ring slot `slot`; false when a tensor copy
+// never completed (bounded wait).
+template <bool TMA>
+__device__ __forceinline__ bool gas3_commit(const Gas3Args &a, Gas3Plane &f, Gas3Smem &S, int slot, int ox, int oy,
+                                            bool interior)
 {
     using T = Gas3T;
-    asm volatile("cp.async.wait_group 0;" ::: "memory");   // this thread's copies have landed
+    if constexpr (TMA) {
+        const bool ok = mbar_wait(&S.mbar, f.phase & 1u);
+        f.phase++;
+        if (!ok) return false;
+    } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");   // this thread's copies have landed
+    }
 #pragma unroll
     for (int k = 0; k < T::K; k++) {
         const int q = threadIdx.x + k * T::THREADS;
@@ -220,12 +303,31 @@ __device__ __forceinline__ void gas3_commit(const Gas3Args &a, const Gas3Plane &
         int lx, ly;
         gas3_cell(q, lx, ly);
         float c5[5], w[5];
+        unsigned flip;
+        if constexpr (TMA) {
+            // the cell's place in the box: the halo beyond a side is the
+            // nearest cell or the mirror image (flip), clamped into the box
+            // (cells far outside a small grid feed only faces outside it)
+            bool fx = false, fy = false;
+            int gx = ox + lx, gy = oy + ly;
+            if (!interior) {
+                gx = gas3_map(gx, a.n0, a.wall[0][0], a.wall[0][1], &fx);
+                gy = gas3_map(gy, a.n1, a.wall[1][0], a.wall[1][1], &fy);
+            }
+            const int bx = min(max(gx - (ox - 4), 0), T::BX - 1), by = min(max(gy - (oy - T::H), 0), T::BY - 1);
 #pragma unroll
-        for (int v = 0; v < 5; v++) c5[v] = S.stage[k][v][threadIdx.x];
-        gas3_prim(a, c5, (f.flip >> (3 * k)) & 7u, w);
+            for (int v = 0; v < 5; v++) c5[v] = S.xfer[(v * T::BY + by) * T::BX + bx];
+            flip = (fx ? 1u : 0u) | (fy ? 2u : 0u) | f.flip;
+        } else {
+#pragma unroll
+            for (int v = 0; v < 5; v++) c5[v] = S.xfer[(k * 5 + v) * T::THREADS + threadIdx.x];
+            flip = (f.flip >> (3 * k)) & 7u;
+        }
+        gas3_prim(a, c5, flip, w);
         S.pa[slot][ly + T::H][lx + T::H] = make_float4(w[0], w[1], w[2], w[3]);
         S.pp[slot][ly + T::H][lx + T::H] = w[4];
     }
+    return true;
 }
 
 // primitives of the column's own cell in a ring slot
@@ -284,14 +386,40 @@ __device__ __forceinline__ void gas3_unorient(const float F[5], int d, float o[5
     o[4] = F[4];
 }
 
-template <int STAGE>
-__global__ void __launch_bounds__(Gas3T::THREADS, 3) k_gas3_stage(Gas3Args a)
+// A tensor copy that did not complete in the bounded wait: report it, and
+// give it one more bounded wait before the CTA's shared memory is released.
+__device__ __forceinline__ void gas3_fail(const Gas3Args &a, Gas3Smem &S, const Gas3Plane &f)
+{
+    if (threadIdx.x == 0) {
+        atomicOr(&a.ctl->err, (unsigned)ERR_TIMEOUT);
+        (void)mbar_wait(&S.mbar, (f.phase - 1u) & 1u);
+    }
+}
+
+// TMA: the plane boxes come by tensor copies through `map` (over the stage
+// input's first five planes); else by per-thread asynchronous copies.
+template <int STAGE, bool TMA>
+__global__ void __launch_bounds__(Gas3T::THREADS, 3) k_gas3_stage(Gas3Args a, const __grid_constant__ CUtensorMap map)
 {
     pdl_enter();
     using T = Gas3T;
-    extern __shared__ __align__(16) unsigned char gas3_smem_raw[];
+    // the dynamic shared memory is the kernel's only shared memory and starts
+    // the CTA's shared window; a tensor copy needs its slot 128-byte aligned
+    extern __shared__ __align__(128) unsigned char gas3_smem_raw[];
     Gas3Smem &S = *reinterpret_cast<Gas3Smem *>(gas3_smem_raw);
     const int tid = threadIdx.x;
+    if (TMA) {
+        if ((smem_u32(S.xfer) & 127u) != 0) {
+            // never issue a misaligned tensor copy: report and stop
+            if (tid == 0) atomicOr(&a.ctl->err, (unsigned)ERR_TIMEOUT);
+            return;
+        }
+        if (tid == 0) {
+            mbar_init(&S.mbar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
     const int ox = blockIdx.x * T::TX, oy = blockIdx.y * T::TY;
     const int z0 = blockIdx.z * a.zc, z1 = min(z0 + a.zc, a.n2);
     const bool interior = ox >= T::H && ox + T::TX + T::H <= a.n0 && oy >= T::H && oy + T::TY + T::H <= a.n1;
@@ -309,12 +437,18 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 3) k_gas3_stage(Gas3Args a)
     // (committed by the first plane's step 1);
     // the column's planes z0-2, z0-1 for its first z slopes
     Gas3Plane fp;
-    gas3_fetch(a, S, fp, ox, oy, z0, interior);
-    gas3_commit(a, fp, S, z0 % T::RING);
-    gas3_fetch(a, S, fp, ox, oy, z0 + 1, interior);
-    gas3_commit(a, fp, S, (z0 + 1) % T::RING);
-    gas3_fetch(a, S, fp, ox, oy, z0 + 2, interior);
-    __syncthreads();
+    fp.phase = 0u;
+    gas3_fetch<TMA>(a, &map, S, fp, ox, oy, z0, interior);
+    if (__syncthreads_or(!gas3_commit<TMA>(a, fp, S, z0 % T::RING, ox, oy, interior))) {
+        gas3_fail(a, S, fp);
+        return;
+    }
+    gas3_fetch<TMA>(a, &map, S, fp, ox, oy, z0 + 1, interior);
+    if (__syncthreads_or(!gas3_commit<TMA>(a, fp, S, (z0 + 1) % T::RING, ox, oy, interior))) {
+        gas3_fail(a, S, fp);
+        return;
+    }
+    gas3_fetch<TMA>(a, &map, S, fp, ox, oy, z0 + 2, interior);
     if (own) {
         float wm2[5], wm1[5], w0[5], w1[5], lo[5], hi[5], hiM[5], A[5], B[5], F[5];
         gas3_column(a, gx, gy, z0 - 2, wm2);
@@ -340,11 +474,13 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 3) k_gas3_stage(Gas3Args a)
     for (int z = z0; z < z1; z++) {
         const int sz = z % T::RING, s1 = (z + 1) % T::RING, s2 = (z + 2) % T::RING;
         // 1. plane z+2 into the ring (its slot held plane z-1, whose last
-        // readers are behind the previous plane's barriers); plane z+3 and
-        // the cell's own stage input and step-start values fetched
-        gas3_commit(a, fp, S, s2);
-        if (z + 3 <= z1 + 1) gas3_fetch(a, S, fp, ox, oy, z + 3, interior);
-        __syncthreads();
+        // readers are behind the previous plane's barriers); then, with the
+        // fetch slot read by every thread, plane z+3 fetched into it
+        if (__syncthreads_or(!gas3_commit<TMA>(a, fp, S, s2, ox, oy, interior))) {
+            gas3_fail(a, S, fp);
+            return;
+        }
+        if (z + 3 <= z1 + 1) gas3_fetch<TMA>(a, &map, S, fp, ox, oy, z + 3, interior);
 
         // 2. slopes: x and y of plane z (face values to shared memory), z of plane z+1
         float qRx[5], qRy[5], qRz1[5], qLz1[5];
@@ -546,6 +682,13 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 3) k_gas3_stage(Gas3Args a)
 
 // Host side (dfv_gas_f32_k.cu).
 cudaError_t gas3_prepare();
-cudaError_t gas3_stage(int stage, const Gas3Args &a, cudaStream_t st);
+// The tensor map of a stage input's first five planes (rho .. rho E) with the
+// plane box of the kernel: 4-D (x, y, z, variable) over n0 x n1 x n2 x 5
+// floats at base, row stride n0, plane stride n0 n1, variable stride pitch.
+// False when the grid does not allow it (rows or planes not a multiple of 16
+// bytes, a misaligned base); the kernel then copies per thread.
+bool gas3_encode_map(CUtensorMap *map, const void *base, int n0, int n1, int n2, long long pitch);
+// map: the stage input's tensor map, or nullptr for the per-thread copies.
+cudaError_t gas3_stage(int stage, const Gas3Args &a, const CUtensorMap *map, cudaStream_t st);
 
 }  // namespace dfv

@@ -24,7 +24,8 @@
 // and no shared memory or block barrier is involved: the warps of a CTA
 // share nothing.  Without a moving body the upwind r flux vanishes and r is
 // not reconstructed, so a halo of 2 suffices (MUSCL).  The arithmetic per
-// face and per cell is that of the tile kernel (dfv_gas.cuh).
+// face and per cell is that of the general stage kernel written for one gas
+// (dfv_gas.cuh).
 #pragma once
 
 #include "dfv_gas.cuh"
