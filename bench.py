@@ -104,6 +104,20 @@ def recorded_traffic(name):
     return d
 
 
+def whole_job_rate(local_ms, units_per_rank, world, device):
+    """Whole-job throughput of `world` replicas, one per rank: the units every
+    rank processed over the slowest rank's time (the maximum over ranks of
+    the local timed region, all-reduced when world > 1).  Returns (rate per
+    second, slowest ms)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return world * units_per_rank / (slowest * 1e-3), slowest
+
+
 def bytes_per_cell_step(nvar, w):
     """Algorithmic HBM bytes of one stage-by-stage SSP-RK3 step per cell:
     stage 1 reads U^n and writes U1, stages 2 and 3 read their input and U^n
@@ -478,7 +492,8 @@ def run_e2e(torch, B, wls, stream, job_steps):
     el = time.perf_counter() - t0
     nbytes = int(sum(h.numel() * 8 for h in host_in))
     del bt
-    return {"value": cells * job_steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes / job_steps,
+    return {"value": cells * job_steps / el, "ms": 1e3 * el, "units": cells * job_steps, "unit": UNIT,
+            "h2d_bytes_per_step": nbytes / job_steps,
             "d2h_bytes_per_step": nbytes / job_steps,
             "job": "set_fields(pinned host, %d instances) + %d steps + get_fields(pinned host), %.3f s" % (
                 len(wls), job_steps, el)}
@@ -548,18 +563,14 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     head, wls = run_headline(torch, B, W, stream, args, lambda: Clocks(local) if rank == 0 else None)
-    t = torch.tensor([head["ms"]], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * args.steps * head["cells"] / (total_ms * 1e-3)
+    value, total_ms = whole_job_rate(head["ms"], args.steps * head["cells"], world, dev)
 
     extra = {}
     if not args.no_extra:
         extra["batched_fp64"] = run_batch_fp64(torch, B, wls, stream, 10)
         extra["batched_fp64"]["fp32_over_fp64"] = value / world / extra["batched_fp64"]["value"]
         e2e = run_e2e(torch, B, wls, stream, 300)
-        e2e["value"] *= world
+        e2e["value"], _ = whole_job_rate(e2e.pop("ms"), e2e.pop("units"), world, dev)
         flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
         forms = [
             ("cylinder_2d", "cylinder_2d_512x512_mach3", ("cylinder", (512,)), 200, 20, flush),
