@@ -481,6 +481,16 @@ __global__ void __launch_bounds__(Gas3T::THREADS, 3) k_gas3_stage(Gas3Args a, co
             return;
         }
         if (z + 3 <= z1 + 1) gas3_fetch<TMA>(a, &map, S, fp, ox, oy, z + 3, interior);
+        if (col && z + 1 < z1) {
+            // the cell's stage input and U^n at the next plane into L1 (read
+            // at that plane's update; no register or shared slot holds them)
+            const long long cn = gx + (long long)a.n0 * (gy + (long long)a.n1 * (z + 1));
+#pragma unroll
+            for (int v = 0; v < 6; v++) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(a.in + cn + v * a.pitch));
+                if (STAGE > 1) asm volatile("prefetch.global.L1 [%0];" ::"l"(a.un + cn + v * a.pitch));
+            }
+        }
 
         // 2. slopes: x and y of plane z (face values to shared memory), z of plane z+1
         float qRx[5], qRy[5], qRz1[5], qLz1[5];
