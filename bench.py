@@ -483,11 +483,9 @@ def run_e2e(torch, B, wls, stream, job_steps):
     bt.autotune(trial_steps=2, cfl=0.8)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i, h in enumerate(host_in):
-        bt.set_fields(i, h.numpy())
+    bt.set_all_fields([h.numpy() for h in host_in])
     bt.run(job_steps, 0.8)
-    for i, h in enumerate(host_out):
-        bt.get_fields(i, B.DFV_FIELDS_PRIMITIVE, out=h.numpy())
+    bt.get_all_fields(B.DFV_FIELDS_PRIMITIVE, outs=[h.numpy() for h in host_out])
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     nbytes = int(sum(h.numel() * 8 for h in host_in))
@@ -495,7 +493,7 @@ def run_e2e(torch, B, wls, stream, job_steps):
     return {"value": cells * job_steps / el, "ms": 1e3 * el, "units": cells * job_steps, "unit": UNIT,
             "h2d_bytes_per_step": nbytes / job_steps,
             "d2h_bytes_per_step": nbytes / job_steps,
-            "job": "set_fields(pinned host, %d instances) + %d steps + get_fields(pinned host), %.3f s" % (
+            "job": "set_all_fields(pinned host, %d instances) + %d steps + get_all_fields(pinned host), %.3f s" % (
                 len(wls), job_steps, el)}
 
 

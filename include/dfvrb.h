@@ -271,6 +271,15 @@ dfv_status dfv_batch_add_material(dfv_batch *b, int kind, const dfv_material_par
 /* Initial primitive fields of instance i (FP64 planes, host or device). */
 dfv_status dfv_batch_set_fields(dfv_batch *b, int i, const double *prim, int on_device);
 dfv_status dfv_batch_get_fields(dfv_batch *b, int i, double *out, int which, int on_device);
+/* The same for every instance in one call (Sec. 4 setup of many independent
+ * problems): prim[i] / out[i] (count pointers, caller-owned, host or device
+ * as on_device says) hold instance i's nvar FP64 planes of n[0] n[1] values.
+ * The copies and conversions of all instances are issued back to back on the
+ * batch's stream and the call returns when they are done (host buffers may
+ * then be reused). DFV_ERR_ARG for a null pointer (nothing is copied) or,
+ * when reading, an instance whose fields were never set. */
+dfv_status dfv_batch_set_all_fields(dfv_batch *b, const double *const *prim, int on_device);
+dfv_status dfv_batch_get_all_fields(dfv_batch *b, double *const *out, int which, int on_device);
 /* `steps` steps of every instance, each with its own dt = cfl / (its CFL
  * bound), clipped to t_end when t_end > 0; no host synchronisation. */
 dfv_status dfv_batch_run(dfv_batch *b, int steps, double cfl, double t_end);

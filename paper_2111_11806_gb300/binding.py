@@ -29,7 +29,7 @@ EXPORTS = ("dfv_workspace_bytes", "dfv_create_grid", "dfv_add_material", "dfv_se
            "dfv_batch_workspace_bytes", "dfv_batch_create", "dfv_batch_add_material", "dfv_batch_set_fields",
            "dfv_batch_get_fields", "dfv_batch_run", "dfv_batch_autotune", "dfv_batch_set_schedule",
            "dfv_batch_get_time", "dfv_batch_profile", "dfv_batch_launch_count", "dfv_batch_destroy",
-           "dfv_batch_last_error")
+           "dfv_batch_last_error", "dfv_batch_set_all_fields", "dfv_batch_get_all_fields")
 
 
 class dfv_material_params(ctypes.Structure):
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
     L.dfv_batch_add_material.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(dfv_material_params)]
     L.dfv_batch_set_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int]
     L.dfv_batch_get_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int]
+    L.dfv_batch_set_all_fields.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int]
+    L.dfv_batch_get_all_fields.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int]
     L.dfv_batch_run.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
     L.dfv_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _ip]
     L.dfv_batch_set_schedule.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
@@ -444,9 +446,27 @@ class Batch:
             _bcheck(load().dfv_batch_set_fields(self._h, int(i), _vp(a.ctypes.data), 0), self._h,
                     "dfv_batch_set_fields")
 
-    def set_all_fields(self):
-        for i, wl in enumerate(self.wls):
-            self.set_fields(i, wl.prim)
+    def set_all_fields(self, prims=None):
+        """Every instance's primitive fields in one call (dfv_batch_set_all_fields);
+        prims: one FP64 array per instance (default: the workloads' own)."""
+        prims = [wl.prim for wl in self.wls] if prims is None else list(prims)
+        arrs = [np.ascontiguousarray(np.asarray(p, dtype=np.float64)) for p in prims]
+        assert len(arrs) == self.count
+        ptrs = (_vp * self.count)(*[_vp(a.ctypes.data) for a in arrs])
+        with self._ctx():
+            _bcheck(load().dfv_batch_set_all_fields(self._h, ptrs, 0), self._h, "dfv_batch_set_all_fields")
+
+    def get_all_fields(self, which=DFV_FIELDS_CONSERVED, outs=None):
+        """Every instance's fields in one call (dfv_batch_get_all_fields); outs:
+        one C-contiguous FP64 array of nvar x cells per instance (default: new)."""
+        outs = [np.zeros((self.nvar, c)) for c in self.cells] if outs is None else list(outs)
+        assert len(outs) == self.count
+        for a, c in zip(outs, self.cells):
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.nvar * c
+        ptrs = (_vp * self.count)(*[_vp(a.ctypes.data) for a in outs])
+        with self._ctx():
+            _bcheck(load().dfv_batch_get_all_fields(self._h, ptrs, which, 0), self._h, "dfv_batch_get_all_fields")
+        return outs
 
     def get_fields(self, i, which=DFV_FIELDS_CONSERVED, out=None):
         a = np.zeros((self.nvar, self.cells[i])) if out is None else out

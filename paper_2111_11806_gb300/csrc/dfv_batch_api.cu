@@ -529,13 +529,15 @@ dfv_status dfv_batch_add_material(dfv_batch *b, int kind, const dfv_material_par
     return DFV_OK;
 }
 
-dfv_status dfv_batch_set_fields(dfv_batch *b, int i, const double *prim, int on_device)
+}  // extern "C"
+
+namespace {
+
+// The copy and conversion of one instance's fields, issued on the batch's
+// stream (the staging buffer is reused in stream order: no synchronisation
+// between instances is needed).
+dfv_status set_one(dfv_batch *b, int i, const double *prim, int on_device)
 {
-    if (!b) return DFV_ERR_ARG;
-    if (i < 0 || i >= b->count || !prim) return bfail(b, DFV_ERR_ARG, "dfv_batch_set_fields: bad arguments");
-    if (b->nmat != b->nmat_opt) return bfail(b, DFV_ERR_ARG, "dfv_batch_set_fields: materials missing");
-    dfv_status s = upload(b);
-    if (s != DFV_OK) return s;
     const GridP &g = b->hinst[i].g;
     const int w = b->precision == DFV_FP32 ? 4 : 8;
     const size_t bytes = sizeof(double) * b->ops->nvar * (size_t)g.ncell;
@@ -547,17 +549,13 @@ dfv_status dfv_batch_set_fields(dfv_batch *b, int i, const double *prim, int on_
     b->launches++;
     // new r: the instance's rigid box is unknown until its next stage 3
     B_CU(b, cudaMemsetAsync(&b->d_ctl[i].rbox_valid, 0, sizeof(int), b->stream), "set_fields box");
-    if (!on_device) B_CU(b, cudaStreamSynchronize(b->stream), "set_fields sync");
     b->fields_set[i] = 1;
     b->dt_valid = false;
     return DFV_OK;
 }
 
-dfv_status dfv_batch_get_fields(dfv_batch *b, int i, double *outp, int which, int on_device)
+dfv_status get_one(dfv_batch *b, int i, double *outp, int which, int on_device)
 {
-    if (!b) return DFV_ERR_ARG;
-    if (i < 0 || i >= b->count || !outp || !b->fields_set[i])
-        return bfail(b, DFV_ERR_ARG, "dfv_batch_get_fields: bad arguments");
     const GridP &g = b->hinst[i].g;
     const int w = b->precision == DFV_FP32 ? 4 : 8;
     const void *Ui = (const char *)b->U + (size_t)w * b->hinst[i].off;
@@ -571,7 +569,65 @@ dfv_status dfv_batch_get_fields(dfv_batch *b, int i, double *outp, int which, in
     B_CU(b, cudaMemcpyAsync(outp, b->staging, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                             b->stream),
          "get_fields copy");
+    return DFV_OK;
+}
+
+dfv_status set_ready(dfv_batch *b)
+{
+    if (b->nmat != b->nmat_opt) return bfail(b, DFV_ERR_ARG, "dfv_batch_set_fields: materials missing");
+    return upload(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+dfv_status dfv_batch_set_fields(dfv_batch *b, int i, const double *prim, int on_device)
+{
+    if (!b) return DFV_ERR_ARG;
+    if (i < 0 || i >= b->count || !prim) return bfail(b, DFV_ERR_ARG, "dfv_batch_set_fields: bad arguments");
+    dfv_status s = set_ready(b);
+    if (s == DFV_OK) s = set_one(b, i, prim, on_device);
+    if (s != DFV_OK) return s;
+    if (!on_device) B_CU(b, cudaStreamSynchronize(b->stream), "set_fields sync");
+    return DFV_OK;
+}
+
+dfv_status dfv_batch_set_all_fields(dfv_batch *b, const double *const *prim, int on_device)
+{
+    if (!b) return DFV_ERR_ARG;
+    if (!prim) return bfail(b, DFV_ERR_ARG, "dfv_batch_set_all_fields: bad arguments");
+    for (int i = 0; i < b->count; i++)
+        if (!prim[i]) return bfail(b, DFV_ERR_ARG, "dfv_batch_set_all_fields: bad arguments");
+    dfv_status s = set_ready(b);
+    for (int i = 0; i < b->count && s == DFV_OK; i++) s = set_one(b, i, prim[i], on_device);
+    if (s != DFV_OK) return s;
+    if (!on_device) B_CU(b, cudaStreamSynchronize(b->stream), "set_all_fields sync");
+    return DFV_OK;
+}
+
+dfv_status dfv_batch_get_fields(dfv_batch *b, int i, double *outp, int which, int on_device)
+{
+    if (!b) return DFV_ERR_ARG;
+    if (i < 0 || i >= b->count || !outp || !b->fields_set[i])
+        return bfail(b, DFV_ERR_ARG, "dfv_batch_get_fields: bad arguments");
+    dfv_status s = get_one(b, i, outp, which, on_device);
+    if (s != DFV_OK) return s;
     if (!on_device) B_CU(b, cudaStreamSynchronize(b->stream), "get_fields sync");
+    return DFV_OK;
+}
+
+dfv_status dfv_batch_get_all_fields(dfv_batch *b, double *const *out, int which, int on_device)
+{
+    if (!b) return DFV_ERR_ARG;
+    if (!out) return bfail(b, DFV_ERR_ARG, "dfv_batch_get_all_fields: bad arguments");
+    for (int i = 0; i < b->count; i++)
+        if (!out[i] || !b->fields_set[i]) return bfail(b, DFV_ERR_ARG, "dfv_batch_get_all_fields: bad arguments");
+    for (int i = 0; i < b->count; i++) {
+        dfv_status s = get_one(b, i, out[i], which, on_device);
+        if (s != DFV_OK) return s;
+    }
+    if (!on_device) B_CU(b, cudaStreamSynchronize(b->stream), "get_all_fields sync");
     return DFV_OK;
 }
 

@@ -111,3 +111,23 @@ def test_full_size_batch_sampled_instances_match_oracle():
         assert np.all(err <= 1e-4), (i, wls[i].n, err)
     for i in range(len(wls)):
         b.time(i)
+
+
+def test_all_instance_field_io_matches_per_instance_calls():
+    """dfv_batch_set_all_fields / get_all_fields against the per-instance
+    calls: the same bits; a null instance pointer is refused."""
+    wls = instances()
+    a = B.Batch(wls, precision=B.DFV_FP32)
+    a.set_all_fields()
+    a.run(3, 0.8)
+    b = B.Batch(wls, precision=B.DFV_FP32)
+    for i, wl in enumerate(wls):
+        b.set_fields(i, wl.prim)
+    b.run(3, 0.8)
+    for which in (B.DFV_FIELDS_CONSERVED, B.DFV_FIELDS_PRIMITIVE):
+        got = a.get_all_fields(which)
+        for i in range(len(wls)):
+            np.testing.assert_array_equal(got[i], b.get_fields(i, which))
+    ptrs = (B._vp * len(wls))(*([None] * len(wls)))
+    with pytest.raises(B.DfvError):
+        B._bcheck(B.load().dfv_batch_set_all_fields(a._h, ptrs, 0), a._h, "dfv_batch_set_all_fields")
