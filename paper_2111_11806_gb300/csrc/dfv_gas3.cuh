@@ -74,7 +74,9 @@ struct Gas3T {
     static constexpr int RING = 3;
     static constexpr int NP = 6;                             // rho, rho u, rho v, rho w, rho E, r
     static constexpr int FXS = TX + 1, FYS = TY + 1;
-    static constexpr int ZCHUNK = 32;                        // planes per CTA
+    // planes per CTA (256^3 sphere, cell-updates/s at 16 / 24 / 32 / 48 / 64
+    // planes: 8.59 / 8.64 / 8.40 / 8.52 / 8.04e9)
+    static constexpr int ZCHUNK = 24;
     // the TMA box of a plane: x from ox-4 (a 16-byte boundary) to ox+35, y
     // from oy-2 to oy+9, the five conserved planes rho .. rho E
     static constexpr int BX = TX + 8, BY = PY, BV = 5;
