@@ -1,5 +1,7 @@
 """GPU parity of the stage kernels of single-gas FP32 grids (2-D: warp-marching
-strips, dfv_gasw.cuh; 3-D: marching columns, dfv_gas3.cuh): against the FP64
+strips, dfv_gasw.cuh; 3-D: marching columns, dfv_gas3.cuh, whose plane boxes
+come by TMA when rows are 16-byte multiples (widths 40, 48 below) and by
+per-thread asynchronous copies otherwise (widths 33-37)): against the FP64
 oracle (relative L1 per conserved plane <= 1e-4) on grids with ragged last
 strips and chunks, odd widths, a single strip, grids narrower than the halo,
 reflective walls on every side, a stiffened gas, with and without a body;
@@ -34,7 +36,7 @@ def water(wl):
 
 CASES = [
     ("ragged_100x37", lambda: W.random_state(2, (100, 37), 1, False, seed=201)),
-    ("one_tile_32x16", lambda: W.random_state(2, (32, 16), 1, False, seed=202)),
+    ("two_strips_32x16", lambda: W.random_state(2, (32, 16), 1, False, seed=202)),
     ("tiny_4x3", lambda: W.random_state(2, (4, 3), 1, False, seed=203, body=False)),
     ("thin_128x8", lambda: W.random_state(2, (128, 8), 1, False, seed=204)),
     ("walls_all_68x50", lambda: walled(W.random_state(2, (68, 50), 1, False, seed=205), (1, 1, 1, 1))),
