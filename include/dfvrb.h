@@ -170,6 +170,13 @@ dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device);
  * on_device selects a device or host destination; a host copy synchronises. */
 dfv_status dfv_get_fields(dfv_grid *g, double *out, int which, int on_device);
 
+/* The same two calls for a caller's padded structure-of-arrays buffer: plane
+ * v starts plane_pitch elements after plane v-1 (plane_pitch >= the cell
+ * count; the padding is neither read nor written).  DFV_ERR_ARG when
+ * plane_pitch is below the cell count. */
+dfv_status dfv_set_fields_pitched(dfv_grid *g, const double *prim, long long plane_pitch, int on_device);
+dfv_status dfv_get_fields_pitched(dfv_grid *g, double *out, long long plane_pitch, int which, int on_device);
+
 /* Rigid-body velocity v_r (Sec. 2.3, eq:revo), position and mass.  dynamic =
  * 1: after every step v += dt F/m, x += dt v with F the pressure force sum
  * over grad r (not in the paper, which imposes v_r).  Only dim components of

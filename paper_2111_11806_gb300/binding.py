@@ -29,7 +29,8 @@ EXPORTS = ("dfv_workspace_bytes", "dfv_create_grid", "dfv_add_material", "dfv_se
            "dfv_batch_workspace_bytes", "dfv_batch_create", "dfv_batch_add_material", "dfv_batch_set_fields",
            "dfv_batch_get_fields", "dfv_batch_run", "dfv_batch_autotune", "dfv_batch_set_schedule",
            "dfv_batch_get_time", "dfv_batch_profile", "dfv_batch_launch_count", "dfv_batch_destroy",
-           "dfv_batch_last_error", "dfv_batch_set_all_fields", "dfv_batch_get_all_fields")
+           "dfv_batch_last_error", "dfv_batch_set_all_fields", "dfv_batch_get_all_fields",
+           "dfv_set_fields_pitched", "dfv_get_fields_pitched")
 
 
 class dfv_material_params(ctypes.Structure):
@@ -75,6 +76,8 @@ def load(path: str = LIB_PATH):
     L.dfv_add_material.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(dfv_material_params), _ip]
     L.dfv_set_fields.argtypes = [_vp, _vp, ctypes.c_int]
     L.dfv_get_fields.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int]
+    L.dfv_set_fields_pitched.argtypes = [_vp, _vp, ctypes.c_longlong, ctypes.c_int]
+    L.dfv_get_fields_pitched.argtypes = [_vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int]
     L.dfv_set_body.argtypes = [_vp, _dp, _dp, ctypes.c_double, ctypes.c_int]
     L.dfv_get_body.argtypes = [_vp, _dp, _dp, _dp]
     L.dfv_compute_dt.argtypes = [_vp, ctypes.c_double, _dp]
@@ -284,6 +287,23 @@ class Grid:
         a = np.ascontiguousarray(np.asarray(prim, dtype=np.float64)).reshape(self.nvar, self.ncell)
         with self._ctx():
             _check(load().dfv_set_fields(self._h, _vp(a.ctypes.data), 0), self._h, "dfv_set_fields")
+
+    def set_fields_pitched(self, prim):
+        """prim: a host float64 array of shape (nvar, pitch), pitch >= ncell (a
+        padded buffer; columns ncell .. pitch-1 of each plane are not read)."""
+        a = np.asarray(prim, dtype=np.float64)
+        assert a.ndim == 2 and a.shape[0] == self.nvar and a.flags.c_contiguous
+        with self._ctx():
+            _check(load().dfv_set_fields_pitched(self._h, _vp(a.ctypes.data), int(a.shape[1]), 0), self._h,
+                   "dfv_set_fields_pitched")
+
+    def get_fields_pitched(self, out, which=DFV_FIELDS_CONSERVED):
+        """Into a host float64 array of shape (nvar, pitch), pitch >= ncell."""
+        assert out.dtype == np.float64 and out.ndim == 2 and out.shape[0] == self.nvar and out.flags.c_contiguous
+        with self._ctx():
+            _check(load().dfv_get_fields_pitched(self._h, _vp(out.ctypes.data), int(out.shape[1]), which, 0),
+                   self._h, "dfv_get_fields_pitched")
+        return out
 
     def get_fields(self, which=DFV_FIELDS_CONSERVED, out=None):
         if out is not None and hasattr(out, "is_cuda") and out.is_cuda:

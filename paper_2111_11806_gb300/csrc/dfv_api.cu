@@ -533,16 +533,39 @@ dfv_status dfv_add_material(dfv_grid *g, int kind, const dfv_material_params *m,
     return DFV_OK;
 }
 
-dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device)
+}  // extern "C"
+
+namespace {
+
+// nvar planes between the caller's buffer (planes `pitch` elements apart)
+// and the packed staging planes: one copy when packed, else one per plane
+dfv_status copy_planes(dfv_grid *g, double *dst, long long dpitch, const double *src, long long spitch,
+                       cudaMemcpyKind kind, const char *what)
+{
+    const long long n = g->g.ncell;
+    const int nv = g->ops->nvar;
+    if (dpitch == n && spitch == n) {
+        DFV_CU(g, cudaMemcpyAsync(dst, src, sizeof(double) * nv * (size_t)n, kind, g->stream), what);
+        return DFV_OK;
+    }
+    for (int v = 0; v < nv; v++)
+        DFV_CU(g, cudaMemcpyAsync(dst + v * dpitch, src + v * spitch, sizeof(double) * (size_t)n, kind, g->stream),
+               what);
+    return DFV_OK;
+}
+
+dfv_status set_fields_impl(dfv_grid *g, const double *prim, long long pitch, int on_device)
 {
     if (!g) return DFV_ERR_ARG;
     if (!prim) return fail(g, DFV_ERR_ARG, "dfv_set_fields: null field pointer");
+    if (pitch < g->g.ncell) return fail(g, DFV_ERR_ARG, "dfv_set_fields: plane pitch below the cell count");
     if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
     if (g->nmat != g->nmat_opt) return fail(g, DFV_ERR_ARG, "dfv_set_fields: materials missing");
-    const size_t bytes = sizeof(double) * g->ops->nvar * (size_t)g->g.ncell;
-    DFV_CU(g, cudaMemcpyAsync(g->staging, prim, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                              g->stream),
-           "dfv_set_fields copy");
+    if (dfv_status cs = copy_planes(g, g->staging, g->g.ncell, prim, pitch,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    "dfv_set_fields copy");
+        cs != DFV_OK)
+        return cs;
     DFV_CU(g, g->ops->prim_to_cons(g->g, g->staging, g->g.ncell, g->U, g->stream), "k_prim_to_cons");
     g->launches++;
     // new r: the rigid box is unknown until the next stage 3
@@ -554,11 +577,12 @@ dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device)
     return DFV_OK;
 }
 
-dfv_status dfv_get_fields(dfv_grid *g, double *outp, int which, int on_device)
+dfv_status get_fields_impl(dfv_grid *g, double *outp, long long pitch, int which, int on_device)
 {
     if (!g) return DFV_ERR_ARG;
     if (!outp) return fail(g, DFV_ERR_ARG, "dfv_get_fields: null output");
     if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_get_fields: fields not set");
+    if (pitch < g->g.ncell) return fail(g, DFV_ERR_ARG, "dfv_get_fields: plane pitch below the cell count");
     if (which == DFV_FIELDS_PRIMITIVE) {
         DFV_CU(g, g->ops->cons_to_prim(g->g, g->U, g->staging, g->g.ncell, g->stream), "k_cons_to_prim");
     } else if (which == DFV_FIELDS_CONSERVED) {
@@ -567,12 +591,37 @@ dfv_status dfv_get_fields(dfv_grid *g, double *outp, int which, int on_device)
         return fail(g, DFV_ERR_ARG, "dfv_get_fields: bad `which`");
     }
     g->launches++;
-    const size_t bytes = sizeof(double) * g->ops->nvar * (size_t)g->g.ncell;
-    DFV_CU(g, cudaMemcpyAsync(outp, g->staging, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                              g->stream),
-           "dfv_get_fields copy");
+    if (dfv_status cs = copy_planes(g, outp, pitch, g->staging, g->g.ncell,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    "dfv_get_fields copy");
+        cs != DFV_OK)
+        return cs;
     if (!on_device) DFV_CU(g, cudaStreamSynchronize(g->stream), "dfv_get_fields sync");
     return DFV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device)
+{
+    return set_fields_impl(g, prim, g ? g->g.ncell : 0, on_device);
+}
+
+dfv_status dfv_set_fields_pitched(dfv_grid *g, const double *prim, long long plane_pitch, int on_device)
+{
+    return set_fields_impl(g, prim, plane_pitch, on_device);
+}
+
+dfv_status dfv_get_fields(dfv_grid *g, double *outp, int which, int on_device)
+{
+    return get_fields_impl(g, outp, g ? g->g.ncell : 0, which, on_device);
+}
+
+dfv_status dfv_get_fields_pitched(dfv_grid *g, double *outp, long long plane_pitch, int which, int on_device)
+{
+    return get_fields_impl(g, outp, plane_pitch, which, on_device);
 }
 
 dfv_status dfv_set_body(dfv_grid *g, const double v[3], const double x[3], double mass, int dynamic)

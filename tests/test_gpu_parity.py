@@ -193,3 +193,25 @@ def test_invalid_arguments_raise():
         B.Grid(2, (0, 4), (0, 0), (1, 1), [W.AIR])
     with pytest.raises(B.DfvError, match="UNSUPPORTED"):
         B.Grid(3, (8, 8, 8), (0, 0, 0), (1, 1, 1), [W.ALUMINIUM], solid=True)
+
+
+def test_pitched_field_io_matches_packed():
+    """dfv_set_fields_pitched / dfv_get_fields_pitched with padded planes give
+    the packed calls' bits; the padding is neither read nor written; a pitch
+    below the cell count is refused."""
+    wl = W.random_state(2, (37, 23), 2, False, seed=41)
+    a = B.Grid.from_workload(wl, precision=B.DFV_FP64)
+    b = B.Grid.from_workload(wl, precision=B.DFV_FP64)
+    pitch = wl.ncell + 13
+    padded = np.full((wl.prim.shape[0], pitch), np.nan)
+    padded[:, :wl.ncell] = wl.prim
+    b.set_fields_pitched(padded)
+    for g in (a, b):
+        g.step(2e-7)
+    for which in (B.DFV_FIELDS_CONSERVED, B.DFV_FIELDS_PRIMITIVE):
+        out = np.full((wl.prim.shape[0], pitch), -7.0)
+        b.get_fields_pitched(out, which)
+        np.testing.assert_array_equal(out[:, :wl.ncell], a.get_fields(which))
+        assert np.all(out[:, wl.ncell:] == -7.0)
+    with pytest.raises(B.DfvError):
+        b.set_fields_pitched(padded[:, : wl.ncell - 1].copy())
