@@ -48,6 +48,8 @@ def lib():
             L.o_set_options.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
             L.o_set_variants.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.o_set_walls.argtypes = [ctypes.c_void_p, _ip]
+            L.o_set_seed_stages.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.o_get_stage_input.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
             L.o_seed_normals.argtypes = [ctypes.c_void_p, _dp]
             L.o_cut_fraction.argtypes = [ctypes.c_double] * 7
             L.o_cut_fraction.restype = ctypes.c_double
@@ -116,11 +118,12 @@ class Oracle:
 
     @classmethod
     def from_workload(cls, wl, use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0, normal_method=0,
-                      probe_mode=0):
+                      probe_mode=0, seed_stages=False):
         solid = 2 if (wl.solid and getattr(wl, "history", False)) else wl.solid
         o = cls(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, solid, wl.periodic)
         o.set_options(use_thinc, thinc_beta)
         o.set_variants(hllc_lm, seed_variant, normal_method, probe_mode)
+        o.set_seed_stages(seed_stages)
         o.set_walls(getattr(wl, "walls", (0,) * 6))
         o.set_prim(wl.prim)
         o.set_body(wl.body_v, wl.body_x, wl.body_mass, wl.body_dynamic)
@@ -147,6 +150,18 @@ class Oracle:
         """HLLC-LM flux (True/False), seeding variant (0 original, 1 Riemann),
         normal method (0 Youngs, 1 ELVIRA in 2-D), probe (0 stepped, 1 fixed 1.5 dx)."""
         lib().o_set_variants(self._h, int(bool(hllc_lm)), int(seed_variant), int(normal_method), int(probe_mode))
+
+    def set_seed_stages(self, on=True):
+        """Seed every stage input (U1 before stage 2, U3 before stage 3) as
+        well as the step-start state (on), or the step-start state only."""
+        lib().o_set_seed_stages(self._h, int(bool(on)))
+
+    def stage_input(self, k):
+        """Conserved planes of the last step's input of stage k+1 (k = 1: U1,
+        k = 2: U3), as that stage read them."""
+        out = np.zeros((self.nvar, self.ncell))
+        lib().o_get_stage_input(self._h, int(k), out.ctypes.data_as(_dp))
+        return out
 
     def set_walls(self, walls):
         """Reflective walls: walls[2d], walls[2d+1] for the low / high side of direction d."""

@@ -72,6 +72,9 @@ typedef struct {
     int seed_variant;   /* 0: original seeding, 1: Riemann-problem based (Sec. 3.2) */
     int normal_method;  /* 0: Youngs, 1: ELVIRA (2-D) (Sec. 3.3) */
     int probe_mode;     /* 0: stepped probe 1.0..4.0 dx, 1: fixed 1.5 dx (Sec. 3.2) */
+    int seed_stages;    /* 1: the stage inputs U1, U3 are seeded too, before stages 2 and 3
+                           [reading: Sec. 3.2 seeds the ghost region once per step, before
+                           stage 1; seeding every stage input is the option] */
     int reflect[3][2];  /* reflective wall on the low / high side of direction d */
     double *seed_n;     /* normal used by the last seeding per cell (3 planes) */
 } ostate;
@@ -1361,6 +1364,14 @@ void o_step(ostate *s, double dt)
     double *in[3] = {s->Un, s->U1, s->U3};
     double *out[3] = {s->U1, s->U3, s->U};
     for (int st = 0; st < 3; st++) {
+        if (st > 0 && s->seed_stages) {
+            /* the stage input's rigid band from its own fluid cells (the
+             * mask and the force stay those of the step-start state) */
+            double *keep = s->U;
+            s->U = in[st];
+            o_seed(s);
+            s->U = keep;
+        }
         compute_D(s, in[st], s->D);
         for (int v = 0; v < nv; v++)
             for (long c = 0; c < nc; c++) {
@@ -1473,6 +1484,18 @@ void o_set_variants(void *h, int hllc_lm, int seed_variant, int normal_method, i
     s->seed_variant = seed_variant;
     s->normal_method = normal_method;
     s->probe_mode = probe_mode;
+}
+
+/* Seeding of every stage input (1) or of the step-start state only (0). */
+void o_set_seed_stages(void *h, int on) { ((ostate *)h)->seed_stages = on != 0; }
+
+/* The conserved planes of a stage input of the last step: k = 1 the input of
+ * stage 2 (U1), k = 2 that of stage 3 (U3), as the stage read them (seeded
+ * when the option is on). */
+void o_get_stage_input(void *h, int k, double *out)
+{
+    ostate *s = (ostate *)h;
+    memcpy(out, k == 1 ? s->U1 : s->U3, sizeof(double) * s->nvar * s->ncell);
 }
 
 /* Reflective walls: refl[2 d] / refl[2 d + 1] for the low / high side of a
