@@ -137,6 +137,10 @@ typedef struct {
                             columns marches through that many rows): 0 chooses
                             from the total cell count (4 to 32), else 1 to 4096;
                             results do not depend on it */
+    int seed_stages;     /* 1: seed the stage inputs too (U1 before stage 2, U3
+                            before stage 3; Sec. 3.2 seeds the step-start state
+                            only, 0); single grids only (a batch returns
+                            DFV_ERR_UNSUPPORTED) */
 } dfv_options;
 
 typedef struct dfv_grid dfv_grid;

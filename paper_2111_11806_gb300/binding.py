@@ -43,7 +43,7 @@ class dfv_options(ctypes.Structure):
     _fields_ = [("nmat", ctypes.c_int), ("solid", ctypes.c_int), ("use_thinc", ctypes.c_int),
                 ("thinc_beta", ctypes.c_double), ("hllc_lm", ctypes.c_int), ("seed_variant", ctypes.c_int),
                 ("normal_method", ctypes.c_int), ("probe_mode", ctypes.c_int), ("general_stage", ctypes.c_int),
-                ("gas_rows", ctypes.c_int)]
+                ("gas_rows", ctypes.c_int), ("seed_stages", ctypes.c_int)]
 
 
 class dfv_instance_desc(ctypes.Structure):
@@ -204,7 +204,8 @@ class Grid:
 
     def __init__(self, dim, n, lo, hi, materials, solid=False, precision=DFV_FP64, periodic=None,
                  use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0, normal_method=0, probe_mode=0,
-                 walls=None, device="cuda:0", stream=None, general_stage=False, workspace=None, gas_rows=0):
+                 walls=None, device="cuda:0", stream=None, general_stage=False, workspace=None, gas_rows=0,
+                 seed_stages=False):
         import torch
         if not torch.cuda.is_available():
             raise DfvError("a CUDA device is required (no CPU fallback)")
@@ -237,7 +238,7 @@ class Grid:
         hi3 = _d3(hi)
         opt = dfv_options(self.nmat, skind, int(bool(use_thinc)), float(thinc_beta), int(bool(hllc_lm)),
                           int(seed_variant), int(normal_method), int(probe_mode), int(bool(general_stage)),
-                          int(gas_rows))
+                          int(gas_rows), int(bool(seed_stages)))
         h = _vp()
         with torch.cuda.device(self.device):
             st = L.dfv_create_grid(dim, n3, lo3.ctypes.data_as(_dp), hi3.ctypes.data_as(_dp), bc, precision,
@@ -398,7 +399,8 @@ class Batch:
     grid, body velocity and time step.  Device memory: one torch workspace."""
 
     def __init__(self, workloads, precision=DFV_FP32, use_thinc=True, thinc_beta=1.6, hllc_lm=False, seed_variant=0,
-                 normal_method=0, probe_mode=0, device="cuda:0", stream=None, general_stage=False, gas_rows=0):
+                 normal_method=0, probe_mode=0, device="cuda:0", stream=None, general_stage=False, gas_rows=0,
+                 seed_stages=False):
         import torch
         if not torch.cuda.is_available():
             raise DfvError("a CUDA device is required (no CPU fallback)")
@@ -426,7 +428,8 @@ class Batch:
                 d.v_body[k] = wl.body_v[k] if k < len(wl.body_v) else 0.0
         self._descs = descs
         opt = dfv_options(self.nmat, 0, int(bool(use_thinc)), float(thinc_beta), int(bool(hllc_lm)), int(seed_variant),
-                          int(normal_method), int(probe_mode), int(bool(general_stage)), int(gas_rows))
+                          int(normal_method), int(probe_mode), int(bool(general_stage)), int(gas_rows),
+                          int(bool(seed_stages)))
         nbytes = ctypes.c_size_t()
         _check(L.dfv_batch_workspace_bytes(2, self.count, descs, precision, ctypes.byref(opt), ctypes.byref(nbytes)),
                None, "dfv_batch_workspace_bytes")

@@ -59,6 +59,7 @@ struct dfv_grid {
     bool gas3_tma = false;     // ... with the tensor maps of its plane boxes over U, U1, U3
     CUtensorMap gas3_map[3];
     bool body_moving = false;
+    bool seed_stages = false;  // seed the stage inputs U1, U3 too (dfv_options.seed_stages)
     dfv::GasInst *d_ginst = nullptr;
     int gas_grid = 1;
     long long gas_items = 0;
@@ -322,6 +323,20 @@ dfv_status launch_stage(dfv_grid *g, int s, const void *in, const void *un, void
     return DFV_OK;
 }
 
+// Seeding of a stage input in place (the option seed_stages), the free
+// buffer as the fixed probe's scratch.  A moving body's rigid region moves
+// within the step: the published box of the step-start state is marked
+// invalid first, so that the whole grid is scanned (the step's finalize
+// publishes the box again).
+dfv_status seed_stage_input(dfv_grid *g, void *buf, void *scratch)
+{
+    if (g->dynamic || g->body_moving)
+        DFV_CU(g, cudaMemsetAsync(&g->ctl->rbox_valid, 0, sizeof(int), g->stream), "stage seeding box");
+    DFV_CU(g, g->ops->seed(g->g, buf, scratch, g->ctl, 0, g->stream), "k_seed (stage input)");
+    g->launches += g->g.probe_mode == 1 ? 2 : 1;
+    return DFV_OK;
+}
+
 // fin_in: mode of the previous step's deferred finalize to run in this step's
 // seeding launch (0: none); defer: leave this step's finalize pending.
 dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false, int fin_in = 0, bool defer = false)
@@ -341,8 +356,10 @@ dfv_status launch_step(dfv_grid *g, int mode_extra, bool capturing = false, int 
     dfv_status ss = launch_stage(g, 1, g->U, g->U, g->U1, want_force, fin_in != 0 ? 1 : 0);
     if (ss != DFV_OK) return ss;
     if (rec) DFV_CU(g, cudaEventRecord(ev[2], g->stream), "event");
+    if (g->seed_stages && (ss = seed_stage_input(g, g->U1, g->U3)) != DFV_OK) return ss;
     if ((ss = launch_stage(g, 2, g->U1, g->U, g->U3, 0, 0)) != DFV_OK) return ss;
     if (rec) DFV_CU(g, cudaEventRecord(ev[3], g->stream), "event");
+    if (g->seed_stages && (ss = seed_stage_input(g, g->U3, g->U1)) != DFV_OK) return ss;
     if ((ss = launch_stage(g, 3, g->U3, g->U, g->U, 0, 0)) != DFV_OK) return ss;
     if (rec) DFV_CU(g, cudaEventRecord(ev[4], g->stream), "event");
     // one block: CFL maximum (folded by the stage-3 tiles), force sum, body
@@ -414,6 +431,7 @@ dfv_status dfv_create_grid(int dim, const int n[3], const double lo[3], const do
     g->precision = precision;
     g->nmat_opt = opt->nmat;
     g->solid = solid_kind(opt->solid);
+    g->seed_stages = opt->seed_stages != 0;
     for (int k = 0; k < 6; k++) g->bc[k] = bcs[k];
     g->ops = ops;
     g->stream = (cudaStream_t)stream;

@@ -311,6 +311,7 @@ dfv_status dfv_batch_workspace_bytes(int dim, int count, const dfv_instance_desc
     if (dim != 2 || opt->solid || opt->nmat < 1 || opt->nmat > 2) return DFV_ERR_UNSUPPORTED;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
     if (opt->gas_rows < 0 || opt->gas_rows > 4096) return DFV_ERR_ARG;
+    if (opt->seed_stages) return DFV_ERR_UNSUPPORTED;
     Plan P;
     if (!plan_batch(count, desc, precision, opt->nmat, opt->gas_rows, P)) return DFV_ERR_ARG;
     *bytes = P.total;
@@ -326,6 +327,7 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
     if (dim != 2 || opt->solid || opt->nmat < 1 || opt->nmat > 2) return DFV_ERR_UNSUPPORTED;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
     if (opt->gas_rows < 0 || opt->gas_rows > 4096) return DFV_ERR_ARG;
+    if (opt->seed_stages) return DFV_ERR_UNSUPPORTED;
     dfv_batch *b = new dfv_batch();
     b->count = count;
     b->precision = precision;

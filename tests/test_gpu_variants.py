@@ -97,3 +97,67 @@ def test_batch_with_variants_equals_single_grids(precision):
         g = B.Grid.from_workload(wl, precision=precision, **BOTH)
         g.run(4, 0.8)
         same_kernel_bits(b.get_fields(i), g.cons(), wl, precision)
+
+
+# ---- seeding of every stage input (dfv_options.seed_stages; oracle pins in
+# tests/test_oracle_seed_stages.py)
+
+SS = dict(seed_stages=True)
+
+SEED_STAGES_ONE = [
+    ("two_fluid_body_70x45_ss", lambda: W.random_state(2, (70, 45), 2, False, seed=11), SS),
+    ("one_fluid_body_70x45_fixed_probe_ss", lambda: W.random_state(2, (70, 45), 1, False, seed=11),
+     dict(seed_stages=True, probe_mode=1)),
+    ("dynamic_body_128x64_ss", lambda: W.dynamic_body_2d(128, 64), SS),
+    ("solid_two_mat_40x37_ss", lambda: W.random_state(2, (40, 37), 2, True, seed=12, amp=0.02), SS),
+    ("sphere_3d_36x20x18_ss", lambda: W.random_state(3, (36, 20, 18), 1, False, seed=15), SS),
+]
+
+
+@pytest.mark.parametrize("name,make,var", SEED_STAGES_ONE, ids=[c[0] for c in SEED_STAGES_ONE])
+def test_seed_stages_fp64_one_step(name, make, var):
+    wl = make()
+    o, g = run_both(wl, 1, B.DFV_FP64, **var)
+    err = rel_l1(g.cons(), o.cons(), wl)
+    assert np.all(err <= 1e-12), err
+
+
+@pytest.mark.parametrize("name,make,var", [SEED_STAGES_ONE[0], SEED_STAGES_ONE[2]],
+                         ids=[SEED_STAGES_ONE[i][0] for i in (0, 2)])
+def test_seed_stages_fp64_100_steps(name, make, var):
+    wl = make()
+    o, g = run_both(wl, 100, B.DFV_FP64, **var)
+    err = rel_l1(g.cons(), o.cons(), wl)
+    assert np.all(err <= 1e-8), err
+
+
+@pytest.mark.parametrize("name,make,steps", [
+    ("cylinder_64", lambda: W.cylinder_2d(64), 30),                       # the 2-D gas kernel path
+    ("one_fluid_body_70x45", lambda: W.random_state(2, (70, 45), 1, False, seed=11), 20),
+    ("sphere_3d_36x20x18", lambda: W.random_state(3, (36, 20, 18), 1, False, seed=15), 10),
+])
+def test_seed_stages_fp32(name, make, steps):
+    wl = make()
+    o, g = run_both(wl, steps, B.DFV_FP32, seed_stages=True)
+    err = rel_l1(g.cons(), o.cons(), wl)
+    assert np.all(err <= 1e-4), err
+
+
+def test_seed_stages_device_run_equals_host_steps():
+    """dfv_run (graph replay; the extra seeding launches captured) against
+    host-driven steps, bit for bit."""
+    wl = W.random_state(2, (70, 45), 1, False, seed=11)
+    g1 = B.Grid.from_workload(wl, precision=B.DFV_FP64, seed_stages=True)
+    g2 = B.Grid.from_workload(wl, precision=B.DFV_FP64, seed_stages=True)
+    t1 = 0.0
+    for _ in range(8):
+        dt = g1.compute_dt(0.8)
+        g1.step(dt)
+        t1 += dt
+    assert g2.run(8, 0.8) == pytest.approx(t1, rel=1e-15)
+    np.testing.assert_array_equal(g1.cons(), g2.cons())
+
+
+def test_batch_refuses_seed_stages():
+    with pytest.raises(B.DfvError, match="UNSUPPORTED"):
+        B.Batch([W.ellipse_instance(0, n=64)], precision=B.DFV_FP32, seed_stages=True)
