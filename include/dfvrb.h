@@ -179,6 +179,14 @@ dfv_status dfv_get_fields(dfv_grid *g, double *out, int which, int on_device);
  * count; the padding is neither read nor written).  DFV_ERR_ARG when
  * plane_pitch is below the cell count. */
 dfv_status dfv_set_fields_pitched(dfv_grid *g, const double *prim, long long plane_pitch, int on_device);
+
+/* Restore a state saved with dfv_get_fields(DFV_FIELDS_CONSERVED) (FP64
+ * conserved planes, layout above; host or device, caller-owned): checkpoint
+ * and resume.  The planes are stored as they are (FP64) or narrowed (FP32,
+ * the exact inverse of the widening of dfv_get_fields), so that with the body
+ * state (dfv_get_body / dfv_set_body) a resumed run continues bit for bit.
+ * Returns when the host buffer may be reused. */
+dfv_status dfv_set_state(dfv_grid *g, const double *cons, int on_device);
 dfv_status dfv_get_fields_pitched(dfv_grid *g, double *out, long long plane_pitch, int which, int on_device);
 
 /* Rigid-body velocity v_r (Sec. 2.3, eq:revo), position and mass.  dynamic =

@@ -30,7 +30,7 @@ EXPORTS = ("dfv_workspace_bytes", "dfv_create_grid", "dfv_add_material", "dfv_se
            "dfv_batch_get_fields", "dfv_batch_run", "dfv_batch_autotune", "dfv_batch_set_schedule",
            "dfv_batch_get_time", "dfv_batch_profile", "dfv_batch_launch_count", "dfv_batch_destroy",
            "dfv_batch_last_error", "dfv_batch_set_all_fields", "dfv_batch_get_all_fields",
-           "dfv_set_fields_pitched", "dfv_get_fields_pitched")
+           "dfv_set_fields_pitched", "dfv_get_fields_pitched", "dfv_set_state")
 
 
 class dfv_material_params(ctypes.Structure):
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
     L.dfv_set_fields.argtypes = [_vp, _vp, ctypes.c_int]
     L.dfv_get_fields.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int]
     L.dfv_set_fields_pitched.argtypes = [_vp, _vp, ctypes.c_longlong, ctypes.c_int]
+    L.dfv_set_state.argtypes = [_vp, _vp, ctypes.c_int]
     L.dfv_get_fields_pitched.argtypes = [_vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int]
     L.dfv_set_body.argtypes = [_vp, _dp, _dp, ctypes.c_double, ctypes.c_int]
     L.dfv_get_body.argtypes = [_vp, _dp, _dp, _dp]
@@ -288,6 +289,12 @@ class Grid:
         a = np.ascontiguousarray(np.asarray(prim, dtype=np.float64)).reshape(self.nvar, self.ncell)
         with self._ctx():
             _check(load().dfv_set_fields(self._h, _vp(a.ctypes.data), 0), self._h, "dfv_set_fields")
+
+    def set_state(self, cons):
+        """Restore FP64 conserved planes (nvar, ncell) saved with cons() (checkpoint/resume)."""
+        a = np.ascontiguousarray(np.asarray(cons, dtype=np.float64)).reshape(self.nvar, self.ncell)
+        with self._ctx():
+            _check(load().dfv_set_state(self._h, _vp(a.ctypes.data), 0), self._h, "dfv_set_state")
 
     def set_fields_pitched(self, prim):
         """prim: a host float64 array of shape (nvar, pitch), pitch >= ncell (a

@@ -170,6 +170,19 @@ __global__ void k_set_body(Ctl *c, double v0, double v1, double v2, double x0, d
     dfv::ctl_sync_v(c);
 }
 
+// A saved FP64 conserved state (packed planes) into the FP32 storage planes
+// (pitch elements apart): the narrowing inverts the widening of
+// dfv_get_fields exactly.
+__global__ void k_state_from_f64(const double *src, float *dst, long long ncell, long long pitch, int nv)
+{
+    const long long total = ncell * nv;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long v = t / ncell, c = t - v * ncell;
+        dst[v * pitch + c] = (float)src[t];
+    }
+}
+
 __global__ void k_set_run(Ctl *c, double cfl, double t_end)
 {
     c->cfl = cfl;
@@ -640,6 +653,36 @@ dfv_status dfv_get_fields(dfv_grid *g, double *outp, int which, int on_device)
 dfv_status dfv_get_fields_pitched(dfv_grid *g, double *outp, long long plane_pitch, int which, int on_device)
 {
     return get_fields_impl(g, outp, plane_pitch, which, on_device);
+}
+
+dfv_status dfv_set_state(dfv_grid *g, const double *cons, int on_device)
+{
+    if (!g) return DFV_ERR_ARG;
+    if (!cons) return fail(g, DFV_ERR_ARG, "dfv_set_state: null state pointer");
+    if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
+    if (g->nmat != g->nmat_opt) return fail(g, DFV_ERR_ARG, "dfv_set_state: materials missing");
+    const long long n = g->g.ncell, P = g->g.pitch;
+    const int nv = g->ops->nvar;
+    const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (g->precision == DFV_FP64) {
+        for (int v = 0; v < nv; v++)
+            DFV_CU(g, cudaMemcpyAsync((double *)g->U + v * P, cons + v * n, sizeof(double) * (size_t)n, in, g->stream),
+                   "dfv_set_state copy");
+    } else {
+        DFV_CU(g, cudaMemcpyAsync(g->staging, cons, sizeof(double) * nv * (size_t)n, in, g->stream),
+               "dfv_set_state copy");
+        const long long blocks = std::min((n * nv + 255) / 256, 152LL * 16);
+        k_state_from_f64<<<(unsigned)std::max(1LL, blocks), 256, 0, g->stream>>>(g->staging, (float *)g->U, n, P, nv);
+        DFV_CU(g, cudaGetLastError(), "k_state_from_f64");
+        g->launches++;
+    }
+    // the rigid box of the restored state is unknown until the next stage 3
+    DFV_CU(g, cudaMemsetAsync(&g->ctl->rbox_valid, 0, sizeof(int), g->stream), "dfv_set_state box");
+    if (!on_device) DFV_CU(g, cudaStreamSynchronize(g->stream), "dfv_set_state sync");
+    g->fields_set = true;
+    g->smax_valid = false;
+    g->dt_valid = false;
+    return DFV_OK;
 }
 
 dfv_status dfv_set_body(dfv_grid *g, const double v[3], const double x[3], double mass, int dynamic)
