@@ -185,7 +185,8 @@ dfv_status dfv_set_fields_pitched(dfv_grid *g, const double *prim, long long pla
  * and resume.  The planes are stored as they are (FP64) or narrowed (FP32,
  * the exact inverse of the widening of dfv_get_fields), so that with the body
  * state (dfv_get_body / dfv_set_body) a resumed run continues bit for bit.
- * Returns when the host buffer may be reused. */
+ * The grid's time t starts again at 0.  Returns when the host buffer may be
+ * reused. */
 dfv_status dfv_set_state(dfv_grid *g, const double *cons, int on_device);
 dfv_status dfv_get_fields_pitched(dfv_grid *g, double *out, long long plane_pitch, int which, int on_device);
 
