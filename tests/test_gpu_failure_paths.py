@@ -8,7 +8,12 @@
   byte pattern before the grid is created; after steps on small grids of odd
   sizes (every precision and dimension, the gas and general stage kernels,
   solids, walls) the padding elements of every plane of U^n, U1, U3 and the
-  bytes past the workspace's end still hold the canary."""
+  bytes past the workspace's end still hold the canary;
+* reads outside the state: a workspace filled with 0xFF bytes (NaN in FP32
+  and FP64) before creation gives the same bits as one filled with zeros, so
+  that no kernel lets plane padding or workspace it has not written reach its
+  arithmetic (a NaN read would spread into the fields or set the error
+  word)."""
 import numpy as np
 import pytest
 
@@ -80,3 +85,29 @@ def test_no_write_outside_the_state(name, make, prec, _):
             assert np.all(host[a:b] == CANARY), (name, o, v)
     # past the workspace the library was given
     assert np.all(host[base + nbytes:] == CANARY)
+
+
+def _run_in(ws, wl, prec, solid):
+    g = B.Grid(wl.dim, wl.n, wl.lo, wl.hi, wl.materials, solid=solid, precision=prec, periodic=wl.periodic,
+               walls=getattr(wl, "walls", None), workspace=ws)
+    g.set_fields(wl.prim)
+    g.set_body(wl.body_v, wl.body_x, wl.body_mass, wl.body_dynamic)
+    g.run(5, 0.6)
+    for _k in range(2):
+        g.step(g.compute_dt(0.6))
+    g.check(timeout_ms=60000)
+    return g.cons()
+
+
+@pytest.mark.parametrize("name,make,prec,_", CASES, ids=[c[0] for c in CASES])
+def test_no_read_outside_the_state(name, make, prec, _):
+    import torch
+    wl = make()
+    solid = 2 if (wl.solid and getattr(wl, "history", False)) else wl.solid
+    nbytes = B.workspace_bytes(wl.dim, wl.n, wl.nmat, int(bool(solid)), prec)
+    nan_ws = torch.full((nbytes + 256,), 0xFF, dtype=torch.uint8, device="cuda")
+    zero_ws = torch.zeros((nbytes + 256,), dtype=torch.uint8, device="cuda")
+    a = _run_in(nan_ws, wl, prec, solid)
+    b = _run_in(zero_ws, wl, prec, solid)
+    assert np.all(np.isfinite(a))
+    np.testing.assert_array_equal(a, b)
