@@ -5,11 +5,13 @@ forms against the plain FP64 form, at a stated L1 error against the FP64
 oracle, as a fraction of the HBM roofline.
 
 Headline workload (the batched form): 256 independent 2-D shock-over-rigid-
-ellipse instances, grid sizes drawn from {128,192,256,384,512}^2 (about 27 M
-cells, 0.54 GB per FP32 state copy, larger than the 129 MB L2, so no flush is
-needed), Mach U[1.5,3], FP32, advanced by one persistent launch per phase in a
-captured CUDA graph with the autotuned schedule.  One benchmark step = one
-time step of every instance (seeding, three SSP-RK3 stages, CFL reduction).
+ellipse instances, grid sizes drawn from {128,192,256,384,512}^2 (26.3 M
+cells, 0.53 GB per FP32 state copy, larger than the 129 MB L2, so no flush is
+needed), Mach U[1.5,3], FP32, advanced by one launch per phase over an
+(instance, work item) list in a captured CUDA graph, with the launch shape and
+schedule the autotuner picks (persistent CTAs, or one CTA per work item).  One
+benchmark step = one time step of every instance (seeding, three SSP-RK3
+stages, CFL reduction).
 
 The roofline is taken from the timed region itself: (8 nvar + 1) w
 algorithmic bytes per cell-step (eight plane touches per conserved variable
