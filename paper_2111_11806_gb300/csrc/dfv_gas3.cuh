@@ -5,14 +5,17 @@
 // A CTA owns a 32 x 8 column of cells and marches through a chunk of planes
 // in z.  A ring of three planes of primitives (z, z+1, z+2, each with its x
 // and y halo of 2) sits in shared memory; per plane z:
-//   1. plane z+2 is converted from the conserved values the CTA fetched into
-//      registers one plane earlier (and plane z+3 is fetched);
+//   1. plane z+2 is converted from the conserved values that arrived in the
+//      shared fetch slot during the previous plane (one TMA tensor copy of
+//      the plane's box, or per-thread asynchronous copies when rows are not
+//      16-byte multiples); then plane z+3 is fetched into the slot, and the
+//      cell's own values of plane z+1 are prefetched into L1;
 //   2. slopes: every cell of plane z its van Leer slopes in x and y (face
 //      values to shared memory, one warp the halo), every cell of plane z+1
 //      its slope in z;
 //   3. faces: every thread the HLLC fluxes of its cell's left x face, bottom
 //      y face and top z face; the bottom z face and the top z-face value of
-//      plane z were carried in registers from the previous plane;
+//      plane z were carried in shared memory from the previous plane;
 //   4. update of plane z: divergence with a compensated (TwoSum) sum, rigid
 //      mask, RK combination; in stage 3 the CFL maximum and the rigid box.
 // Each primitive is converted once per chunk and each slope computed once;
