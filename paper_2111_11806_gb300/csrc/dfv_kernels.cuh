@@ -145,6 +145,53 @@ __device__ __forceinline__ void block_reduce4(double v[4], double *scratch /* 4*
     }
 }
 
+// Fixed-order compensated block sum of three FP32 values per thread: TwoSum
+// at every addition with the low parts summed alongside, over the warp by
+// shuffles and then over the warp leaders in index order; the result (hi +
+// lo, widened) in thread 0.  The FP32 form's pressure-force partials: no FP64
+// arithmetic in the bulk.
+template <int THREADS>
+__device__ __forceinline__ void block_sum3_f32(const float v[3], float *scratch /* 6*32 */, double out[3])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float hi[3], lo[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        hi[k] = v[k];
+        lo[k] = 0.f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float oh = __shfl_down_sync(0xffffffffu, hi[k], o), ol = __shfl_down_sync(0xffffffffu, lo[k], o);
+            float s, e;
+            two_sum(hi[k], oh, s, e);
+            hi[k] = s;
+            lo[k] = lo[k] + (ol + e);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            scratch[k * 32 + warp] = hi[k];
+            scratch[(3 + k) * 32 + warp] = lo[k];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        constexpr int NW = (THREADS + 31) / 32;
+        for (int k = 0; k < 3; k++) {
+            float h = scratch[k * 32], l = scratch[(3 + k) * 32];
+            for (int w = 1; w < NW; w++) {
+                float s, e;
+                two_sum(h, scratch[k * 32 + w], s, e);
+                h = s;
+                l = l + (scratch[(3 + k) * 32 + w] + e);
+            }
+            out[k] = (double)h + (double)l;
+        }
+    }
+}
+
 // Block maximum of one value per thread (fixed order; result in thread 0).
 template <int THREADS, class T>
 __device__ __forceinline__ T block_max(T v, T *scratch /* 32 */)
@@ -1121,7 +1168,7 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
 
     if (early) pdl_wait();   // Δt and the seeded cells of U^n are final from here on
     const R dt = ctl_dt<R>(a.ctl);
-    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    R fcell[3] = {R(0), R(0), R(0)};   // the cell's pressure-force contribution (stage 1)
     R smax_cell = R(0);
     bool rigid_new = false;
     if (inside) {
@@ -1183,7 +1230,7 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
             for (int d = 0; d < DIM; d++) {
                 const int sd = B::stride(d);
                 const R gr = (sW[L::IR * B::N + bcell + sd] - sW[L::IR * B::N + bcell - sd]) / (R(2) * gc.dx[d]);
-                red[1 + d] = (double)(p * gr * gc.dV);
+                fcell[d] = p * gr * gc.dV;
             }
         }
         if (STAGE == 3) rigid_new = o[L::IR] > R(0.5);
@@ -1235,12 +1282,22 @@ __device__ __forceinline__ void stage_tile(const GridP &g, const StageArgs &a, i
         }
     }
     if (STAGE == 1 && a.want_force) {
-        block_reduce4<TL::THREADS>(red, sred);
+        // the block's force partial: a compensated FP32 sum in the FP32 form,
+        // an FP64 sum in the FP64 form
+        double fs[3];
+        if constexpr (sizeof(R) == 4) {
+            const float fv[3] = {(float)fcell[0], (float)fcell[1], (float)fcell[2]};
+            block_sum3_f32<TL::THREADS>(fv, reinterpret_cast<float *>(sred), fs);
+        } else {
+            double red[4] = {0.0, (double)fcell[0], (double)fcell[1], (double)fcell[2]};
+            block_reduce4<TL::THREADS>(red, sred);
+            for (int k = 0; k < 3; k++) fs[k] = red[1 + k];
+        }
         if (threadIdx.x == 0) {
             double *pp = a.partials + 4 * tile_id;
-            pp[1] = red[1];
-            pp[2] = red[2];
-            pp[3] = red[3];
+            pp[1] = fs[0];
+            pp[2] = fs[1];
+            pp[3] = fs[2];
         }
     }
 }
