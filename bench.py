@@ -471,10 +471,12 @@ def run_batch_fp64(torch, B, wls, stream, steps):
     return rec
 
 
-def run_e2e(torch, B, wls, stream, job_steps):
+def run_e2e(torch, B, wls, stream, job_steps, reps=3):
     """End to end through the C ABI with host buffers: every instance's
     primitive fields in from pinned host memory, the configuration's steps,
-    every instance's fields back to pinned host memory."""
+    every instance's fields back to pinned host memory.  The job runs `reps`
+    times from the same fields (the host transfers vary from run to run by
+    some tens of ms); the median job time is reported."""
     cells = int(sum(wl.ncell for wl in wls))
     host_in = [torch.empty(wl.prim.shape, dtype=torch.float64, pin_memory=True) for wl in wls]
     host_out = [torch.empty(wl.prim.shape, dtype=torch.float64, pin_memory=True) for wl in wls]
@@ -483,20 +485,24 @@ def run_e2e(torch, B, wls, stream, job_steps):
     bt = B.Batch(wls, precision=B.DFV_FP32, stream=stream)
     bt.set_all_fields()
     bt.autotune(trial_steps=2, cfl=0.8)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    bt.set_all_fields([h.numpy() for h in host_in])
-    bt.run(job_steps, 0.8)
-    bt.get_all_fields(B.DFV_FIELDS_PRIMITIVE, outs=[h.numpy() for h in host_out])
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bt.set_all_fields([h.numpy() for h in host_in])
+        bt.run(job_steps, 0.8)
+        bt.get_all_fields(B.DFV_FIELDS_PRIMITIVE, outs=[h.numpy() for h in host_out])
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    el = statistics.median(times)
     nbytes = int(sum(h.numel() * 8 for h in host_in))
     del bt
     return {"value": cells * job_steps / el, "ms": 1e3 * el, "units": cells * job_steps, "unit": UNIT,
             "h2d_bytes_per_step": nbytes / job_steps,
             "d2h_bytes_per_step": nbytes / job_steps,
-            "job": "set_all_fields(pinned host, %d instances) + %d steps + get_all_fields(pinned host), %.3f s" % (
-                len(wls), job_steps, el)}
+            "job": "set_all_fields(pinned host, %d instances) + %d steps + get_all_fields(pinned host): "
+                   "median of %d jobs %.3f s (%s)" % (len(wls), job_steps, reps, el,
+                                                      " / ".join("%.3f" % t for t in times))}
 
 
 def gpu_accuracy_run(torch, B, stream, spec, checkpoints, batched):
