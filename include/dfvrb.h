@@ -104,7 +104,7 @@ typedef struct {
 } dfv_material_params;
 
 typedef struct {
-    int nmat;            /* number of materials, 1 to 3 (the batched form: 1 or 2) */
+    int nmat;            /* number of materials, 1 to 3 */
     int solid;           /* 1: carry the stretch tensor V (elastoplastic); 2: also one
                             equivalent-plastic-strain plane (phi rho eps)_l per
                             material after r (Sec. 2.1.1 history variables; the

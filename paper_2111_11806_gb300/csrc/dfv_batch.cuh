@@ -263,8 +263,9 @@ struct Kern {
 template <class R>
 Kern batch_kernels(int nmat)
 {
-    return nmat == 1 ? Kern{BK<R, 1>::prepare, BK<R, 1>::max_ctas_per_sm, BK<R, 1>::launch}
-                     : Kern{BK<R, 2>::prepare, BK<R, 2>::max_ctas_per_sm, BK<R, 2>::launch};
+    return nmat == 1   ? Kern{BK<R, 1>::prepare, BK<R, 1>::max_ctas_per_sm, BK<R, 1>::launch}
+           : nmat == 2 ? Kern{BK<R, 2>::prepare, BK<R, 2>::max_ctas_per_sm, BK<R, 2>::launch}
+                       : Kern{BK<R, 3>::prepare, BK<R, 3>::max_ctas_per_sm, BK<R, 3>::launch};
 }
 
 // One translation unit per precision (the FP32 one is built with the fast

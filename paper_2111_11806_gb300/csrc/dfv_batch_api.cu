@@ -308,7 +308,7 @@ dfv_status dfv_batch_workspace_bytes(int dim, int count, const dfv_instance_desc
                                      const dfv_options *opt, size_t *bytes)
 {
     if (!desc || !opt || !bytes || count < 1) return DFV_ERR_ARG;
-    if (dim != 2 || opt->solid || opt->nmat < 1 || opt->nmat > 2) return DFV_ERR_UNSUPPORTED;
+    if (dim != 2 || opt->solid || opt->nmat < 1 || opt->nmat > 3) return DFV_ERR_UNSUPPORTED;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
     if (opt->gas_rows < 0 || opt->gas_rows > 4096) return DFV_ERR_ARG;
     if (opt->seed_stages) return DFV_ERR_UNSUPPORTED;
@@ -324,7 +324,7 @@ dfv_status dfv_batch_create(int dim, int count, const dfv_instance_desc *desc, i
 {
     if (!out || !desc || !opt || count < 1) return DFV_ERR_ARG;
     *out = nullptr;
-    if (dim != 2 || opt->solid || opt->nmat < 1 || opt->nmat > 2) return DFV_ERR_UNSUPPORTED;
+    if (dim != 2 || opt->solid || opt->nmat < 1 || opt->nmat > 3) return DFV_ERR_UNSUPPORTED;
     if (precision != DFV_FP64 && precision != DFV_FP32) return DFV_ERR_ARG;
     if (opt->gas_rows < 0 || opt->gas_rows > 4096) return DFV_ERR_ARG;
     if (opt->seed_stages) return DFV_ERR_UNSUPPORTED;

@@ -131,3 +131,41 @@ def test_all_instance_field_io_matches_per_instance_calls():
     ptrs = (B._vp * len(wls))(*([None] * len(wls)))
     with pytest.raises(B.DfvError):
         B._bcheck(B.load().dfv_batch_set_all_fields(a._h, ptrs, 0), a._h, "dfv_batch_set_all_fields")
+
+
+MIXTURE_SIZES = [(70, 45), (33, 64), (96, 40)]
+
+
+@pytest.mark.parametrize("nmat", [2, 3])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_batch_of_mixtures_equals_single_grids(nmat, precision):
+    """Two- and three-material fluid instances (blobs of water and helium in
+    air around a rigid body) step in the batch exactly as single grids do."""
+    wls = [W.random_state(2, n, nmat, False, seed=40 + i) for i, n in enumerate(MIXTURE_SIZES)]
+    b = B.Batch(wls, precision=precision)
+    b.set_all_fields()
+    b.run(4, 0.6)
+    for i, wl in enumerate(wls):
+        g = B.Grid.from_workload(wl, precision=precision)
+        g.run(4, 0.6)
+        same_kernel_bits(b.get_fields(i), g.cons(), wl, precision)
+
+
+def test_batch_of_three_material_mixtures_matches_oracle():
+    from oracle import Oracle
+    wls = [W.random_state(2, n, 3, False, seed=50 + i) for i, n in enumerate(MIXTURE_SIZES)]
+    b = B.Batch(wls, precision=B.DFV_FP64)
+    b.set_all_fields()
+    b.run(1, 0.6)
+    for i, wl in enumerate(wls):
+        o = Oracle.from_workload(wl)
+        o.step(o.compute_dt(0.6))
+        err = rel_l1(b.get_fields(i), o.cons(), wl)
+        assert np.all(err <= 1e-12), (i, err)
+
+
+def test_batch_refuses_four_materials():
+    wl = W.ellipse_instance(0, n=32)
+    wl.materials = [W.AIR] * 4
+    with pytest.raises(B.DfvError):
+        B.Batch([wl], precision=B.DFV_FP32)
