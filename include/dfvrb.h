@@ -164,7 +164,11 @@ dfv_status dfv_add_material(dfv_grid *g, int kind, const dfv_material_params *p,
 
 /* Initial fields from FP64 primitive planes (layout above).  on_device = 1:
  * `prim` is a device pointer; 0: host pointer.  Conversion to conserved
- * variables uses the mixture rules of Sec. 2.2. */
+ * variables uses the mixture rules of Sec. 2.2.  Device fields and host
+ * fields in page-locked memory registered with CUDA (cudaHostAlloc,
+ * cudaHostRegister) are converted in place by the device; other host memory
+ * is first copied into the grid's staging buffer.  A host call returns when
+ * the buffer may be reused.  The same holds for every field call below. */
 dfv_status dfv_set_fields(dfv_grid *g, const double *prim, int on_device);
 
 /* Copy the current fields out as FP64 planes (layout above): which =
@@ -296,7 +300,8 @@ dfv_status dfv_batch_get_fields(dfv_batch *b, int i, double *out, int which, int
  * as on_device says) hold instance i's nvar FP64 planes of n[0] n[1] values.
  * The copies and conversions of all instances are issued back to back on the
  * batch's stream and the call returns when they are done (host buffers may
- * then be reused). DFV_ERR_ARG for a null pointer (nothing is copied) or,
+ * then be reused); page-locked host buffers are converted in place, without
+ * the staging copy, as for dfv_set_fields. DFV_ERR_ARG for a null pointer (nothing is copied) or,
  * when reading, an instance whose fields were never set. */
 dfv_status dfv_batch_set_all_fields(dfv_batch *b, const double *const *prim, int on_device);
 dfv_status dfv_batch_get_all_fields(dfv_batch *b, double *const *out, int which, int on_device);

@@ -570,6 +570,20 @@ namespace {
 
 // nvar planes between the caller's buffer (planes `pitch` elements apart)
 // and the packed staging planes: one copy when packed, else one per plane
+// A host buffer the device can address (page-locked memory registered with
+// CUDA): the device address of `p`, else null.  The conversion kernels then
+// read or write the host fields in place over the CPU-GPU link instead of
+// going through a copy into the staging buffer.
+const void *mapped_host(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 dfv_status copy_planes(dfv_grid *g, double *dst, long long dpitch, const double *src, long long spitch,
                        cudaMemcpyKind kind, const char *what)
 {
@@ -592,12 +606,19 @@ dfv_status set_fields_impl(dfv_grid *g, const double *prim, long long pitch, int
     if (pitch < g->g.ncell) return fail(g, DFV_ERR_ARG, "dfv_set_fields: plane pitch below the cell count");
     if (dfv_status fs = flush_fin(g); fs != DFV_OK) return fs;
     if (g->nmat != g->nmat_opt) return fail(g, DFV_ERR_ARG, "dfv_set_fields: materials missing");
-    if (dfv_status cs = copy_planes(g, g->staging, g->g.ncell, prim, pitch,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                    "dfv_set_fields copy");
-        cs != DFV_OK)
-        return cs;
-    DFV_CU(g, g->ops->prim_to_cons(g->g, g->staging, g->g.ncell, g->U, g->stream), "k_prim_to_cons");
+    // device and page-locked host fields are converted in place; other host
+    // memory goes through the staging buffer
+    const double *src = on_device ? prim : static_cast<const double *>(mapped_host(prim));
+    long long spitch = pitch;
+    if (!src) {
+        if (dfv_status cs = copy_planes(g, g->staging, g->g.ncell, prim, pitch, cudaMemcpyHostToDevice,
+                                        "dfv_set_fields copy");
+            cs != DFV_OK)
+            return cs;
+        src = g->staging;
+        spitch = g->g.ncell;
+    }
+    DFV_CU(g, g->ops->prim_to_cons(g->g, src, spitch, g->U, g->stream), "k_prim_to_cons");
     g->launches++;
     // new r: the rigid box is unknown until the next stage 3
     DFV_CU(g, cudaMemsetAsync(&g->ctl->rbox_valid, 0, sizeof(int), g->stream), "dfv_set_fields box");
@@ -614,19 +635,26 @@ dfv_status get_fields_impl(dfv_grid *g, double *outp, long long pitch, int which
     if (!outp) return fail(g, DFV_ERR_ARG, "dfv_get_fields: null output");
     if (!g->fields_set) return fail(g, DFV_ERR_ARG, "dfv_get_fields: fields not set");
     if (pitch < g->g.ncell) return fail(g, DFV_ERR_ARG, "dfv_get_fields: plane pitch below the cell count");
-    if (which == DFV_FIELDS_PRIMITIVE) {
-        DFV_CU(g, g->ops->cons_to_prim(g->g, g->U, g->staging, g->g.ncell, g->stream), "k_cons_to_prim");
-    } else if (which == DFV_FIELDS_CONSERVED) {
-        DFV_CU(g, g->ops->cons_to_f64(g->g, g->U, g->staging, g->g.ncell, g->ops->nvar, g->stream), "k_cons_to_f64");
-    } else {
+    if (which != DFV_FIELDS_PRIMITIVE && which != DFV_FIELDS_CONSERVED)
         return fail(g, DFV_ERR_ARG, "dfv_get_fields: bad `which`");
+    // into device or page-locked host fields in place; other host memory
+    // through the staging buffer
+    double *dst = on_device ? outp : static_cast<double *>(const_cast<void *>(mapped_host(outp)));
+    const bool staged = dst == nullptr;
+    const long long dpitch = staged ? g->g.ncell : pitch;
+    if (staged) dst = g->staging;
+    if (which == DFV_FIELDS_PRIMITIVE) {
+        DFV_CU(g, g->ops->cons_to_prim(g->g, g->U, dst, dpitch, g->stream), "k_cons_to_prim");
+    } else {
+        DFV_CU(g, g->ops->cons_to_f64(g->g, g->U, dst, dpitch, g->ops->nvar, g->stream), "k_cons_to_f64");
     }
     g->launches++;
-    if (dfv_status cs = copy_planes(g, outp, pitch, g->staging, g->g.ncell,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                    "dfv_get_fields copy");
-        cs != DFV_OK)
-        return cs;
+    if (staged) {
+        if (dfv_status cs = copy_planes(g, outp, pitch, g->staging, g->g.ncell, cudaMemcpyDeviceToHost,
+                                        "dfv_get_fields copy");
+            cs != DFV_OK)
+            return cs;
+    }
     if (!on_device) DFV_CU(g, cudaStreamSynchronize(g->stream), "dfv_get_fields sync");
     return DFV_OK;
 }

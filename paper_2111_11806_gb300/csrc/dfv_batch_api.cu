@@ -535,18 +535,35 @@ dfv_status dfv_batch_add_material(dfv_batch *b, int kind, const dfv_material_par
 
 namespace {
 
+// A host buffer the device can address (page-locked memory registered with
+// CUDA): the device address of `p`, else null.  The conversion kernels then
+// read or write the host fields in place over the CPU-GPU link instead of
+// going through a copy into the staging buffer.
+const void *mapped_host(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // The copy and conversion of one instance's fields, issued on the batch's
 // stream (the staging buffer is reused in stream order: no synchronisation
-// between instances is needed).
+// between instances is needed).  Page-locked host fields are converted in
+// place, without the staging copy.
 dfv_status set_one(dfv_batch *b, int i, const double *prim, int on_device)
 {
     const GridP &g = b->hinst[i].g;
     const int w = b->precision == DFV_FP32 ? 4 : 8;
     const size_t bytes = sizeof(double) * b->ops->nvar * (size_t)g.ncell;
-    B_CU(b, cudaMemcpyAsync(b->staging, prim, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            b->stream),
-         "set_fields copy");
-    B_CU(b, b->ops->prim_to_cons(g, b->staging, g.ncell, (char *)b->U + (size_t)w * b->hinst[i].off, b->stream),
+    const double *src = on_device ? prim : static_cast<const double *>(mapped_host(prim));
+    if (!src) {
+        B_CU(b, cudaMemcpyAsync(b->staging, prim, bytes, cudaMemcpyHostToDevice, b->stream), "set_fields copy");
+        src = b->staging;
+    }
+    B_CU(b, b->ops->prim_to_cons(g, src, g.ncell, (char *)b->U + (size_t)w * b->hinst[i].off, b->stream),
          "prim_to_cons");
     b->launches++;
     // new r: the instance's rigid box is unknown until its next stage 3
@@ -561,16 +578,19 @@ dfv_status get_one(dfv_batch *b, int i, double *outp, int which, int on_device)
     const GridP &g = b->hinst[i].g;
     const int w = b->precision == DFV_FP32 ? 4 : 8;
     const void *Ui = (const char *)b->U + (size_t)w * b->hinst[i].off;
+    double *dst = on_device ? outp : static_cast<double *>(const_cast<void *>(mapped_host(outp)));
+    const bool staged = dst == nullptr;
+    if (staged) dst = b->staging;
     if (which == DFV_FIELDS_PRIMITIVE) {
-        B_CU(b, b->ops->cons_to_prim(g, Ui, b->staging, g.ncell, b->stream), "cons_to_prim");
+        B_CU(b, b->ops->cons_to_prim(g, Ui, dst, g.ncell, b->stream), "cons_to_prim");
     } else {
-        B_CU(b, b->ops->cons_to_f64(g, Ui, b->staging, g.ncell, b->ops->nvar, b->stream), "cons_to_f64");
+        B_CU(b, b->ops->cons_to_f64(g, Ui, dst, g.ncell, b->ops->nvar, b->stream), "cons_to_f64");
     }
     b->launches++;
-    const size_t bytes = sizeof(double) * b->ops->nvar * (size_t)g.ncell;
-    B_CU(b, cudaMemcpyAsync(outp, b->staging, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                            b->stream),
-         "get_fields copy");
+    if (staged) {
+        const size_t bytes = sizeof(double) * b->ops->nvar * (size_t)g.ncell;
+        B_CU(b, cudaMemcpyAsync(outp, b->staging, bytes, cudaMemcpyDeviceToHost, b->stream), "get_fields copy");
+    }
     return DFV_OK;
 }
 

@@ -215,3 +215,46 @@ def test_pitched_field_io_matches_packed():
         assert np.all(out[:, wl.ncell:] == -7.0)
     with pytest.raises(B.DfvError):
         b.set_fields_pitched(padded[:, : wl.ncell - 1].copy())
+
+
+@pytest.mark.parametrize("pitched", [False, True])
+def test_page_locked_and_device_fields_match_pageable(pitched):
+    """Fields in page-locked host memory or on the device are converted in
+    place (no staging copy): the same bits in and out as pageable host
+    memory, packed or with padded planes (the padding untouched)."""
+    import torch
+    wl = W.random_state(2, (37, 23), 2, False, seed=42)
+    nv = wl.prim.shape[0]
+    pitch = wl.ncell + (13 if pitched else 0)
+
+    def padded(fill, **kw):
+        return torch.full((nv, pitch), fill, dtype=torch.float64, **kw)
+
+    L = B.load()
+    ref = B.Grid.from_workload(wl, precision=B.DFV_FP32)
+    ref.step(2e-7)
+    grids = []
+    for kind in ("pinned", "device"):
+        buf = padded(float("nan"), pin_memory=True) if kind == "pinned" else padded(float("nan"), device="cuda")
+        buf[:, :wl.ncell] = torch.from_numpy(wl.prim)
+        g = B.Grid.from_workload(wl, precision=B.DFV_FP32)
+        ptr = B._vp(buf.data_ptr())
+        if pitched:
+            B._check(L.dfv_set_fields_pitched(g._h, ptr, pitch, int(kind == "device")), g._h, "set pitched")
+        else:
+            B._check(L.dfv_set_fields(g._h, ptr, int(kind == "device")), g._h, "set")
+        g.step(2e-7)
+        grids.append((kind, g))
+    for which in (B.DFV_FIELDS_CONSERVED, B.DFV_FIELDS_PRIMITIVE):
+        want = ref.get_fields(which)
+        for kind, g in grids:
+            out = padded(-7.0, pin_memory=True) if kind == "pinned" else padded(-7.0, device="cuda")
+            ptr = B._vp(out.data_ptr())
+            if pitched:
+                B._check(L.dfv_get_fields_pitched(g._h, ptr, pitch, which, int(kind == "device")), g._h, "get")
+            else:
+                B._check(L.dfv_get_fields(g._h, ptr, which, int(kind == "device")), g._h, "get")
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            np.testing.assert_array_equal(got[:, :wl.ncell], want, err_msg=kind)
+            assert np.all(got[:, wl.ncell:] == -7.0), kind
