@@ -85,30 +85,26 @@ __device__ __forceinline__ float4 gasw_prim(const A &a, const float c[4], bool f
     return make_float4(w[0], fx ? -w[1] : w[1], fy ? -w[2] : w[2], w[3]);
 }
 
+// the (rho, u) and (v, p) halves of a state, for the packed FP32 units
+__device__ __forceinline__ float2 gasw_lo(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 gasw_hi(const float4 &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 gasw_cat(const float2 &l, const float2 &h) { return make_float4(l.x, l.y, h.x, h.y); }
+
 // van Leer face values of cell c from its backward and forward differences
 // db = c - m, df = p - c along one direction: lo at its face towards m, hi
 // at its face towards p
 __device__ __forceinline__ void gasw_faces_d(const float4 &c, const float4 &db, const float4 &df, float4 &lo,
                                              float4 &hi)
 {
-    float s;
-    s = gas_vanleer(db.x, df.x);
-    lo.x = fmaf(-0.5f, s, c.x);
-    hi.x = fmaf(0.5f, s, c.x);
-    s = gas_vanleer(db.y, df.y);
-    lo.y = fmaf(-0.5f, s, c.y);
-    hi.y = fmaf(0.5f, s, c.y);
-    s = gas_vanleer(db.z, df.z);
-    lo.z = fmaf(-0.5f, s, c.z);
-    hi.z = fmaf(0.5f, s, c.z);
-    s = gas_vanleer(db.w, df.w);
-    lo.w = fmaf(-0.5f, s, c.w);
-    hi.w = fmaf(0.5f, s, c.w);
+    const float2 s0 = gas_vanleer2(gasw_lo(db), gasw_lo(df)), s1 = gas_vanleer2(gasw_hi(db), gasw_hi(df));
+    const float2 mh = make_float2(-0.5f, -0.5f), ph = make_float2(0.5f, 0.5f);
+    lo = gasw_cat(__ffma2_rn(mh, s0, gasw_lo(c)), __ffma2_rn(mh, s1, gasw_hi(c)));
+    hi = gasw_cat(__ffma2_rn(ph, s0, gasw_lo(c)), __ffma2_rn(ph, s1, gasw_hi(c)));
 }
 
 __device__ __forceinline__ float4 gasw_sub(const float4 &p, const float4 &q)
 {
-    return make_float4(p.x - q.x, p.y - q.y, p.z - q.z, p.w - q.w);
+    return gasw_cat(gas_sub2(gasw_lo(p), gasw_lo(q)), gas_sub2(gasw_hi(p), gasw_hi(q)));
 }
 
 // the same from the neighbours m and p
@@ -144,18 +140,22 @@ __device__ __forceinline__ float4 gasw_shfl_down(const float4 &v)
                        __shfl_down_sync(0xffffffffu, v.z, 1), __shfl_down_sync(0xffffffffu, v.w, 1));
 }
 
-// one conserved variable of an owned cell: flux divergence (TwoSum), rigid
-// mask, RK combination
+// two conserved variables of an owned cell: flux divergence (the x and y
+// terms summed by TwoSum, the error kept as the low part), rigid mask, RK
+// combination out = ca un + cb (in - dt (hi + lo)), the low part first
 template <int STAGE>
-__device__ __forceinline__ float gasw_update(float unv, float inv, float fxl, float fxr, float fyl, float fyr,
-                                             float idx, float idy, float dt, float ca, float cb, bool masked)
+__device__ __forceinline__ float2 gasw_update2(float2 unv, float2 inv, float2 fxl, float2 fxr, float2 fyl, float2 fyr,
+                                              float2 idx, float2 idy, float2 mdt, float2 ca, float2 cb, bool masked)
 {
-    const float div = __fmul_rn(fxr - fxl, idx);
-    const float dvy = __fmul_rn(fyr - fyl, idy);
-    Acc<float> D;
-    D.set(div);
-    D.add(dvy);
-    return masked ? unv : rk_combine<float>(STAGE, unv, inv, D, dt, ca, cb);
+    const float2 div = __fmul2_rn(gas_sub2(fxr, fxl), idx);
+    const float2 dvy = __fmul2_rn(gas_sub2(fyr, fyl), idy);
+    const float2 hi = __fadd2_rn(div, dvy);
+    const float2 bp = gas_sub2(hi, div);
+    const float2 err = __fadd2_rn(gas_sub2(div, gas_sub2(hi, bp)), gas_sub2(dvy, bp));
+    const float2 lo = __fadd2_rn(make_float2(0.f, 0.f), err);
+    const float2 y = __ffma2_rn(mdt, hi, __ffma2_rn(mdt, lo, inv));
+    if (masked) return unv;
+    return STAGE == 1 ? y : __ffma2_rn(cb, y, __fmul2_rn(ca, unv));
 }
 
 // the next work item of a warp from the dynamic queue (lane 0 takes it)
@@ -247,11 +247,19 @@ __device__ __forceinline__ void gasw_item(const GaswArgs &a, const GasInst &I, i
 
         if (owned) {
             const bool masked = u5[4] > 0.5f;
+            const float2 idx2 = make_float2(idx, idx), idy2 = make_float2(idy, idy);
+            const float2 mdt2 = make_float2(-dt, -dt), ca2 = make_float2(ca, ca), cb2 = make_float2(cb, cb);
             float o[5];
-            o[0] = gasw_update<STAGE>(u5[0], cin[0], FxL.x, FxR.x, FyB.x, FyT.x, idx, idy, dt, ca, cb, masked);
-            o[1] = gasw_update<STAGE>(u5[1], cin[1], FxL.y, FxR.y, FyB.y, FyT.y, idx, idy, dt, ca, cb, masked);
-            o[2] = gasw_update<STAGE>(u5[2], cin[2], FxL.z, FxR.z, FyB.z, FyT.z, idx, idy, dt, ca, cb, masked);
-            o[3] = gasw_update<STAGE>(u5[3], cin[3], FxL.w, FxR.w, FyB.w, FyT.w, idx, idy, dt, ca, cb, masked);
+            const float2 o01 = gasw_update2<STAGE>(make_float2(u5[0], u5[1]), make_float2(cin[0], cin[1]),
+                                                   gasw_lo(FxL), gasw_lo(FxR), gasw_lo(FyB), gasw_lo(FyT), idx2, idy2,
+                                                   mdt2, ca2, cb2, masked);
+            const float2 o23 = gasw_update2<STAGE>(make_float2(u5[2], u5[3]), make_float2(cin[2], cin[3]),
+                                                   gasw_hi(FxL), gasw_hi(FxR), gasw_hi(FyB), gasw_hi(FyT), idx2, idy2,
+                                                   mdt2, ca2, cb2, masked);
+            o[0] = o01.x;
+            o[1] = o01.y;
+            o[2] = o23.x;
+            o[3] = o23.y;
             {
                 // r: no flux without a moving body
                 Acc<float> D;
